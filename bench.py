@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark: patch.atom Gibbs updates/s of BPFA dictionary learning on GB300.
+
+Workload (one "step"): learn a dictionary from scratch on a 512x512 synthetic
+STEM frame (two lattice grains with a 15 degree boundary, Poisson noise at
+50 e-/px), 10% random mask, 10x10 patches at stride 1 (N = 253,009 patches,
+P = 100), K = 128 atoms, 50 Gibbs iterations (code sweep, dictionary sweep,
+pi / gamma draws), then the overlap-add reconstruction.  The frame is resident
+in HBM; an L2 flush (256 MiB write) precedes every timed step.
+
+value = N * K * iterations * steps / (sum of per-step CUDA-event times), over
+all ranks (independent replicas, weak scaling).  ``e2e`` repeats the step
+through the C ABI with pinned host buffers (frame copied in, reconstruction
+copied out inside the timed region).  ``roofline`` reports the code-sweep
+kernel against the SM issue ceiling; ``cpu_baseline`` times the FP64 oracle.
+
+``--impl reference`` times the FP64 CPU oracle (the only reference for this
+method) on the same workload: each step is one Gibbs iteration of a band of
+frame rows, sized so the whole run ends within a few minutes.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(M=(512, 512), B=(10, 10), S=(1, 1), K=128, frac=0.10, grains=2, iters=50, seed=0)
+WORKLOAD_NAME = ("stem512_k128: 512x512 two-grain synthetic STEM frame, 10% Bernoulli mask, "
+                 "10x10 patches stride 1 (N=253009, P=100), K=128, 50 Gibbs iterations "
+                 "(codes + dictionary + pi/gamma) from the prior, then overlap-add")
+METRIC = "patch·atom Gibbs updates/s"
+UNIT = "patch·atom updates/s"
+
+# Algorithmic lane-operations of one code update (roofline):
+#   2 |Omega_i| FMAs (masked norm + correlation), 75 fixed (Philox4x32-10:
+#   60, log-odds / sigmoid / threshold: 15), 14 more when z = 1 (Box-Muller +
+#   weight), |Omega_i| FMAs when the weight changes (rank-1 residual update).
+OPS_FIXED, OPS_GAUSS = 75, 14
+SMS, LANES_PER_SM = 152, 128
+
+
+def _frame():
+    from paper_2311_15061_gb300 import synth
+    x, clean = synth.stem_frame(WORKLOAD["M"], WORKLOAD["seed"], grains=WORKLOAD["grains"])
+    mask = synth.random_mask(WORKLOAD["M"], WORKLOAD["frac"], WORKLOAD["seed"])
+    return x, clean, mask
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _traffic_record(kernel_file):
+    """dram bytes per launch of the code sweep from the committed ncu summary,
+    valid only while the kernel source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "sweep_kernel_stem512_k128_traffic.txt")
+    src = os.path.join(ROOT, "paper_2311_15061_gb300", "csrc", kernel_file)
+    try:
+        kv = dict(line.split(":", 1) for line in open(path).read().splitlines() if ":" in line)
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if kv.get("source_sha256", "").strip() != digest:
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = []
+        for line in getattr(self, "out", "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or not parts[0].isdigit() or int(parts[0]) != self.gpu_index:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for _, _, r in rows for j in range(4) if r[j].lower() == "active"})
+        busy = [r for r in rows if r[0] > 0.5 * r[1]] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in busy), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_gpu(args):
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2311_15061_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2311_15061_gb300 import sensai
+
+    x, clean, mask = _frame()
+    w = WORKLOAD
+    prm = sensai.make_params(w["M"], w["B"], w["S"], w["K"], seed=w["seed"] + rank)
+    ctx = sensai.Context(prm, mask)
+    N, K, iters = ctx.N, ctx.K, w["iters"]
+    stream = torch.cuda.current_stream()
+    frame = torch.from_numpy(x).cuda()
+    out = torch.empty_like(frame)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    ctx.sensai_set_frame(frame, stream)
+
+    def step():
+        ctx.sensai_reset(stream)
+        ctx.sensai_learn(None, iters, stream)
+        ctx.sensai_reconstruct(out, stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or 0) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = ctx.sensai_get_stats().kernel_launches
+    ctx.sensai_profile(1)
+    with ClockSampler(gpu_index) as clocks:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    stats = ctx.sensai_get_stats()
+    launches = stats.kernel_launches - launches0
+    prof = ctx.sensai_profile_read()
+    ctx.sensai_profile(0)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    updates = float(N) * K * iters * args.steps * world
+    value = updates / (total_ms / 1e3)
+
+    # roofline of the code sweep (dominant kernel)
+    sweep_ms, sweep_n = prof["codes"]
+    n_obs = ctx.sensai_get_stats().n_observed
+    ops = (sweep_n * K * (2.0 * n_obs + OPS_FIXED * N) + float(stats.changed_observed)
+           + OPS_GAUSS * float(stats.active_draws))
+    peaks, peak_src = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SMS * LANES_PER_SM * sm_mhz * 1e6 / 1e12   # T lane-ops/s
+    achieved = ops / sweep_n / (sweep_ms / sweep_n / 1e3) / 1e12
+    traffic = _traffic_record("sweep.cu")
+
+    # end to end through the C ABI with pinned host buffers
+    xh = torch.from_numpy(x).pin_memory()
+    oh = torch.empty(x.shape, dtype=torch.float32).pin_memory()
+    xh_np, oh_np = xh.numpy(), oh.numpy()
+    e2e_steps = max(1, min(args.steps, 20))
+    ctx.sensai_reset(stream)
+    ctx.sensai_learn(xh_np, iters, stream)
+    ctx.sensai_reconstruct(oh_np, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.sensai_reset(stream)
+        ctx.sensai_learn(xh_np, iters, stream)
+        ctx.sensai_reconstruct(oh_np, stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = float(N) * K * iters * e2e_steps * world / e2e_s
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "l2": "flushed before each step (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "patches": N, "atoms": K, "iterations": iters},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes),
+                "d2h_bytes_per_step": int(x.nbytes), "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "kernel": "sweep_kernel (code sweep)", "achieved": achieved,
+                     "peak": peak, "unit": "T lane-ops/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz ({peak_src} max SM clock)",
+                     "ms_per_launch": sweep_ms / sweep_n, "launches": sweep_n},
+        "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "wall_s": wall,
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _oracle_band(rows):
+    """The workload restricted to the first ``rows`` frame rows."""
+    import oracle as O
+    x, clean, mask = _frame()
+    w = WORKLOAD
+    xs, ms = np.ascontiguousarray(x[:rows]), np.ascontiguousarray(mask[:rows])
+    prm = O.params((rows, w["M"][1]), w["B"], w["S"], w["K"], seed=w["seed"])
+    return O, prm, xs, ms
+
+
+def _oracle_iteration(rows, iters=1):
+    O, prm, xs, ms = _oracle_band(rows)
+    st = O.State(prm)
+    t0 = time.perf_counter()
+    O.learn(st, xs, ms, iters)
+    dt = time.perf_counter() - t0
+    return O.num_patches(prm) * prm.K * iters, dt, O.num_threads()
+
+
+def cpu_baseline():
+    rows = WORKLOAD["M"][0]
+    upd, dt, cores = _oracle_iteration(rows, 1)
+    return {"value": upd / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"1 full Gibbs iteration (codes + dictionary + pi/gamma) of the full 512x512 "
+                      f"K=128 workload from the prior, {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    budget_s = 150.0
+    # calibrate on a small band, then size the per-step band to the budget
+    upd, dt, cores = _oracle_iteration(24, 1)
+    per_row_s = dt / 24.0
+    steps_total = args.steps + args.warmup
+    rows = int(max(12, min(WORKLOAD["M"][0], budget_s / steps_total / per_row_s)))
+    for _ in range(args.warmup):
+        _oracle_iteration(rows, 1)
+    total_upd, total_s = 0.0, 0.0
+    for _ in range(args.steps):
+        u, d, cores = _oracle_iteration(rows, 1)
+        total_upd += u
+        total_s += d
+    value = total_upd / total_s
+    sample = (f"per step: 1 Gibbs iteration (codes + dictionary + pi/gamma) of the first {rows} "
+              f"of 512 frame rows of the workload (same patch size, K, mask density)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAME},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["sensai", "reference"], default="sensai")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

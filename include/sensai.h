@@ -1,0 +1,194 @@
+/*
+ * sensai.h -- C ABI of the GB300 (sm_103a) BPFA inpainting library.
+ *
+ * The library runs the Gibbs sampler of Beta-Process Factor Analysis (BPFA),
+ * the model the paper's "Beta-Process Factor Analysis (BPFA)" section uses for
+ * joint dictionary learning and sparse coding, over every overlapping N-D
+ * patch of a subsampled frame ("N-Dimensional Inpainting" section), with all
+ * arithmetic in hand-written CUDA kernels on one GPU.
+ *
+ * Model (from the nonparametric factor-analysis papers the BPFA section
+ * cites): patch i of P pixels, observed on its mask Omega_i,
+ *   x_i = D (z_i o s_i) + eps_i,  d_k ~ N(0, I/P),  s_ik ~ N(0, 1/gamma_s),
+ *   z_ik ~ Bernoulli(pi_k),  pi_k ~ Beta(a/K, b(K-1)/K),
+ *   gamma_s ~ Gamma(c, d),  gamma_eps ~ Gamma(e, f)  (shape, rate),
+ *   eps_i ~ N(0, I/gamma_eps).
+ * One iteration t: (1) sparse-code sweep, patches in parallel, atoms
+ * k = 0..K-1 in order, z_ik drawn with s_ik integrated out, then s_ik | z=1;
+ * (2) dictionary sweep, atoms in order, d_kp from its conjugate Gaussian;
+ * (3) pi_k, gamma_s, gamma_eps from their conjugate Beta / Gamma laws.
+ * Inactive weights are not stored (w_ik = z_ik s_ik, zero when z_ik = 0).
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by `seed`,
+ * counter (index0, index1, t, tag | attempt << 8); uniforms (x + 1) 2^-32;
+ * Box-Muller normals; Marsaglia-Tsang Gamma.  Results depend only on the
+ * parameters, seed, frame, mask and iteration index.
+ *
+ * Conventions for every entry point:
+ *  - Frames, masks and outputs are row-major over M (last dimension fastest).
+ *    Patches are numbered row-major over the grid of patch starts; pixels in
+ *    a patch row-major over B.  D is K x P row-major.
+ *  - Pointers documented "host or device" are classified with
+ *    cudaPointerGetAttributes; device pointers must be on the context's GPU.
+ *    The caller owns every buffer it passes and keeps it valid until the call
+ *    returns; calls that read or write host memory synchronise `stream`
+ *    before returning.  Calls that only touch device memory are asynchronous
+ *    on `stream` (a cudaStream_t; NULL is the legacy default stream).
+ *  - Errors are returned, never raised: SENSAI_EINVAL for bad arguments
+ *    (nothing is changed), SENSAI_ENOMEM when device memory runs out,
+ *    SENSAI_ECUDA for a CUDA error, SENSAI_ESTATE when the context is unusable
+ *    (after a sticky CUDA error, or a frame is needed and none was given).
+ *    sensai_last_error() returns a message for the calling thread.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef SENSAI_H
+#define SENSAI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sensai_ctx sensai_ctx;
+
+typedef enum {
+    SENSAI_OK = 0,
+    SENSAI_EINVAL = 1,
+    SENSAI_ENOMEM = 2,
+    SENSAI_ECUDA = 3,
+    SENSAI_ETIMEOUT = 4,
+    SENSAI_EBUSY = 5,
+    SENSAI_ESTATE = 6
+} sensai_status;
+
+/* Problem definition.  Requirements: 1 <= ndim <= 4; 1 <= B[d] <= M[d];
+ * stride[d] >= 1 with (M[d] - B[d]) divisible by stride[d]; 1 <= K <= 1024;
+ * P = prod(B) <= 1024; number of patches < 2^31.  a <= 0 selects a = K and
+ * b <= 0 selects b = N / 8 (N = number of patches).  c..f > 0.  flags must
+ * be 0. */
+typedef struct {
+    int32_t ndim;
+    int64_t M[4];
+    int32_t B[4];
+    int32_t stride[4];
+    int32_t K;
+    double a, b;
+    double c, d;
+    double e, f;
+    uint64_t seed;
+    int32_t flags;
+} sensai_params;
+
+/* Sampler state as host arrays (get/set).  Any pointer may be NULL to skip
+ * that part.  D: K*P floats.  Z: N*K bytes, patch-major (Z[i*K + k]).  S:
+ * N*K floats, patch-major; S is 0 where Z is 0.  pi: K doubles. */
+typedef struct {
+    float* D;
+    uint8_t* Z;
+    float* S;
+    double* pi;
+    double gamma_s;
+    double gamma_eps;   /* <= 0 on get: not yet initialised; on set: leave unset */
+    int64_t iter;       /* iteration index t used by the next draws */
+} sensai_state;
+
+/* Summary of the last completed phase, read back from the device. */
+typedef struct {
+    int64_t iter;          /* current iteration index t */
+    int64_t n_patches;     /* N */
+    int64_t patch_size;    /* P */
+    int64_t n_observed;    /* sum_i |Omega_i| */
+    int64_t n_active;      /* sum_ik z_ik */
+    int32_t max_observed;  /* max_i |Omega_i| */
+    int32_t K;
+    double sum_s2;         /* sum of s_ik^2 over active entries */
+    double sum_r2;         /* sum_i ||r_i||^2 on observed pixels (last residual pass) */
+    double gamma_s;
+    double gamma_eps;
+    int64_t kernel_launches;   /* kernels this context has launched so far */
+    int64_t changed_updates;   /* code updates whose weight changed, since the last profile start */
+    int64_t changed_observed;  /* sum of |Omega_i| over those updates */
+    int64_t active_draws;      /* code draws with z = 1, since the last profile start */
+} sensai_stats;
+
+/* Create a context on the current CUDA device.  `mask` is prod(M) host bytes
+ * (nonzero = sampled pixel), copied.  Geometry (observed-pixel lists, per-
+ * pixel patch bitmaps) is built on the device; the dictionary is drawn from
+ * its prior (counter (p, k, 0, INIT)), all codes are 0, pi_k = 0.5,
+ * gamma_s = 1 and gamma_eps is set from the first frame as
+ * 1 / max(var(observed pixels), 1e-12).  Device memory is allocated here
+ * and released by sensai_destroy.  Sec. "N-Dimensional Inpainting" (patch
+ * shape B in any dimension), Sec. "SenseAI: Feature Summary" (modular
+ * library, programmatic signal selection = the caller's mask). */
+sensai_status sensai_create(const sensai_params* params, const uint8_t* mask, sensai_ctx** out);
+void sensai_destroy(sensai_ctx* ctx);
+
+/* Copy a frame (prod(M) floats, host or device) into the context. */
+sensai_status sensai_set_frame(sensai_ctx* ctx, const float* frame, void* stream);
+
+/* Return the state to its initial draw (dictionary from the prior, codes 0,
+ * pi = 0.5, gamma_s = 1, gamma_eps unset, t = 0).  Asynchronous. */
+sensai_status sensai_reset(sensai_ctx* ctx, void* stream);
+
+/* Joint dictionary learning and sparse coding (Sec. "Beta-Process Factor
+ * Analysis (BPFA)": each iteration performs a dictionary-learning step and a
+ * sparse-coding step).  `frame` (host or device, may be NULL to keep the
+ * current frame) is copied first.  Runs `iters` iterations, each: code
+ * sweep, dictionary sweep, pi / gamma draws, then t += 1. */
+sensai_status sensai_learn(sensai_ctx* ctx, const float* frame, int32_t iters, void* stream);
+
+/* Sparse coding with the dictionary held fixed (dictionary transfer, Sec.
+ * "SenseAI: Feature Summary"): copies `frame` (host or device, not NULL),
+ * clears the codes, runs `sweeps` iterations of code sweep + pi / gamma
+ * draws (t += 1 each), then writes the overlap-add reconstruction to `out`
+ * (prod(M) floats, host or device; may be NULL to skip). */
+sensai_status sensai_inpaint(sensai_ctx* ctx, const float* frame, int32_t sweeps, float* out, void* stream);
+
+/* Single phases at the current t (t is not advanced):
+ *  - sensai_sweep_codes: one sparse-code sweep (patch extraction fused);
+ *  - sensai_draw_dictionary: one dictionary sweep, atoms in order;
+ *  - sensai_draw_hyper: pi_k, gamma_s, gamma_eps (gamma_eps uses the current
+ *    residual).
+ * These exist so each step can be checked on its own. */
+sensai_status sensai_sweep_codes(sensai_ctx* ctx, void* stream);
+sensai_status sensai_draw_dictionary(sensai_ctx* ctx, void* stream);
+sensai_status sensai_draw_hyper(sensai_ctx* ctx, void* stream);
+
+/* Overlap-add reconstruction: every pixel's mean over the patches covering
+ * it of (D w_i) at that pixel, observed pixels included (the reconstruction
+ * of Sec. "Time-To-Solution").  `out`: prod(M) floats, host or device. */
+sensai_status sensai_reconstruct(sensai_ctx* ctx, float* out, void* stream);
+
+/* Number of patches covering each pixel (int32, prod(M), host or device):
+ * per dimension floor(min(y, last) / S) - ceil(max(0, y - B + 1) / S) + 1
+ * with last = (G - 1) S the final patch start, multiplied over dimensions. */
+sensai_status sensai_overlap_counts(sensai_ctx* ctx, int32_t* out, void* stream);
+
+/* Dictionary transfer: K*P host floats. */
+sensai_status sensai_get_dictionary(sensai_ctx* ctx, float* D);
+sensai_status sensai_set_dictionary(sensai_ctx* ctx, const float* D);
+
+/* Read or replace the sampler state (host arrays, synchronous). */
+sensai_status sensai_get_state(sensai_ctx* ctx, sensai_state* state);
+sensai_status sensai_set_state(sensai_ctx* ctx, const sensai_state* state);
+
+/* Synchronise the last stream used and report the statistics. */
+sensai_status sensai_get_stats(sensai_ctx* ctx, sensai_stats* stats);
+
+/* Per-phase device timing.  enable = 1 clears the record and starts timing:
+ * every later phase records a CUDA event pair on its launching stream;
+ * enable = 0 stops.  sensai_profile_read synchronises and returns, for the
+ * phases {code sweep, dictionary sweep, pi/gamma draws, reconstruction}, the
+ * summed milliseconds ms[4] and the number of timed launches counts[4].
+ * Tracing support; the paper has no counterpart. */
+sensai_status sensai_profile(sensai_ctx* ctx, int32_t enable);
+sensai_status sensai_profile_read(sensai_ctx* ctx, double* ms, int64_t* counts);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* sensai_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

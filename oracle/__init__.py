@@ -102,6 +102,8 @@ def lib():
         "orc_init_dictionary": (None, [pp, P(dbl)]),
         "orc_init_gamma_eps": (dbl, [pp, P(f32), P(u8)]),
         "orc_zs_sweep": (None, [pp, P(f32), P(u8), P(dbl), P(u8), P(dbl), P(dbl), dbl, dbl, i64, P(dbl)]),
+        "orc_zs_sweep_subset": (None, [pp, P(f32), P(u8), P(dbl), P(u8), P(dbl), P(dbl), dbl, dbl, i64,
+                                       P(i64), i64, P(dbl), P(dbl)]),
         "orc_d_sweep": (None, [pp, P(f32), P(u8), P(dbl), P(u8), P(dbl), dbl, i64]),
         "orc_hyper": (None, [pp, P(f32), P(u8), P(dbl), P(u8), P(dbl), P(dbl), P(dbl), P(dbl), i64, P(dbl)]),
         "orc_reconstruct": (None, [pp, P(dbl), P(u8), P(dbl), P(dbl)]),
@@ -206,6 +208,23 @@ def zs_sweep(st, x, mask):
                        _p(st.D, ctypes.c_double), _p(st.Z, ctypes.c_uint8), _p(st.S, ctypes.c_double),
                        _p(st.pi, ctypes.c_double), st.gamma_s, st.gamma_eps, st.t, _p(stats, ctypes.c_double))
     return stats
+
+
+def zs_sweep_subset(st, x, mask, patches=None, want_logodds=False):
+    """Sweep only ``patches`` (all if None); returns (stats, logodds or None)."""
+    x = np.ascontiguousarray(x, np.float32)
+    m = np.ascontiguousarray(mask, np.uint8)
+    if st.gamma_eps is None:
+        st.gamma_eps = init_gamma_eps(st.prm, x, m)
+    stats = np.zeros(3)
+    L = np.full(st.Z.shape, np.nan) if want_logodds else None
+    idx = None if patches is None else np.ascontiguousarray(patches, np.int64)
+    lib().orc_zs_sweep_subset(
+        ctypes.byref(st.prm), _p(x, ctypes.c_float), _p(m, ctypes.c_uint8), _p(st.D, ctypes.c_double),
+        _p(st.Z, ctypes.c_uint8), _p(st.S, ctypes.c_double), _p(st.pi, ctypes.c_double), st.gamma_s,
+        st.gamma_eps, st.t, None if idx is None else _p(idx, ctypes.c_int64), -1 if idx is None else len(idx),
+        None if L is None else _p(L, ctypes.c_double), _p(stats, ctypes.c_double))
+    return stats, L
 
 
 def d_sweep(st, x, mask):

@@ -278,6 +278,14 @@ void orc_zs_sweep(const orc_params* prm, const float* x, const uint8_t* mask,
                   const double* D, uint8_t* Z, double* S, const double* pi,
                   double gamma_s, double gamma_eps, int64_t t, double* stats)
 {
+    orc_zs_sweep_subset(prm, x, mask, D, Z, S, pi, gamma_s, gamma_eps, t, NULL, -1, NULL, stats);
+}
+
+void orc_zs_sweep_subset(const orc_params* prm, const float* x, const uint8_t* mask,
+                         const double* D, uint8_t* Z, double* S, const double* pi,
+                         double gamma_s, double gamma_eps, int64_t t,
+                         const int64_t* patches, int64_t npatches, double* logodds, double* stats)
+{
     const int64_t N = orc_num_patches(prm), P = orc_patch_size(prm);
     const int K = prm->K;
     int64_t* origin = malloc(sizeof(int64_t) * N);
@@ -296,8 +304,10 @@ void orc_zs_sweep(const orc_params* prm, const float* x, const uint8_t* mask,
         int64_t* plist = malloc(sizeof(int64_t) * P);
         double* xlist = malloc(sizeof(double) * P);
         double* r = malloc(sizeof(double) * P);
+const int64_t nvisit = patches ? npatches : N;
 #pragma omp for schedule(static)
-        for (int64_t i = 0; i < N; ++i) {
+        for (int64_t v = 0; v < nvisit; ++v) {
+            const int64_t i = patches ? patches[v] : v;
             int64_t nobs = observed_list(origin, offset, P, i, x, mask, plist, xlist);
             /* residual on the observed pixels: r = x - D w_i */
             for (int64_t j = 0; j < nobs; ++j) {
@@ -321,6 +331,7 @@ void orc_zs_sweep(const orc_params* prm, const float* x, const uint8_t* mask,
                 /* log odds of z = 1 with s integrated out */
                 double L = logit_pi[k] + half_log_gs - 0.5 * log(lam)
                          + gamma_eps * gamma_eps * g * g / (2.0 * lam);
+                if (logodds) logodds[i * K + k] = L;
                 double sig = 1.0 / (1.0 + exp(-L));
                 uint64_t thr = (uint64_t)floor(sig * 4294967296.0);
                 uint32_t blk[4];

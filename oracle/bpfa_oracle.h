@@ -107,6 +107,16 @@ void orc_zs_sweep(const orc_params* prm, const float* x, const uint8_t* mask,
                   const double* D, uint8_t* Z, double* S, const double* pi,
                   double gamma_s, double gamma_eps, int64_t t, double* stats);
 
+/* The same sweep restricted to the listed patches (patches are independent
+ * given D, pi and the precisions, and each keeps its own Philox counters), and
+ * optionally recording the log odds L of every visited draw in logodds
+ * (N x K, may be NULL).  patches == NULL visits all of them.  Test
+ * instrumentation: the arithmetic is that of orc_zs_sweep. */
+void orc_zs_sweep_subset(const orc_params* prm, const float* x, const uint8_t* mask,
+                         const double* D, uint8_t* Z, double* S, const double* pi,
+                         double gamma_s, double gamma_eps, int64_t t,
+                         const int64_t* patches, int64_t npatches, double* logodds, double* stats);
+
 /* Dictionary sweep at iteration t, atoms in order.  Updates D in place. */
 void orc_d_sweep(const orc_params* prm, const float* x, const uint8_t* mask,
                  double* D, const uint8_t* Z, const double* S, double gamma_eps, int64_t t);

@@ -1,0 +1,776 @@
+// api.cu -- the sensai C ABI (include/sensai.h): context, device memory,
+// sequencing of the Gibbs phases, host/device pointer handling, errors.
+//
+// Host code here only validates arguments, allocates, copies and launches;
+// every arithmetic step of the sampler runs in the kernels of sweep.cu,
+// dict.cu, hyper.cu and geometry.cu.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace sensai;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sensai_status fail(sensai_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+}  // namespace
+
+struct sensai_ctx {
+    int device = 0;
+    Geom g{};
+    sensai_params prm{};
+    double a_over_K = 0, b_scaled = 0;
+    int maxobs = 0, max_slots = 0;
+    long long n_observed = 0;
+    int sweep_grid = 0;
+    int64_t t = 0;
+    bool frame_set = false;
+    bool ge_set = false;
+    bool codes_valid = false;   // m / part_s2 describe the current codes
+    bool resid_valid = false;   // R / part_r2 describe the current residual
+    int n_r2 = 0;               // valid entries of part_r2
+    bool broken = false;
+    cudaStream_t last_stream = nullptr;
+    long long launches = 0;     // kernels launched by this context
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed[4];  // per phase
+
+    uint32_t* mask_bits = nullptr;
+    int* imgoff = nullptr;
+    uint16_t* nobs = nullptr;
+    uint16_t* obs = nullptr;
+    uint32_t* Ibits = nullptr;
+    uint32_t* Ipre = nullptr;
+    int* Icnt = nullptr;
+    int* Rbase = nullptr;
+    int* misc = nullptr;        // [0] max observed per patch, [1] max slots per pixel
+    float* x = nullptr;
+    float* D = nullptr;
+    float* W = nullptr;
+    uint32_t* Zb = nullptr;
+    float* R = nullptr;
+    float* Y = nullptr;         // per-patch reconstructions, P x N
+    float* out = nullptr;       // frame-sized staging buffer
+    double* pi = nullptr;
+    float* lpi = nullptr;
+    int* m = nullptr;
+    double* part_s2 = nullptr;
+    double* part_r2 = nullptr;
+    unsigned int* chunk_counter = nullptr;
+    DevScalars* sc = nullptr;
+};
+
+namespace {
+
+#define SENSAI_CUDA(ctx, call)                                                                   \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return cuda_failure((ctx), e_, #call, __LINE__);                 \
+    } while (0)
+
+sensai_status cuda_failure(sensai_ctx* ctx, cudaError_t e, const char* what, int line)
+{
+    if (ctx) ctx->broken = true;
+    const sensai_status st = (e == cudaErrorMemoryAllocation) ? SENSAI_ENOMEM : SENSAI_ECUDA;
+    return fail(st, "CUDA error %d (%s) at api.cu:%d in %s", (int)e, cudaGetErrorString(e), line, what);
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+bool is_device_pointer(const void* p)
+{
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+void free_all(sensai_ctx* c)
+{
+    void* ptrs[] = {c->mask_bits, c->imgoff, c->nobs, c->obs, c->Ibits, c->Ipre, c->Icnt, c->Rbase,
+                    c->misc, c->x, c->D, c->W, c->Zb, c->R, c->Y, c->out, c->pi, c->lpi, c->m,
+                    c->part_s2, c->part_r2, c->chunk_counter, c->sc};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+enum Phase { kPhaseCodes = 0, kPhaseDict = 1, kPhaseHyper = 2, kPhaseRecon = 3 };
+
+// Event pair around one phase on its launching stream (only while profiling).
+struct PhaseTimer {
+    sensai_ctx* ctx;
+    int phase;
+    cudaStream_t s;
+    cudaEvent_t start = nullptr;
+    PhaseTimer(sensai_ctx* c, int ph, cudaStream_t st) : ctx(c), phase(ph), s(st)
+    {
+        if (!ctx->profiling) return;
+        if (cudaEventCreate(&start) != cudaSuccess || cudaEventRecord(start, s) != cudaSuccess) {
+            cudaGetLastError();
+            start = nullptr;
+        }
+    }
+    void stop()
+    {
+        if (!start) return;
+        cudaEvent_t end = nullptr;
+        if (cudaEventCreate(&end) == cudaSuccess && cudaEventRecord(end, s) == cudaSuccess) {
+            ctx->timed[phase].emplace_back(start, end);
+        } else {
+            cudaGetLastError();
+            cudaEventDestroy(start);
+            if (end) cudaEventDestroy(end);
+        }
+        start = nullptr;
+    }
+};
+
+void clear_timers(sensai_ctx* ctx)
+{
+    for (auto& v : ctx->timed) {
+        for (auto& pr : v) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        v.clear();
+    }
+}
+
+sensai_status enter(sensai_ctx* ctx)
+{
+    if (!ctx) return fail(SENSAI_EINVAL, "null context");
+    if (ctx->broken) return fail(SENSAI_ESTATE, "context unusable after an earlier CUDA error");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_failure(ctx, e, "cudaSetDevice", __LINE__);
+    return SENSAI_OK;
+}
+
+sensai_status copy_frame(sensai_ctx* ctx, const float* frame, cudaStream_t s)
+{
+    const size_t bytes = sizeof(float) * (size_t)ctx->g.nframe;
+    const cudaMemcpyKind kind = is_device_pointer(frame) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    SENSAI_CUDA(ctx, cudaMemcpyAsync(ctx->x, frame, bytes, kind, s));
+    if (kind == cudaMemcpyHostToDevice) SENSAI_CUDA(ctx, cudaStreamSynchronize(s));
+    ctx->frame_set = true;
+    ctx->resid_valid = false;
+    return SENSAI_OK;
+}
+
+sensai_status ensure_gamma_eps(sensai_ctx* ctx, cudaStream_t s)
+{
+    if (ctx->ge_set) return SENSAI_OK;
+    SENSAI_CUDA(ctx, launch_init_gamma_eps(ctx->g, ctx->x, ctx->mask_bits, ctx->sc, s));
+    ctx->launches += 1;
+    ctx->ge_set = true;
+    return SENSAI_OK;
+}
+
+sensai_status ensure_residual(sensai_ctx* ctx, cudaStream_t s)
+{
+    if (ctx->resid_valid) return SENSAI_OK;
+    SENSAI_CUDA(ctx, launch_residual(ctx->g, ctx->x, ctx->obs, ctx->nobs, ctx->imgoff, ctx->D, ctx->W, ctx->Zb,
+                                     ctx->Ibits, ctx->Ipre, ctx->Rbase, ctx->R, ctx->part_r2, s));
+    ctx->launches += 1;
+    ctx->resid_valid = true;
+    ctx->n_r2 = ctx->g.NW;
+    return SENSAI_OK;
+}
+
+sensai_status ensure_code_stats(sensai_ctx* ctx, cudaStream_t s)
+{
+    if (ctx->codes_valid) return SENSAI_OK;
+    SENSAI_CUDA(ctx, launch_code_stats(ctx->g, ctx->W, ctx->Zb, ctx->m, ctx->part_s2, s));
+    ctx->launches += 1;
+    ctx->codes_valid = true;
+    return SENSAI_OK;
+}
+
+sensai_status run_sweep(sensai_ctx* ctx, cudaStream_t s)
+{
+    if (!ctx->frame_set) return fail(SENSAI_ESTATE, "no frame: call sensai_set_frame or pass a frame");
+    sensai_status st = ensure_gamma_eps(ctx, s);
+    if (st != SENSAI_OK) return st;
+    SweepArgs a{};
+    a.g = ctx->g;
+    a.x = ctx->x;
+    a.obs = ctx->obs;
+    a.nobs = ctx->nobs;
+    a.imgoff = ctx->imgoff;
+    a.D = ctx->D;
+    a.W = ctx->W;
+    a.Zb = ctx->Zb;
+    a.lpi = ctx->lpi;
+    a.sc = ctx->sc;
+    a.Ibits = ctx->Ibits;
+    a.Ipre = ctx->Ipre;
+    a.Rbase = ctx->Rbase;
+    a.R = ctx->R;
+    a.m = ctx->m;
+    a.part_s2 = ctx->part_s2;
+    a.part_r2 = ctx->part_r2;
+    a.chunk_counter = ctx->chunk_counter;
+    a.sc_out = ctx->sc;
+    a.seed = ctx->prm.seed;
+    a.t = (uint32_t)ctx->t;
+    PhaseTimer timer(ctx, kPhaseCodes, s);
+    SENSAI_CUDA(ctx, cudaMemsetAsync(ctx->m, 0, sizeof(int) * ctx->g.K, s));
+    SENSAI_CUDA(ctx, launch_sweep(a, ctx->maxobs, ctx->sweep_grid, s));
+    timer.stop();
+    ctx->launches += 1;
+    ctx->codes_valid = true;
+    ctx->resid_valid = true;
+    ctx->n_r2 = ctx->g.NW;
+    return SENSAI_OK;
+}
+
+sensai_status run_dictionary(sensai_ctx* ctx, cudaStream_t s)
+{
+    if (!ctx->frame_set) return fail(SENSAI_ESTATE, "no frame: call sensai_set_frame or pass a frame");
+    sensai_status st = ensure_gamma_eps(ctx, s);
+    if (st != SENSAI_OK) return st;
+    st = ensure_residual(ctx, s);
+    if (st != SENSAI_OK) return st;
+    DictArgs a{};
+    a.g = ctx->g;
+    a.D = ctx->D;
+    a.W = ctx->W;
+    a.Zb = ctx->Zb;
+    a.Ibits = ctx->Ibits;
+    a.Ipre = ctx->Ipre;
+    a.Rbase = ctx->Rbase;
+    a.R = ctx->R;
+    a.sc = ctx->sc;
+    a.part_r2 = ctx->part_r2;
+    a.seed = ctx->prm.seed;
+    a.t = (uint32_t)ctx->t;
+    PhaseTimer timer(ctx, kPhaseDict, s);
+    SENSAI_CUDA(ctx, launch_dict(a, ctx->max_slots, s));
+    timer.stop();
+    ctx->launches += 1;
+    ctx->n_r2 = ctx->g.P;
+    return SENSAI_OK;
+}
+
+sensai_status run_hyper(sensai_ctx* ctx, cudaStream_t s)
+{
+    if (!ctx->frame_set) return fail(SENSAI_ESTATE, "no frame: call sensai_set_frame or pass a frame");
+    sensai_status st = ensure_gamma_eps(ctx, s);
+    if (st != SENSAI_OK) return st;
+    st = ensure_code_stats(ctx, s);
+    if (st != SENSAI_OK) return st;
+    st = ensure_residual(ctx, s);
+    if (st != SENSAI_OK) return st;
+    HyperArgs a{};
+    a.g = ctx->g;
+    a.m = ctx->m;
+    a.part_s2 = ctx->part_s2;
+    a.n_s2 = ctx->g.NW;
+    a.part_r2 = ctx->part_r2;
+    a.n_r2 = ctx->n_r2;
+    a.n_observed = ctx->n_observed;
+    a.a_over_K = ctx->a_over_K;
+    a.b_scaled = ctx->b_scaled;
+    a.c = ctx->prm.c;
+    a.d = ctx->prm.d;
+    a.e = ctx->prm.e;
+    a.f = ctx->prm.f;
+    a.pi = ctx->pi;
+    a.lpi = ctx->lpi;
+    a.sc = ctx->sc;
+    a.seed = ctx->prm.seed;
+    a.t = (uint32_t)ctx->t;
+    PhaseTimer timer(ctx, kPhaseHyper, s);
+    SENSAI_CUDA(ctx, launch_hyper(a, s));
+    timer.stop();
+    ctx->launches += 1;
+    return SENSAI_OK;
+}
+
+sensai_status clear_codes(sensai_ctx* ctx, cudaStream_t s)
+{
+    SENSAI_CUDA(ctx, cudaMemsetAsync(ctx->W, 0, sizeof(float) * (size_t)ctx->g.K * ctx->g.N, s));
+    SENSAI_CUDA(ctx, cudaMemsetAsync(ctx->Zb, 0, sizeof(uint32_t) * (size_t)ctx->g.K * ctx->g.NW, s));
+    ctx->codes_valid = false;
+    ctx->resid_valid = false;
+    return SENSAI_OK;
+}
+
+sensai_status reset_state(sensai_ctx* ctx, cudaStream_t s)
+{
+    sensai_status st = clear_codes(ctx, s);
+    if (st != SENSAI_OK) return st;
+    SENSAI_CUDA(ctx, launch_init_state(ctx->g, ctx->D, ctx->pi, ctx->lpi, ctx->sc, ctx->prm.seed, s));
+    ctx->launches += 2;
+    ctx->t = 0;
+    ctx->ge_set = false;
+    return SENSAI_OK;
+}
+
+sensai_status write_out(sensai_ctx* ctx, const void* src, void* dst, size_t bytes, cudaStream_t s)
+{
+    const bool dev = is_device_pointer(dst);
+    SENSAI_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!dev) SENSAI_CUDA(ctx, cudaStreamSynchronize(s));
+    return SENSAI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sensai_last_error(void) { return g_last_error.c_str(); }
+
+sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensai_ctx** out)
+{
+    g_last_error.clear();
+    if (!prm || !mask || !out) return fail(SENSAI_EINVAL, "null argument");
+    *out = nullptr;
+    const sensai_params& p = *prm;
+    if (p.ndim < 1 || p.ndim > kMaxDim) return fail(SENSAI_EINVAL, "ndim must be 1..4 (got %d)", p.ndim);
+    if (p.K < 1 || p.K > 1024) return fail(SENSAI_EINVAL, "K must be 1..1024 (got %d)", p.K);
+    if (p.flags != 0) return fail(SENSAI_EINVAL, "flags must be 0");
+    if (!(p.c > 0 && p.d > 0 && p.e > 0 && p.f > 0)) return fail(SENSAI_EINVAL, "c, d, e, f must be > 0");
+    Geom g{};
+    g.ndim = p.ndim;
+    g.K = p.K;
+    long long P = 1, N = 1, nframe = 1;
+    for (int d = 0; d < p.ndim; ++d) {
+        if (p.M[d] < 1 || p.B[d] < 1 || p.B[d] > p.M[d] || p.stride[d] < 1)
+            return fail(SENSAI_EINVAL, "dimension %d: need 1 <= B <= M and stride >= 1", d);
+        if ((p.M[d] - p.B[d]) % p.stride[d] != 0)
+            return fail(SENSAI_EINVAL, "dimension %d: (M - B) = %lld not divisible by stride %d", d,
+                        (long long)(p.M[d] - p.B[d]), p.stride[d]);
+        g.M[d] = p.M[d];
+        g.B[d] = p.B[d];
+        g.S[d] = p.stride[d];
+        g.G[d] = (p.M[d] - p.B[d]) / p.stride[d] + 1;
+        P *= p.B[d];
+        N *= g.G[d];
+        nframe *= p.M[d];
+    }
+    if (P > 1024) return fail(SENSAI_EINVAL, "patch size P = %lld exceeds 1024", P);
+    if (N >= (1LL << 31)) return fail(SENSAI_EINVAL, "too many patches (%lld)", N);
+    if (nframe >= (1LL << 31)) return fail(SENSAI_EINVAL, "frame too large (%lld pixels)", nframe);
+    long long s = 1;
+    for (int d = p.ndim - 1; d >= 0; --d) {
+        g.fs[d] = s;
+        s *= g.M[d];
+    }
+    g.P = (int)P;
+    g.N = N;
+    g.NW = (int)((N + 31) / 32);
+    g.nframe = nframe;
+
+    int device = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return cuda_failure(nullptr, e, "cudaGetDevice", __LINE__);
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e != cudaSuccess) return cuda_failure(nullptr, e, "cudaDeviceGetAttribute", __LINE__);
+    if (sweep_smem_bytes(g) > optin)
+        return fail(SENSAI_EINVAL, "dictionary of K=%d atoms x P=%d pixels does not fit in shared memory", g.K, g.P);
+    if (sizeof(float) * (size_t)g.K * (((size_t)g.P + 31) & ~(size_t)31) > (size_t)optin)
+        return fail(SENSAI_EINVAL, "dictionary of K=%d atoms x P=%d pixels does not fit in shared memory", g.K, g.P);
+
+    sensai_ctx* ctx = new (std::nothrow) sensai_ctx();
+    if (!ctx) return fail(SENSAI_ENOMEM, "host allocation failed");
+    ctx->device = device;
+    ctx->g = g;
+    ctx->prm = p;
+    ctx->a_over_K = (p.a > 0 ? p.a : (double)p.K) / p.K;
+    ctx->b_scaled = (p.b > 0 ? p.b : (double)N / 8.0) * (p.K - 1) / p.K;
+
+    const cudaStream_t st0 = nullptr;
+    uint8_t* mask_dev = nullptr;
+    auto bail = [&](sensai_status status) {
+        if (mask_dev) cudaFree(mask_dev);
+        free_all(ctx);
+        delete ctx;
+        return status;
+    };
+#define CREATE_CUDA(call)                                                             \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) return bail(cuda_failure(nullptr, e_, #call, __LINE__)); \
+    } while (0)
+
+    const long long nmw = (nframe + 31) / 32;
+    CREATE_CUDA(dalloc(&mask_dev, (size_t)nframe));
+    CREATE_CUDA(dalloc(&ctx->mask_bits, (size_t)nmw));
+    CREATE_CUDA(dalloc(&ctx->imgoff, (size_t)P));
+    CREATE_CUDA(dalloc(&ctx->nobs, (size_t)N));
+    CREATE_CUDA(dalloc(&ctx->misc, 2));
+    CREATE_CUDA(cudaMemcpy(mask_dev, mask, (size_t)nframe, cudaMemcpyHostToDevice));
+    CREATE_CUDA(cudaMemset(ctx->misc, 0, 2 * sizeof(int)));
+    CREATE_CUDA(launch_geometry(g, mask_dev, ctx->mask_bits, ctx->imgoff, ctx->nobs, ctx->misc, st0));
+    ctx->launches += 3;
+    int misc[2] = {0, 0};
+    CREATE_CUDA(cudaMemcpy(misc, ctx->misc, sizeof(misc), cudaMemcpyDeviceToHost));
+    cudaFree(mask_dev);
+    mask_dev = nullptr;
+    ctx->maxobs = misc[0];
+    if (ctx->maxobs > 128) {
+        fail(SENSAI_EINVAL, "a patch observes %d pixels; at most 128 observed pixels per patch are supported",
+             ctx->maxobs);
+        return bail(SENSAI_EINVAL);
+    }
+    CREATE_CUDA(dalloc(&ctx->obs, (size_t)(ctx->maxobs > 0 ? ctx->maxobs : 1) * N));
+    CREATE_CUDA(dalloc(&ctx->Ibits, (size_t)P * g.NW));
+    CREATE_CUDA(dalloc(&ctx->Ipre, (size_t)P * g.NW));
+    CREATE_CUDA(dalloc(&ctx->Icnt, (size_t)P));
+    CREATE_CUDA(dalloc(&ctx->Rbase, (size_t)P + 1));
+    CREATE_CUDA(launch_slots(g, ctx->mask_bits, ctx->imgoff, ctx->obs, ctx->Ibits, ctx->Ipre, ctx->Icnt,
+                             ctx->Rbase, ctx->misc + 1, st0));
+    ctx->launches += 4;
+    int total = 0;
+    CREATE_CUDA(cudaMemcpy(&total, ctx->Rbase + P, sizeof(int), cudaMemcpyDeviceToHost));
+    CREATE_CUDA(cudaMemcpy(&ctx->max_slots, ctx->misc + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    ctx->n_observed = total;
+
+    CREATE_CUDA(dalloc(&ctx->x, (size_t)nframe));
+    CREATE_CUDA(dalloc(&ctx->out, (size_t)nframe));
+    CREATE_CUDA(dalloc(&ctx->D, (size_t)g.K * P));
+    CREATE_CUDA(dalloc(&ctx->W, (size_t)g.K * N));
+    CREATE_CUDA(dalloc(&ctx->Zb, (size_t)g.K * g.NW));
+    CREATE_CUDA(dalloc(&ctx->R, (size_t)total));
+    CREATE_CUDA(dalloc(&ctx->Y, (size_t)P * N));
+    CREATE_CUDA(dalloc(&ctx->pi, (size_t)g.K));
+    CREATE_CUDA(dalloc(&ctx->lpi, (size_t)g.K));
+    CREATE_CUDA(dalloc(&ctx->m, (size_t)g.K));
+    CREATE_CUDA(dalloc(&ctx->part_s2, (size_t)g.NW));
+    CREATE_CUDA(dalloc(&ctx->part_r2, (size_t)(g.NW > P ? g.NW : P)));
+    CREATE_CUDA(dalloc(&ctx->chunk_counter, 1));
+    CREATE_CUDA(dalloc(&ctx->sc, 1));
+    ctx->sweep_grid = sweep_grid_size(g, ctx->maxobs, device);
+    if (ctx->sweep_grid < 1) {
+        fail(SENSAI_ECUDA, "no launch configuration for the code sweep (max observed %d)", ctx->maxobs);
+        return bail(SENSAI_ECUDA);
+    }
+    if (reset_state(ctx, st0) != SENSAI_OK) return bail(SENSAI_ECUDA);
+    CREATE_CUDA(cudaDeviceSynchronize());
+#undef CREATE_CUDA
+    *out = ctx;
+    return SENSAI_OK;
+}
+
+void sensai_destroy(sensai_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    clear_timers(ctx);
+    free_all(ctx);
+    delete ctx;
+}
+
+sensai_status sensai_set_frame(sensai_ctx* ctx, const float* frame, void* stream)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    if (!frame) return fail(SENSAI_EINVAL, "null frame");
+    ctx->last_stream = (cudaStream_t)stream;
+    return copy_frame(ctx, frame, (cudaStream_t)stream);
+}
+
+sensai_status sensai_reset(sensai_ctx* ctx, void* stream)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    ctx->last_stream = (cudaStream_t)stream;
+    return reset_state(ctx, (cudaStream_t)stream);
+}
+
+sensai_status sensai_sweep_codes(sensai_ctx* ctx, void* stream)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    ctx->last_stream = (cudaStream_t)stream;
+    return run_sweep(ctx, (cudaStream_t)stream);
+}
+
+sensai_status sensai_draw_dictionary(sensai_ctx* ctx, void* stream)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    ctx->last_stream = (cudaStream_t)stream;
+    return run_dictionary(ctx, (cudaStream_t)stream);
+}
+
+sensai_status sensai_draw_hyper(sensai_ctx* ctx, void* stream)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    ctx->last_stream = (cudaStream_t)stream;
+    return run_hyper(ctx, (cudaStream_t)stream);
+}
+
+sensai_status sensai_learn(sensai_ctx* ctx, const float* frame, int32_t iters, void* stream)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    if (iters < 0) return fail(SENSAI_EINVAL, "iters must be >= 0");
+    const cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    if (frame) {
+        st = copy_frame(ctx, frame, s);
+        if (st != SENSAI_OK) return st;
+    }
+    if (!ctx->frame_set) return fail(SENSAI_ESTATE, "no frame: pass one or call sensai_set_frame");
+    for (int it = 0; it < iters; ++it) {
+        if ((st = run_sweep(ctx, s)) != SENSAI_OK) return st;
+        if ((st = run_dictionary(ctx, s)) != SENSAI_OK) return st;
+        if ((st = run_hyper(ctx, s)) != SENSAI_OK) return st;
+        ctx->t += 1;
+    }
+    return SENSAI_OK;
+}
+
+sensai_status sensai_inpaint(sensai_ctx* ctx, const float* frame, int32_t sweeps, float* out, void* stream)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    if (!frame) return fail(SENSAI_EINVAL, "null frame");
+    if (sweeps < 0) return fail(SENSAI_EINVAL, "sweeps must be >= 0");
+    const cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    if ((st = copy_frame(ctx, frame, s)) != SENSAI_OK) return st;
+    if ((st = clear_codes(ctx, s)) != SENSAI_OK) return st;
+    for (int it = 0; it < sweeps; ++it) {
+        if ((st = run_sweep(ctx, s)) != SENSAI_OK) return st;
+        if ((st = run_hyper(ctx, s)) != SENSAI_OK) return st;
+        ctx->t += 1;
+    }
+    if (!out) return SENSAI_OK;
+    const bool dev = is_device_pointer(out);
+    float* dst = dev ? out : ctx->out;
+    {
+        PhaseTimer timer(ctx, kPhaseRecon, s);
+        SENSAI_CUDA(ctx, launch_reconstruct(ctx->g, ctx->D, ctx->W, ctx->Zb, ctx->Y, dst, s));
+        timer.stop();
+        ctx->launches += 2;
+    }
+    if (!dev) return write_out(ctx, ctx->out, out, sizeof(float) * (size_t)ctx->g.nframe, s);
+    return SENSAI_OK;
+}
+
+sensai_status sensai_reconstruct(sensai_ctx* ctx, float* out, void* stream)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    if (!out) return fail(SENSAI_EINVAL, "null output");
+    const cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    const bool dev = is_device_pointer(out);
+    float* dst = dev ? out : ctx->out;
+    {
+        PhaseTimer timer(ctx, kPhaseRecon, s);
+        SENSAI_CUDA(ctx, launch_reconstruct(ctx->g, ctx->D, ctx->W, ctx->Zb, ctx->Y, dst, s));
+        timer.stop();
+        ctx->launches += 2;
+    }
+    if (!dev) return write_out(ctx, ctx->out, out, sizeof(float) * (size_t)ctx->g.nframe, s);
+    return SENSAI_OK;
+}
+
+sensai_status sensai_overlap_counts(sensai_ctx* ctx, int32_t* out, void* stream)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    if (!out) return fail(SENSAI_EINVAL, "null output");
+    const cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    const bool dev = is_device_pointer(out);
+    int* dst = dev ? out : (int*)ctx->out;
+    SENSAI_CUDA(ctx, launch_overlap_counts(ctx->g, dst, s));
+    ctx->launches += 1;
+    if (!dev) return write_out(ctx, ctx->out, out, sizeof(int) * (size_t)ctx->g.nframe, s);
+    return SENSAI_OK;
+}
+
+sensai_status sensai_get_dictionary(sensai_ctx* ctx, float* D)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    if (!D) return fail(SENSAI_EINVAL, "null dictionary");
+    SENSAI_CUDA(ctx, cudaDeviceSynchronize());
+    SENSAI_CUDA(ctx, cudaMemcpy(D, ctx->D, sizeof(float) * (size_t)ctx->g.K * ctx->g.P, cudaMemcpyDefault));
+    return SENSAI_OK;
+}
+
+sensai_status sensai_set_dictionary(sensai_ctx* ctx, const float* D)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    if (!D) return fail(SENSAI_EINVAL, "null dictionary");
+    SENSAI_CUDA(ctx, cudaDeviceSynchronize());
+    SENSAI_CUDA(ctx, cudaMemcpy(ctx->D, D, sizeof(float) * (size_t)ctx->g.K * ctx->g.P, cudaMemcpyDefault));
+    ctx->resid_valid = false;
+    return SENSAI_OK;
+}
+
+sensai_status sensai_get_state(sensai_ctx* ctx, sensai_state* state)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    if (!state) return fail(SENSAI_EINVAL, "null state");
+    const Geom& g = ctx->g;
+    SENSAI_CUDA(ctx, cudaDeviceSynchronize());
+    if (state->D) SENSAI_CUDA(ctx, cudaMemcpy(state->D, ctx->D, sizeof(float) * (size_t)g.K * g.P, cudaMemcpyDefault));
+    if (state->pi) SENSAI_CUDA(ctx, cudaMemcpy(state->pi, ctx->pi, sizeof(double) * g.K, cudaMemcpyDefault));
+    if (state->Z || state->S) {
+        uint8_t* z = nullptr;
+        float* sv = nullptr;
+        const size_t n = (size_t)g.N * g.K;
+        SENSAI_CUDA(ctx, dalloc(&z, n));
+        cudaError_t e = dalloc(&sv, n);
+        if (e != cudaSuccess) {
+            cudaFree(z);
+            return cuda_failure(ctx, e, "dalloc", __LINE__);
+        }
+        e = launch_export_codes(g, ctx->W, ctx->Zb, z, sv, nullptr);
+        if (e == cudaSuccess && state->Z) e = cudaMemcpy(state->Z, z, n, cudaMemcpyDefault);
+        if (e == cudaSuccess && state->S) e = cudaMemcpy(state->S, sv, n * sizeof(float), cudaMemcpyDefault);
+        cudaFree(z);
+        cudaFree(sv);
+        if (e != cudaSuccess) return cuda_failure(ctx, e, "export codes", __LINE__);
+    }
+    DevScalars sc;
+    SENSAI_CUDA(ctx, cudaMemcpy(&sc, ctx->sc, sizeof(sc), cudaMemcpyDeviceToHost));
+    state->gamma_s = sc.gamma_s;
+    state->gamma_eps = ctx->ge_set ? sc.gamma_eps : 0.0;
+    state->iter = ctx->t;
+    return SENSAI_OK;
+}
+
+sensai_status sensai_set_state(sensai_ctx* ctx, const sensai_state* state)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    if (!state) return fail(SENSAI_EINVAL, "null state");
+    if ((state->Z == nullptr) != (state->S == nullptr)) return fail(SENSAI_EINVAL, "Z and S must be set together");
+    if (!(state->gamma_s > 0)) return fail(SENSAI_EINVAL, "gamma_s must be > 0");
+    if (state->iter < 0) return fail(SENSAI_EINVAL, "iter must be >= 0");
+    if (state->pi)
+        for (int k = 0; k < ctx->g.K; ++k)
+            if (!(state->pi[k] > 0.0 && state->pi[k] < 1.0)) return fail(SENSAI_EINVAL, "pi[%d] must be in (0, 1)", k);
+    const Geom& g = ctx->g;
+    SENSAI_CUDA(ctx, cudaDeviceSynchronize());
+    if (state->D) SENSAI_CUDA(ctx, cudaMemcpy(ctx->D, state->D, sizeof(float) * (size_t)g.K * g.P, cudaMemcpyDefault));
+    if (state->pi) {
+        SENSAI_CUDA(ctx, cudaMemcpy(ctx->pi, state->pi, sizeof(double) * g.K, cudaMemcpyDefault));
+        SENSAI_CUDA(ctx, launch_logit(g.K, ctx->pi, ctx->lpi, nullptr));
+    }
+    if (state->Z) {
+        uint8_t* z = nullptr;
+        float* sv = nullptr;
+        const size_t n = (size_t)g.N * g.K;
+        SENSAI_CUDA(ctx, dalloc(&z, n));
+        cudaError_t e = dalloc(&sv, n);
+        if (e == cudaSuccess) e = cudaMemcpy(z, state->Z, n, cudaMemcpyDefault);
+        if (e == cudaSuccess) e = cudaMemcpy(sv, state->S, n * sizeof(float), cudaMemcpyDefault);
+        if (e == cudaSuccess) e = launch_import_codes(g, z, sv, ctx->W, ctx->Zb, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(z);
+        if (sv) cudaFree(sv);
+        if (e != cudaSuccess) return cuda_failure(ctx, e, "import codes", __LINE__);
+    }
+    DevScalars sc;
+    SENSAI_CUDA(ctx, cudaMemcpy(&sc, ctx->sc, sizeof(sc), cudaMemcpyDeviceToHost));
+    sc.gamma_s = state->gamma_s;
+    if (state->gamma_eps > 0) {
+        sc.gamma_eps = state->gamma_eps;
+        sc.ge_set = 1;
+        ctx->ge_set = true;
+    }
+    SENSAI_CUDA(ctx, cudaMemcpy(ctx->sc, &sc, sizeof(sc), cudaMemcpyHostToDevice));
+    ctx->t = state->iter;
+    ctx->codes_valid = false;
+    ctx->resid_valid = false;
+    return SENSAI_OK;
+}
+
+sensai_status sensai_get_stats(sensai_ctx* ctx, sensai_stats* stats)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    if (!stats) return fail(SENSAI_EINVAL, "null stats");
+    SENSAI_CUDA(ctx, cudaStreamSynchronize(ctx->last_stream));
+    DevScalars sc;
+    SENSAI_CUDA(ctx, cudaMemcpy(&sc, ctx->sc, sizeof(sc), cudaMemcpyDeviceToHost));
+    stats->iter = ctx->t;
+    stats->n_patches = ctx->g.N;
+    stats->patch_size = ctx->g.P;
+    stats->n_observed = ctx->n_observed;
+    stats->n_active = sc.n_active;
+    stats->max_observed = ctx->maxobs;
+    stats->K = ctx->g.K;
+    stats->sum_s2 = sc.sum_s2;
+    stats->sum_r2 = sc.sum_r2;
+    stats->gamma_s = sc.gamma_s;
+    stats->gamma_eps = ctx->ge_set ? sc.gamma_eps : 0.0;
+    stats->kernel_launches = ctx->launches;
+    stats->changed_updates = (int64_t)sc.chg_n;
+    stats->changed_observed = (int64_t)sc.chg_obs;
+    stats->active_draws = (int64_t)sc.act_n;
+    return SENSAI_OK;
+}
+
+sensai_status sensai_profile(sensai_ctx* ctx, int32_t enable)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    if (enable) {
+        SENSAI_CUDA(ctx, cudaDeviceSynchronize());
+        clear_timers(ctx);
+        const unsigned long long zero[3] = {0, 0, 0};
+        SENSAI_CUDA(ctx, cudaMemcpy(&ctx->sc->chg_n, zero, sizeof(zero), cudaMemcpyHostToDevice));
+    }
+    ctx->profiling = enable != 0;
+    return SENSAI_OK;
+}
+
+sensai_status sensai_profile_read(sensai_ctx* ctx, double* ms, int64_t* counts)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    if (!ms || !counts) return fail(SENSAI_EINVAL, "null output");
+    SENSAI_CUDA(ctx, cudaDeviceSynchronize());
+    for (int ph = 0; ph < 4; ++ph) {
+        double total = 0.0;
+        for (auto& pr : ctx->timed[ph]) {
+            float t = 0.0f;
+            SENSAI_CUDA(ctx, cudaEventElapsedTime(&t, pr.first, pr.second));
+            total += t;
+        }
+        ms[ph] = total;
+        counts[ph] = (int64_t)ctx->timed[ph].size();
+    }
+    return SENSAI_OK;
+}
+
+}  // extern "C"

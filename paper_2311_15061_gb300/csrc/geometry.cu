@@ -1,0 +1,290 @@
+// geometry.cu -- patch geometry on the device (the N-D patch extraction of
+// the "N-Dimensional Inpainting" section: patch shape B and stride S in every
+// dimension of a frame of shape M), built once per sampling mask.
+//
+//  * mask bits: one bit per frame pixel;
+//  * imgoff[p]: frame offset of within-patch pixel p (row-major over B);
+//  * nobs[i], obs[j][i]: the observed within-patch pixels of patch i, in
+//    increasing p, padded layout [maxobs][N] so a warp reads them coalesced;
+//  * Ibits[p][w]: bit b of word w says patch 32w+b observes pixel p;
+//    Ipre[p][w]: popcount of Ibits[p][0..w) -- the rank of a patch among the
+//    patches observing p, i.e. its residual slot for the dictionary chains;
+//  * Rbase[p]: start of pixel p's slots (exclusive scan of the counts);
+//  * overlap counts c_q: per dimension floor(min(y, last)/S) -
+//    ceil(max(0, y - B + 1)/S) + 1, multiplied over dimensions.
+#include "internal.cuh"
+
+namespace sensai {
+
+__global__ void pack_mask_kernel(long long nframe, const uint8_t* bytes, uint32_t* bits)
+{
+    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nw = (nframe + 31) / 32;
+    if (w >= nw) return;
+    uint32_t v = 0;
+    for (int b = 0; b < 32; ++b) {
+        const long long u = w * 32 + b;
+        if (u < nframe && bytes[u]) v |= 1u << b;
+    }
+    bits[w] = v;
+}
+
+__global__ void pixel_offsets_kernel(Geom g, int* imgoff)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.P) return;
+    int rem = p;
+    long long off = 0;
+    for (int d = g.ndim - 1; d >= 0; --d) {
+        off += (long long)(rem % g.B[d]) * g.fs[d];
+        rem /= g.B[d];
+    }
+    imgoff[p] = (int)off;
+}
+
+__device__ __forceinline__ bool mask_at(const uint32_t* bits, long long u)
+{
+    return (bits[u >> 5] >> (u & 31)) & 1u;
+}
+
+__global__ void count_obs_kernel(Geom g, const uint32_t* mbits, const int* imgoff, uint16_t* nobs, int* maxobs)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    const long long org = patch_origin(g, i);
+    int c = 0;
+    for (int p = 0; p < g.P; ++p) c += mask_at(mbits, org + imgoff[p]);
+    nobs[i] = (uint16_t)c;
+    atomicMax(maxobs, c);
+}
+
+__global__ void fill_obs_kernel(Geom g, const uint32_t* mbits, const int* imgoff, uint16_t* obs)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    const long long org = patch_origin(g, i);
+    int c = 0;
+    for (int p = 0; p < g.P; ++p)
+        if (mask_at(mbits, org + imgoff[p])) obs[(long long)(c++) * g.N + i] = (uint16_t)p;
+}
+
+// Grid: (ceil(NW / blockDim), P).
+__global__ void ibits_kernel(Geom g, const uint32_t* mbits, const int* imgoff, uint32_t* Ibits)
+{
+    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.y;
+    if (w >= g.NW) return;
+    uint32_t v = 0;
+    for (int b = 0; b < 32; ++b) {
+        const long long i = w * 32 + b;
+        if (i < g.N && mask_at(mbits, patch_origin(g, i) + imgoff[p])) v |= 1u << b;
+    }
+    Ibits[(long long)p * g.NW + w] = v;
+}
+
+// One CTA per pixel p: exclusive scan of popcounts over the words.
+__global__ void __launch_bounds__(1024) iprefix_kernel(Geom g, const uint32_t* Ibits, uint32_t* Ipre, int* Icnt)
+{
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    const int p = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long base = 0; base < g.NW; base += blockDim.x) {
+        const long long w = base + threadIdx.x;
+        const int v = w < g.NW ? __popc(Ibits[(long long)p * g.NW + w]) : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int n = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += n;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = blockDim.x >> 5;
+            int t = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int n = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += n;
+            }
+            if (lane < nw) warp_tot[lane] = t;  // inclusive over warps
+        }
+        __syncthreads();
+        const int before = carry + (warp > 0 ? warp_tot[warp - 1] : 0) + incl - v;
+        if (w < g.NW) Ipre[(long long)p * g.NW + w] = (uint32_t)before;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_tot[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) Icnt[p] = carry;
+}
+
+// Single thread: Rbase = exclusive scan of Icnt, Rbase[P] = total; largest count.
+__global__ void rbase_kernel(int P, const int* Icnt, int* Rbase, int* max_slots)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    long long acc = 0;
+    int mx = 0;
+    for (int p = 0; p < P; ++p) {
+        Rbase[p] = (int)acc;
+        acc += Icnt[p];
+        mx = Icnt[p] > mx ? Icnt[p] : mx;
+    }
+    Rbase[P] = (int)acc;
+    *max_slots = mx;
+}
+
+__device__ __forceinline__ void cover_range(const Geom& g, int d, long long y, long long* first, long long* last)
+{
+    const long long lastp = (g.G[d] - 1) * g.S[d];
+    long long lo = y - g.B[d] + 1;
+    if (lo < 0) lo = 0;
+    const long long hi = y < lastp ? y : lastp;
+    *first = (lo + g.S[d] - 1) / g.S[d];
+    *last = hi / g.S[d];
+}
+
+__global__ void overlap_counts_kernel(Geom g, int* counts)
+{
+    const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= g.nframe) return;
+    long long rem = u, c = 1;
+    for (int d = g.ndim - 1; d >= 0; --d) {
+        const long long y = rem % g.M[d];
+        rem /= g.M[d];
+        long long f, l;
+        cover_range(g, d, y, &f, &l);
+        c *= (l >= f) ? (l - f + 1) : 0;
+    }
+    counts[u] = (int)c;
+}
+
+// Overlap-add, gather form: pixel q averages Y[p][i] over the patches i that
+// cover it, with p = q - origin(i).  Y holds every patch's reconstruction.
+__global__ void ola_gather_kernel(Geom g, const float* Y, float* out)
+{
+    const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= g.nframe) return;
+    long long y[kMaxDim], f[kMaxDim], l[kMaxDim], cur[kMaxDim];
+    long long rem = u;
+    for (int d = g.ndim - 1; d >= 0; --d) {
+        y[d] = rem % g.M[d];
+        rem /= g.M[d];
+        cover_range(g, d, y[d], &f[d], &l[d]);
+        if (l[d] < f[d]) {
+            out[u] = 0.0f;
+            return;
+        }
+        cur[d] = f[d];
+    }
+    float acc = 0.0f;
+    int count = 0;
+    for (;;) {
+        long long i = 0;
+        int p = 0;
+        for (int d = 0; d < g.ndim; ++d) {
+            i = i * g.G[d] + cur[d];
+            p = p * g.B[d] + (int)(y[d] - cur[d] * g.S[d]);
+        }
+        acc += Y[(long long)p * g.N + i];
+        ++count;
+        int d = g.ndim - 1;
+        while (d >= 0 && ++cur[d] > l[d]) {
+            cur[d] = f[d];
+            --d;
+        }
+        if (d < 0) break;
+    }
+    out[u] = acc / (float)count;
+}
+
+// Per-patch reconstruction Y[p][i] = sum_k z_ik w_ik d_kp.  One thread per
+// patch, 32 pixels at a time; the dictionary chunk is read with warp-uniform
+// (broadcast) shared-memory loads.
+__global__ void __launch_bounds__(256) patch_recon_kernel(Geom g, const float* D, const float* W,
+                                                          const uint32_t* Zb, float* Y)
+{
+    extern __shared__ float Ds[];  // K x ldP, ldP = P rounded up to 32, zero padded
+    const int K = g.K, P = g.P;
+    const int ldP = (P + 31) & ~31;
+    for (int idx = threadIdx.x; idx < K * ldP; idx += blockDim.x) {
+        const int k = idx / ldP, p = idx - k * ldP;
+        Ds[idx] = p < P ? D[(long long)k * P + p] : 0.0f;
+    }
+    __syncthreads();
+    const long long chunk = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (chunk >= g.NW) return;
+    const long long i = chunk * 32 + lane;
+    for (int p0 = 0; p0 < P; p0 += 32) {
+        float acc[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) acc[q] = 0.0f;
+        for (int k = 0; k < K; ++k) {
+            const uint32_t zw = Zb[(long long)k * g.NW + chunk];
+            if ((zw >> lane) & 1u) {
+                const float w = W[(long long)k * g.N + i];
+                const float* dk = Ds + k * ldP + p0;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) acc[q] = fmaf(dk[q], w, acc[q]);
+            }
+        }
+        if (i < g.N) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                if (p0 + q < P) Y[(long long)(p0 + q) * g.N + i] = acc[q];
+        }
+    }
+}
+
+}  // namespace sensai
+
+namespace sensai {
+
+static inline unsigned int blocks_for(long long n, int threads)
+{
+    return (unsigned int)((n + threads - 1) / threads);
+}
+
+cudaError_t launch_geometry(const Geom& g, const uint8_t* mask_bytes, uint32_t* mask_bits, int* imgoff,
+                            uint16_t* nobs, int* maxobs, cudaStream_t s)
+{
+    const long long nmw = (g.nframe + 31) / 32;
+    pack_mask_kernel<<<blocks_for(nmw, 256), 256, 0, s>>>(g.nframe, mask_bytes, mask_bits);
+    pixel_offsets_kernel<<<blocks_for(g.P, 256), 256, 0, s>>>(g, imgoff);
+    count_obs_kernel<<<blocks_for(g.N, 256), 256, 0, s>>>(g, mask_bits, imgoff, nobs, maxobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slots(const Geom& g, const uint32_t* mask_bits, const int* imgoff, uint16_t* obs,
+                         uint32_t* Ibits, uint32_t* Ipre, int* Icnt, int* Rbase, int* max_slots, cudaStream_t s)
+{
+    fill_obs_kernel<<<blocks_for(g.N, 256), 256, 0, s>>>(g, mask_bits, imgoff, obs);
+    ibits_kernel<<<dim3(blocks_for(g.NW, 256), g.P), 256, 0, s>>>(g, mask_bits, imgoff, Ibits);
+    iprefix_kernel<<<g.P, 1024, 0, s>>>(g, Ibits, Ipre, Icnt);
+    rbase_kernel<<<1, 32, 0, s>>>(g.P, Icnt, Rbase, max_slots);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_overlap_counts(const Geom& g, int* counts, cudaStream_t s)
+{
+    overlap_counts_kernel<<<blocks_for(g.nframe, 256), 256, 0, s>>>(g, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reconstruct(const Geom& g, const float* D, const float* W, const uint32_t* Zb, float* Y,
+                               float* out, cudaStream_t s)
+{
+    const int ldP = (g.P + 31) & ~31;
+    const int smem = (int)(sizeof(float) * (size_t)g.K * ldP);
+    cudaError_t e = cudaFuncSetAttribute((void*)patch_recon_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    patch_recon_kernel<<<blocks_for(g.NW, 8), 256, smem, s>>>(g, D, W, Zb, Y);
+    ola_gather_kernel<<<blocks_for(g.nframe, 256), 256, 0, s>>>(g, Y, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sensai

@@ -1,0 +1,275 @@
+// hyper.cu -- conjugate draws of pi_k, gamma_s and gamma_eps, the initial
+// state, and the statistics passes behind them.
+//
+// From the model the BPFA section cites (Beta-Bernoulli and Gamma-Gaussian
+// conjugacy), given the current codes, weights and residual:
+//   pi_k      ~ Beta(a/K + m_k, b(K-1)/K + N - m_k),    m_k = sum_i z_ik
+//   gamma_s   ~ Gamma(c + 1/2 sum_ik z_ik, d + 1/2 sum_{z_ik=1} s_ik^2)
+//   gamma_eps ~ Gamma(e + 1/2 sum_i |Omega_i|, f + 1/2 sum_i ||r_i||^2)
+// (shape, rate).  The global sums are FP64 and reduced in a fixed order from
+// per-chunk (or per-pixel) partials, so the draws are deterministic.
+#include "internal.cuh"
+
+namespace sensai {
+
+constexpr int kHyperThreads = 1024;
+
+// Fixed-order sum of n partials: thread t adds a contiguous range, then a
+// block tree.  Result in thread 0.
+__device__ double sum_partials(const double* v, int n, double* red)
+{
+    const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int lo = threadIdx.x * per;
+    const int hi = min(n, lo + per);
+    double acc = 0.0;
+    for (int j = lo; j < hi; ++j) acc += v[j];
+    return block_sum(acc, red);
+}
+
+__global__ void __launch_bounds__(kHyperThreads) hyper_kernel(const HyperArgs a)
+{
+    __shared__ double red[kHyperThreads / 32];
+    const int K = a.g.K;
+    const double s2 = sum_partials(a.part_s2, a.n_s2, red);
+    const double r2 = sum_partials(a.part_r2, a.n_r2, red);
+    double mk = 0.0;
+    if ((int)threadIdx.x < K) {
+        mk = (double)a.m[threadIdx.x];
+        const double alpha = a.a_over_K + mk;
+        const double beta = a.b_scaled + (double)a.g.N - mk;
+        const double pi = beta_draw(alpha, beta, a.seed, threadIdx.x, a.t);
+        a.pi[threadIdx.x] = pi;
+        a.lpi[threadIdx.x] = (float)(log(pi) - log1p(-pi));
+    }
+    const double mtot = block_sum(mk, red);
+    if (threadIdx.x == 0) {
+        const double gs = gamma_draw(a.c + 0.5 * mtot, a.seed, 0, 0, a.t, kTagGs) / (a.d + 0.5 * s2);
+        const double ge = gamma_draw(a.e + 0.5 * (double)a.n_observed, a.seed, 0, 0, a.t, kTagGe)
+                        / (a.f + 0.5 * r2);
+        a.sc->gamma_s = gs;
+        a.sc->gamma_eps = ge;
+        a.sc->sum_s2 = s2;
+        a.sc->sum_r2 = r2;
+        a.sc->n_active = (long long)mtot;
+    }
+}
+
+cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s)
+{
+    hyper_kernel<<<1, kHyperThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// d_kp ~ N(0, 1/P) from counter (p, k, 0, INIT).
+__global__ void init_dictionary_kernel(Geom g, float* D, unsigned long long seed)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)g.K * g.P) return;
+    const int k = (int)(idx / g.P), p = (int)(idx % g.P);
+    const uint4 blk = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)k, 0u, kTagInit), seed_key(seed));
+    D[idx] = (float)(normal64(blk.x, blk.y) / sqrt((double)g.P));
+}
+
+__global__ void init_scalars_kernel(int K, double* pi, float* lpi, DevScalars* sc)
+{
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        pi[k] = 0.5;
+        lpi[k] = 0.0f;
+    }
+    if (threadIdx.x == 0) {
+        sc->gamma_s = 1.0;
+        sc->gamma_eps = 0.0;
+        sc->sum_s2 = 0.0;
+        sc->sum_r2 = 0.0;
+        sc->n_active = 0;
+        sc->chg_n = 0;
+        sc->chg_obs = 0;
+        sc->act_n = 0;
+        sc->ge_set = 0;
+        sc->status = 0;
+    }
+}
+
+// gamma_eps = 1 / max(var(frame over sampled pixels), 1e-12), two passes.
+__global__ void __launch_bounds__(kHyperThreads) init_gamma_eps_kernel(long long nframe, const float* x,
+                                                                       const uint32_t* mbits, DevScalars* sc)
+{
+    __shared__ double red[kHyperThreads / 32];
+    __shared__ double s_mean;
+    double sum = 0.0, cnt = 0.0;
+    for (long long u = threadIdx.x; u < nframe; u += blockDim.x)
+        if ((mbits[u >> 5] >> (u & 31)) & 1u) {
+            sum += x[u];
+            cnt += 1.0;
+        }
+    sum = block_sum(sum, red);
+    cnt = block_sum(cnt, red);
+    if (threadIdx.x == 0) s_mean = cnt > 0.0 ? sum / cnt : 0.0;
+    __syncthreads();
+    const double mean = s_mean;
+    double ss = 0.0;
+    for (long long u = threadIdx.x; u < nframe; u += blockDim.x)
+        if ((mbits[u >> 5] >> (u & 31)) & 1u) {
+            const double dv = (double)x[u] - mean;
+            ss += dv * dv;
+        }
+    ss = block_sum(ss, red);
+    if (threadIdx.x == 0) {
+        double var = cnt > 0.0 ? ss / cnt : 1.0;
+        if (var < 1e-12) var = 1e-12;
+        sc->gamma_eps = 1.0 / var;
+        sc->ge_set = 1;
+    }
+}
+
+// Statistics of an arbitrary state (after set_state / set_dictionary): active
+// counts per atom and per-chunk sum of s^2.
+__global__ void code_stats_kernel(Geom g, const float* W, const uint32_t* Zb, int* m, double* part_s2)
+{
+    const long long chunk = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (chunk >= g.NW) return;
+    const long long i = chunk * 32 + lane;
+    double s2 = 0.0;
+    for (int k = 0; k < g.K; ++k) {
+        const uint32_t zw = Zb[(long long)k * g.NW + chunk];
+        if (lane == 0 && zw) atomicAdd(&m[k], __popc(zw));
+        if ((zw >> lane) & 1u) {
+            const double w = W[(long long)k * g.N + i];
+            s2 += w * w;
+        }
+    }
+    s2 = warp_sum(s2);
+    if (lane == 0) part_s2[chunk] = s2;
+}
+
+// Residual of an arbitrary state, written to the per-pixel slots, with the
+// per-chunk squared norm.
+__global__ void residual_kernel(Geom g, const float* x, const uint16_t* obs, const uint16_t* nobs,
+                                const int* imgoff, const float* D, const float* W, const uint32_t* Zb,
+                                const uint32_t* Ibits, const uint32_t* Ipre, const int* Rbase, float* R,
+                                double* part_r2)
+{
+    const long long chunk = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (chunk >= g.NW) return;
+    const long long i = chunk * 32 + lane;
+    double r2 = 0.0;
+    if (i < g.N) {
+        const long long org = patch_origin(g, i);
+        const int no = nobs[i];
+        for (int j = 0; j < no; ++j) {
+            const int p = obs[(long long)j * g.N + i];
+            float r = x[org + imgoff[p]];
+            for (int k = 0; k < g.K; ++k)
+                if ((Zb[(long long)k * g.NW + chunk] >> lane) & 1u)
+                    r = fmaf(-D[(long long)k * g.P + p], W[(long long)k * g.N + i], r);
+            const long long w = (long long)p * g.NW + chunk;
+            const int slot = Rbase[p] + (int)Ipre[w] + __popc(Ibits[w] & ((1u << lane) - 1u));
+            R[slot] = r;
+            r2 += (double)r * r;
+        }
+    }
+    r2 = warp_sum(r2);
+    if (lane == 0) part_r2[chunk] = r2;
+}
+
+}  // namespace sensai
+
+namespace sensai {
+
+static inline unsigned int blocks_for(long long n, int threads)
+{
+    return (unsigned int)((n + threads - 1) / threads);
+}
+
+cudaError_t launch_init_state(const Geom& g, float* D, double* pi, float* lpi, DevScalars* sc,
+                              unsigned long long seed, cudaStream_t s)
+{
+    init_dictionary_kernel<<<blocks_for((long long)g.K * g.P, 256), 256, 0, s>>>(g, D, seed);
+    init_scalars_kernel<<<1, 256, 0, s>>>(g.K, pi, lpi, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_gamma_eps(const Geom& g, const float* x, const uint32_t* mbits, DevScalars* sc,
+                                  cudaStream_t s)
+{
+    init_gamma_eps_kernel<<<1, kHyperThreads, 0, s>>>(g.nframe, x, mbits, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_code_stats(const Geom& g, const float* W, const uint32_t* Zb, int* m, double* part_s2,
+                              cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(m, 0, sizeof(int) * g.K, s);
+    if (e != cudaSuccess) return e;
+    code_stats_kernel<<<blocks_for(g.NW, 8), 256, 0, s>>>(g, W, Zb, m, part_s2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const Geom& g, const float* x, const uint16_t* obs, const uint16_t* nobs,
+                            const int* imgoff, const float* D, const float* W, const uint32_t* Zb,
+                            const uint32_t* Ibits, const uint32_t* Ipre, const int* Rbase, float* R,
+                            double* part_r2, cudaStream_t s)
+{
+    residual_kernel<<<blocks_for(g.NW, 8), 256, 0, s>>>(g, x, obs, nobs, imgoff, D, W, Zb, Ibits, Ipre, Rbase,
+                                                        R, part_r2);
+    return cudaGetLastError();
+}
+
+// Patch-major (Z bytes, S floats) <-> device layout (Zb bits [K][NW], W [K][N]).
+__global__ void export_codes_kernel(Geom g, const float* W, const uint32_t* Zb, uint8_t* Z, float* S)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.N * g.K) return;
+    const long long i = idx / g.K;
+    const int k = (int)(idx % g.K);
+    const bool z = (Zb[(long long)k * g.NW + (i >> 5)] >> (i & 31)) & 1u;
+    Z[idx] = z ? 1 : 0;
+    S[idx] = z ? W[(long long)k * g.N + i] : 0.0f;
+}
+
+// One thread per (atom, 32-patch word).
+__global__ void import_codes_kernel(Geom g, const uint8_t* Z, const float* S, float* W, uint32_t* Zb)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)g.K * g.NW) return;
+    const int k = (int)(idx / g.NW);
+    const long long w = idx % g.NW;
+    uint32_t bits = 0;
+    for (int b = 0; b < 32; ++b) {
+        const long long i = w * 32 + b;
+        if (i >= g.N) break;
+        const bool z = Z[i * g.K + k] != 0;
+        if (z) bits |= 1u << b;
+        W[(long long)k * g.N + i] = z ? S[i * g.K + k] : 0.0f;
+    }
+    Zb[idx] = bits;
+}
+
+__global__ void logit_kernel(int K, const double* pi, float* lpi)
+{
+    for (int k = threadIdx.x; k < K; k += blockDim.x) lpi[k] = (float)(log(pi[k]) - log1p(-pi[k]));
+}
+
+cudaError_t launch_export_codes(const Geom& g, const float* W, const uint32_t* Zb, uint8_t* Z, float* S,
+                                cudaStream_t s)
+{
+    export_codes_kernel<<<blocks_for(g.N * g.K, 256), 256, 0, s>>>(g, W, Zb, Z, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import_codes(const Geom& g, const uint8_t* Z, const float* S, float* W, uint32_t* Zb,
+                                cudaStream_t s)
+{
+    import_codes_kernel<<<blocks_for((long long)g.K * g.NW, 256), 256, 0, s>>>(g, Z, S, W, Zb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_logit(int K, const double* pi, float* lpi, cudaStream_t s)
+{
+    logit_kernel<<<1, 256, 0, s>>>(K, pi, lpi);
+    return cudaGetLastError();
+}
+
+}  // namespace sensai

@@ -1,0 +1,264 @@
+// internal.cuh -- device-side building blocks shared by the sensai kernels.
+//
+// Random numbers follow the library's published counter convention (see
+// include/sensai.h): Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) keyed by
+// the 64-bit seed, counter (index0, index1, t, tag | attempt << 8), uniforms
+// (x + 1) 2^-32, Box-Muller normals, Marsaglia-Tsang Gamma (ACM TOMS 2000)
+// with the U^(1/alpha) boost below shape 1, Beta as a ratio of Gammas.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sensai.h"
+
+namespace sensai {
+
+enum : uint32_t {
+    kTagInit = 1,   // dictionary initialisation, counter (p, k, 0)
+    kTagCodes = 2,  // sparse-code draw, counter (i, k, t)
+    kTagDict = 3,   // dictionary draw, counter (p, k, t)
+    kTagPiA = 4,    // Beta draw of pi_k: numerator Gamma, counter (k, 0, t)
+    kTagPiB = 5,    // Beta draw of pi_k: denominator Gamma
+    kTagGs = 6,     // gamma_s, counter (0, 0, t)
+    kTagGe = 7      // gamma_eps, counter (0, 0, t)
+};
+
+constexpr int kMaxDim = 4;
+constexpr int kGammaAttempts = 64;
+
+// Patch geometry, passed by value to kernels.
+struct Geom {
+    int ndim;
+    int P;                 // pixels per patch
+    int K;                 // atoms
+    int NW;                // 32-patch words: ceil(N / 32)
+    long long N;           // patches
+    long long nframe;      // pixels per frame
+    long long M[kMaxDim];  // frame shape
+    long long G[kMaxDim];  // patch-start grid shape
+    long long fs[kMaxDim]; // frame strides (row-major)
+    int B[kMaxDim];
+    int S[kMaxDim];
+};
+
+// Scalars that live on the device between phases.
+struct DevScalars {
+    double gamma_s;
+    double gamma_eps;
+    double sum_s2;     // last code sweep: sum of s^2 over active entries
+    double sum_r2;     // last residual pass: sum of squared residuals
+    long long n_active;
+    unsigned long long chg_n;    // code updates whose weight changed
+    unsigned long long chg_obs;  // sum of |Omega_i| over those updates
+    unsigned long long act_n;    // code draws with z = 1
+    int ge_set;        // gamma_eps initialised from a frame
+    int status;        // sticky error word written by kernels (0 = ok)
+};
+
+// Frame offset of patch i's first pixel.
+__host__ __device__ inline long long patch_origin(const Geom& g, long long i)
+{
+    long long off = 0;
+    for (int d = g.ndim - 1; d >= 0; --d) {
+        long long id = i % g.G[d];
+        i /= g.G[d];
+        off += id * g.S[d] * g.fs[d];
+    }
+    return off;
+}
+
+// ------------------------------------------------------------------- RNG --
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint2 seed_key(unsigned long long seed)
+{
+    return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+__device__ __forceinline__ double uniform64(uint32_t x)
+{
+    return ((double)x + 1.0) * (1.0 / 4294967296.0);
+}
+
+// Box-Muller in FP64: sqrt(-2 ln u1) cos(2 pi u2).
+__device__ __forceinline__ double normal64(uint32_t x0, uint32_t x1)
+{
+    return sqrt(-2.0 * log(uniform64(x0))) * cospi(2.0 * uniform64(x1));
+}
+
+// Box-Muller in FP32 (used for the code draws).
+__device__ __forceinline__ float normal32(uint32_t x0, uint32_t x1)
+{
+    const float scale = 2.3283064365386963e-10f;  // 2^-32
+    const float u1 = fmaf((float)x0, scale, scale);
+    const float u2 = fmaf((float)x1, scale, scale);
+    return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+// Marsaglia-Tsang for shape >= 1; attempt a uses block (c0, c1, t, tag | a << 8):
+// words 0-1 -> the normal, word 2 -> the acceptance uniform.
+__device__ inline double gamma_shape_ge1(double shape, unsigned long long seed, uint32_t c0,
+                                         uint32_t c1, uint32_t t, uint32_t tag)
+{
+    const double dd = shape - 1.0 / 3.0;
+    const double cc = 1.0 / sqrt(9.0 * dd);
+    const uint2 key = seed_key(seed);
+    for (uint32_t a = 0; a < (uint32_t)kGammaAttempts; ++a) {
+        const uint4 blk = philox4x32_10(make_uint4(c0, c1, t, tag | (a << 8)), key);
+        const double xn = normal64(blk.x, blk.y);
+        double v = 1.0 + cc * xn;
+        if (v <= 0.0) continue;
+        v = v * v * v;
+        const double u = uniform64(blk.z);
+        const double x2 = xn * xn;
+        if (u < 1.0 - 0.0331 * x2 * x2) return dd * v;
+        if (log(u) < 0.5 * x2 + dd * (1.0 - v + log(v))) return dd * v;
+    }
+    return dd;
+}
+
+// Gamma(shape, 1); below shape 1: Gamma(shape + 1) U^(1/shape), U = word 3 of
+// the attempt-0 block.
+__device__ inline double gamma_draw(double shape, unsigned long long seed, uint32_t c0, uint32_t c1,
+                                    uint32_t t, uint32_t tag)
+{
+    if (shape >= 1.0) return gamma_shape_ge1(shape, seed, c0, c1, t, tag);
+    const double g = gamma_shape_ge1(shape + 1.0, seed, c0, c1, t, tag);
+    const uint4 blk = philox4x32_10(make_uint4(c0, c1, t, tag), seed_key(seed));
+    return g * pow(uniform64(blk.w), 1.0 / shape);
+}
+
+__device__ inline double beta_draw(double alpha, double beta, unsigned long long seed, uint32_t k, uint32_t t)
+{
+    const double g1 = gamma_draw(alpha, seed, k, 0, t, kTagPiA);
+    const double g2 = gamma_draw(beta, seed, k, 0, t, kTagPiB);
+    return g1 / (g1 + g2);
+}
+
+// ------------------------------------------------------------ reductions --
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Fixed-order block sum (deterministic); result valid in thread 0.
+// `scratch` must hold blockDim.x / 32 doubles.
+__device__ inline double block_sum(double v, double* scratch)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        r = (lane < (int)(blockDim.x >> 5)) ? scratch[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+// ------------------------------------------------------ kernel arguments --
+
+struct SweepArgs {
+    Geom g;
+    const float* x;            // frame
+    const uint16_t* obs;       // [maxobs][N] within-patch index of each observed pixel
+    const uint16_t* nobs;      // [N] observed pixels per patch
+    const int* imgoff;         // [P] frame offset of within-patch pixel p
+    const float* D;            // [K][P]
+    float* W;                  // [K][N] weights (0 where inactive)
+    uint32_t* Zb;              // [K][NW] activity bits
+    const float* lpi;          // [K] logit(pi_k)
+    const DevScalars* sc;
+    const uint32_t* Ibits;     // [P][NW] bit i: patch i observes pixel p
+    const uint32_t* Ipre;      // [P][NW] exclusive popcount prefix of Ibits
+    const int* Rbase;          // [P] start of pixel p's residual slots
+    float* R;                  // residual, slot Rbase[p] + rank of i among patches observing p
+    int* m;                    // [K] active count per atom (accumulated)
+    double* part_s2;           // [NW] per 32-patch chunk
+    double* part_r2;           // [NW] per 32-patch chunk
+    unsigned int* chunk_counter;  // work counter, zeroed before each launch
+    DevScalars* sc_out;           // change counters (same object as sc)
+    unsigned long long seed;
+    uint32_t t;
+};
+
+struct DictArgs {
+    Geom g;
+    float* D;                  // [K][P]
+    const float* W;            // [K][N]
+    const uint32_t* Zb;        // [K][NW]
+    const uint32_t* Ibits;     // [P][NW]
+    const uint32_t* Ipre;      // [P][NW]
+    const int* Rbase;          // [P + 1]
+    float* R;
+    const DevScalars* sc;
+    double* part_r2;           // [P]
+    unsigned long long seed;
+    uint32_t t;
+};
+
+struct HyperArgs {
+    Geom g;
+    const int* m;              // [K]
+    const double* part_s2;
+    int n_s2;
+    const double* part_r2;
+    int n_r2;
+    long long n_observed;
+    double a_over_K, b_scaled, c, d, e, f;
+    double* pi;                // [K]
+    float* lpi;                // [K]
+    DevScalars* sc;
+    unsigned long long seed;
+    uint32_t t;
+};
+
+// Launchers (defined in the .cu files).
+cudaError_t launch_sweep(const SweepArgs& a, int maxobs, int grid, cudaStream_t s);
+int sweep_block_size();
+int sweep_smem_bytes(const Geom& g);
+int sweep_grid_size(const Geom& g, int maxobs, int device);
+cudaError_t launch_dict(const DictArgs& a, int max_slots, cudaStream_t s);
+cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);
+cudaError_t launch_geometry(const Geom& g, const uint8_t* mask_bytes, uint32_t* mask_bits, int* imgoff,
+                            uint16_t* nobs, int* maxobs, cudaStream_t s);
+cudaError_t launch_slots(const Geom& g, const uint32_t* mask_bits, const int* imgoff, uint16_t* obs,
+                         uint32_t* Ibits, uint32_t* Ipre, int* Icnt, int* Rbase, int* max_slots, cudaStream_t s);
+cudaError_t launch_overlap_counts(const Geom& g, int* counts, cudaStream_t s);
+cudaError_t launch_reconstruct(const Geom& g, const float* D, const float* W, const uint32_t* Zb, float* Y,
+                               float* out, cudaStream_t s);
+cudaError_t launch_init_state(const Geom& g, float* D, double* pi, float* lpi, DevScalars* sc,
+                              unsigned long long seed, cudaStream_t s);
+cudaError_t launch_init_gamma_eps(const Geom& g, const float* x, const uint32_t* mbits, DevScalars* sc,
+                                  cudaStream_t s);
+cudaError_t launch_code_stats(const Geom& g, const float* W, const uint32_t* Zb, int* m, double* part_s2,
+                              cudaStream_t s);
+cudaError_t launch_residual(const Geom& g, const float* x, const uint16_t* obs, const uint16_t* nobs,
+                            const int* imgoff, const float* D, const float* W, const uint32_t* Zb,
+                            const uint32_t* Ibits, const uint32_t* Ipre, const int* Rbase, float* R,
+                            double* part_r2, cudaStream_t s);
+cudaError_t launch_export_codes(const Geom& g, const float* W, const uint32_t* Zb, uint8_t* Z, float* S,
+                                cudaStream_t s);
+cudaError_t launch_import_codes(const Geom& g, const uint8_t* Z, const float* S, float* W, uint32_t* Zb,
+                                cudaStream_t s);
+cudaError_t launch_logit(int K, const double* pi, float* lpi, cudaStream_t s);
+
+}  // namespace sensai

@@ -1,0 +1,243 @@
+// sweep.cu -- the sparse-code sweep (patch extraction fused in).
+//
+// For every patch i (in parallel) and every atom k in order (the sparse-coding
+// step of the BPFA section), with r_i the residual of patch i on its observed
+// pixels Omega_i:
+//   n   = sum_{p in Omega_i} d_kp^2,   g = sum_{p in Omega_i} d_kp r_ip + w_ik n
+//   lam = gamma_s + gamma_eps n
+//   L   = logit(pi_k) + 1/2 ln(gamma_s / lam) + gamma_eps^2 g^2 / (2 lam)
+//   z_ik = [ x0 < floor(sigmoid(L) 2^32) ],  x = Philox(i, k, t, CODES)
+//   s_ik = gamma_eps g / lam + lam^-1/2 BoxMuller(x1, x2)   if z_ik = 1
+//   r_i -= d_k (w_new - w_old) on Omega_i
+// (z with s integrated out, then s | z = 1; inactive weights are not stored).
+//
+// GB300 mapping: one thread owns one patch; a warp owns 32 consecutive,
+// 32-aligned patches so the atom's activity bits of the warp form one 32-bit
+// word (ballot).  Warps pull 32-patch chunks from a global counter, so the
+// tail of the grid is a single chunk per warp.  The dictionary sits in shared
+// memory as [p][k] with an odd row pitch plus one zero row (p = P) that padded
+// observation slots point at, so the inner loops need no predicates.  The
+// residual of the patch lives in registers (MAXOBS slots, chosen per problem
+// from the largest |Omega_i|).  Patch extraction is fused: the observed
+// pixels are gathered from the frame and the residual rebuilt from the stored
+// weights at the start of each sweep.  At the end the residual is scattered
+// to the per-pixel slot layout the dictionary kernel consumes.
+#include "internal.cuh"
+
+namespace sensai {
+
+constexpr int kSweepThreads = 256;
+
+template <int MAXOBS>
+__global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_kernel(const SweepArgs a)
+{
+    extern __shared__ float smem[];
+    const int K = a.g.K, P = a.g.P;
+    const int ldK = K | 1;
+    const long long N = a.g.N;
+    const int NW = a.g.NW;
+    float* Ds = smem;                      // (P + 1) x ldK, row P is zero
+    float* lpi = Ds + (P + 1) * ldK;       // K
+    int* cnt = (int*)(lpi + K);            // K
+    __shared__ unsigned int chunk_slot[kSweepThreads / 32];
+
+    for (int idx = threadIdx.x; idx < (P + 1) * ldK; idx += blockDim.x) {
+        const int p = idx / ldK, k = idx - p * ldK;
+        Ds[idx] = (p < P && k < K) ? a.D[(long long)k * P + p] : 0.0f;
+    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        lpi[k] = a.lpi[k];
+        cnt[k] = 0;
+    }
+    __syncthreads();
+
+    const float gs = (float)a.sc->gamma_s;
+    const float ge = (float)a.sc->gamma_eps;
+    const float half_log_gs = 0.5f * logf(gs);
+    const float half_ge2 = 0.5f * ge * ge;
+    const uint2 key = seed_key(a.seed);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned int nchunks = (unsigned int)NW;
+    unsigned int chg_n = 0, chg_obs = 0, act_n = 0;
+
+    for (;;) {
+        if (lane == 0) chunk_slot[warp] = atomicAdd(a.chunk_counter, 1u);
+        __syncwarp();
+        const unsigned int chunk = chunk_slot[warp];
+        __syncwarp();
+        if (chunk >= nchunks) break;
+        const long long i = (long long)chunk * 32 + lane;
+        const bool valid = i < N;
+
+        const int nobs = valid ? (int)a.nobs[i] : 0;
+        const int wmax = __reduce_max_sync(0xffffffffu, nobs);
+        const long long org = valid ? patch_origin(a.g, i) : 0;
+
+        int offK[MAXOBS];
+        float r[MAXOBS];
+#pragma unroll
+        for (int j = 0; j < MAXOBS; ++j) {
+            int p = P;
+            float v = 0.0f;
+            if (j < nobs) {
+                p = a.obs[(long long)j * N + i];
+                v = a.x[org + a.imgoff[p]];
+            }
+            offK[j] = p * ldK;
+            r[j] = v;
+        }
+
+        // residual r = x - D w on the observed pixels, from the stored weights
+        for (int k = 0; k < K; ++k) {
+            const uint32_t zw = a.Zb[(long long)k * NW + chunk];
+            if ((zw >> lane) & 1u) {
+                const float w = a.W[(long long)k * N + i];
+                const float* dk = Ds + k;
+#pragma unroll
+                for (int j = 0; j < MAXOBS; ++j) {
+                    if (j >= wmax) break;
+                    r[j] = fmaf(-dk[offK[j]], w, r[j]);
+                }
+            }
+        }
+
+        float s2 = 0.0f;
+        for (int k = 0; k < K; ++k) {
+            const float* dk = Ds + k;
+            float n = 0.0f, h = 0.0f;
+#pragma unroll
+            for (int j = 0; j < MAXOBS; ++j) {
+                if (j >= wmax) break;
+                const float d = dk[offK[j]];
+                n = fmaf(d, d, n);
+                h = fmaf(d, r[j], h);
+            }
+            const uint32_t zw = a.Zb[(long long)k * NW + chunk];
+            const bool zold = (zw >> lane) & 1u;
+            const float w_old = zold ? a.W[(long long)k * N + i] : 0.0f;
+            const float g = fmaf(w_old, n, h);
+            const float lam = fmaf(ge, n, gs);
+            const float rlam = __frcp_rn(lam);
+            const float L = lpi[k] + half_log_gs - 0.5f * __logf(lam) + half_ge2 * g * g * rlam;
+            const float sig = __frcp_rn(1.0f + __expf(-L));
+            const unsigned long long thr = (unsigned long long)(sig * 4294967296.0f);
+            const uint4 blk = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)k, a.t, kTagCodes), key);
+            const bool z = valid && ((unsigned long long)blk.x < thr);
+            float w_new = 0.0f;
+            if (z) {
+                w_new = fmaf(normal32(blk.y, blk.z), sqrtf(rlam), ge * g * rlam);
+                s2 = fmaf(w_new, w_new, s2);
+                act_n += 1;
+            }
+            const float dw = w_new - w_old;
+            if (dw != 0.0f) {
+                chg_n += 1;
+                chg_obs += (unsigned int)nobs;
+#pragma unroll
+                for (int j = 0; j < MAXOBS; ++j) {
+                    if (j >= wmax) break;
+                    r[j] = fmaf(-dk[offK[j]], dw, r[j]);
+                }
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, z);
+            if (lane == 0) {
+                a.Zb[(long long)k * NW + chunk] = bal;
+                if (bal) atomicAdd(&cnt[k], __popc(bal));
+            }
+            if (z || zold) a.W[(long long)k * N + i] = w_new;
+        }
+
+        // scatter the residual to the per-pixel slots; squared norm
+        float r2 = 0.0f;
+#pragma unroll
+        for (int j = 0; j < MAXOBS; ++j) {
+            if (j >= wmax) break;
+            if (j < nobs) {
+                const int p = a.obs[(long long)j * N + i];
+                const long long w = (long long)p * NW + chunk;
+                const uint32_t ib = a.Ibits[w];
+                const int slot = a.Rbase[p] + (int)a.Ipre[w] + __popc(ib & ((1u << lane) - 1u));
+                a.R[slot] = r[j];
+                r2 = fmaf(r[j], r[j], r2);
+            }
+        }
+        double s2d = warp_sum((double)s2);
+        double r2d = warp_sum((double)r2);
+        if (lane == 0) {
+            a.part_s2[chunk] = s2d;
+            a.part_r2[chunk] = r2d;
+        }
+    }
+    unsigned long long cn = chg_n, co = chg_obs, ca = act_n;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cn += __shfl_down_sync(0xffffffffu, cn, o);
+        co += __shfl_down_sync(0xffffffffu, co, o);
+        ca += __shfl_down_sync(0xffffffffu, ca, o);
+    }
+    if (lane == 0 && (cn | ca)) {
+        atomicAdd(&a.sc_out->chg_n, cn);
+        atomicAdd(&a.sc_out->chg_obs, co);
+        atomicAdd(&a.sc_out->act_n, ca);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+        if (cnt[k]) atomicAdd(&a.m[k], cnt[k]);
+}
+
+int sweep_block_size() { return kSweepThreads; }
+
+int sweep_smem_bytes(const Geom& g)
+{
+    const int ldK = g.K | 1;
+    return (int)(sizeof(float) * ((size_t)(g.P + 1) * ldK + g.K) + sizeof(int) * g.K);
+}
+
+template <int MAXOBS>
+static void* kernel_ptr() { return (void*)sweep_kernel<MAXOBS>; }
+
+static void* select_kernel(int maxobs)
+{
+    if (maxobs <= 8) return kernel_ptr<8>();
+    if (maxobs <= 16) return kernel_ptr<16>();
+    if (maxobs <= 24) return kernel_ptr<24>();
+    if (maxobs <= 32) return kernel_ptr<32>();
+    if (maxobs <= 40) return kernel_ptr<40>();
+    if (maxobs <= 48) return kernel_ptr<48>();
+    if (maxobs <= 64) return kernel_ptr<64>();
+    if (maxobs <= 96) return kernel_ptr<96>();
+    if (maxobs <= 128) return kernel_ptr<128>();
+    return nullptr;
+}
+
+int sweep_grid_size(const Geom& g, int maxobs, int device)
+{
+    void* fn = select_kernel(maxobs);
+    if (!fn) return 0;
+    const int smem = sweep_smem_bytes(g);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSweepThreads, smem) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    if (per_sm < 1) return 0;
+    long long chunks = g.NW;
+    long long warps_per_cta = kSweepThreads / 32;
+    long long want = (chunks + warps_per_cta - 1) / warps_per_cta;
+    long long grid = (long long)per_sm * sms;
+    return (int)(grid < want ? grid : want);
+}
+
+cudaError_t launch_sweep(const SweepArgs& a, int maxobs, int grid, cudaStream_t s)
+{
+    void* fn = select_kernel(maxobs);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(a.chunk_counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    const int smem = sweep_smem_bytes(a.g);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&a};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kSweepThreads), args, (size_t)smem, s);
+}
+
+}  // namespace sensai

@@ -1,0 +1,76 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+* libsensai.so builds for sm_103a and exports exactly the entry points that
+  include/sensai.h declares (and nothing else under the sensai_ prefix).
+* Argument validation happens before any CUDA call: invalid geometry returns
+  SENSAI_EINVAL with a message, on machines with or without a GPU.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2311_15061_gb300 import build
+    build.build()
+    from paper_2311_15061_gb300 import sensai
+    return sensai
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "sensai.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sensai_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declarations_are_exported(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        getattr(lib._lib, n)  # raises AttributeError when missing
+    assert sorted(lib.EXPORTED) == names
+
+
+def test_no_undeclared_sensai_exports(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.library_path()], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("nm unavailable")
+    exported = sorted({l.split()[-1] for l in out.stdout.splitlines() if " sensai_" in l})
+    assert exported == _declared()
+
+
+@pytest.mark.parametrize("M,B,S,K", [
+    ((10,), (4,), (4,), 8),          # (M - B) not divisible by the stride
+    ((10,), (11,), (1,), 8),         # patch larger than the frame
+    ((10, 10), (3, 3), (1, 1), 0),   # no atoms
+    ((40, 40), (33, 33), (1, 1), 4), # P > 1024
+])
+def test_invalid_geometry_is_rejected(lib, M, B, S, K):
+    prm = lib.make_params(M, B, S, K)
+    mask = np.ones(M, np.uint8)
+    h = ctypes.c_void_p()
+    st = lib._lib.sensai_create(ctypes.byref(prm), mask.ctypes.data, ctypes.byref(h))
+    assert st == lib.SENSAI_EINVAL
+    assert h.value is None
+    assert lib.sensai_last_error()
+
+
+def test_invalid_hyperparameters_rejected(lib):
+    prm = lib.make_params((16, 16), (4, 4), (1, 1), 8, c=0.0)
+    mask = np.ones((16, 16), np.uint8)
+    h = ctypes.c_void_p()
+    assert lib._lib.sensai_create(ctypes.byref(prm), mask.ctypes.data, ctypes.byref(h)) == lib.SENSAI_EINVAL
+    prm = lib.make_params((16, 16), (4, 4), (1, 1), 8, flags=3)
+    assert lib._lib.sensai_create(ctypes.byref(prm), mask.ctypes.data, ctypes.byref(h)) == lib.SENSAI_EINVAL
+
+
+def test_null_context_is_an_error_not_a_crash(lib):
+    assert lib._lib.sensai_learn(None, None, 1, None) == lib.SENSAI_EINVAL
+    lib._lib.sensai_destroy(None)

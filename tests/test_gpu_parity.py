@@ -1,0 +1,280 @@
+"""GPU parity: every step of the CUDA path against the FP64 oracle.
+
+Each phase is run on both sides from the same float32-representable state
+(produced by the oracle), through the C ABI, and compared element by element
+with the tolerances stated in parity_helpers:
+
+* a1+a2 code sweep (patch extraction fused), a3+a4 dictionary sweep,
+  a5 pi / gamma draws, a6 overlap-add, a7 overlap counts;
+* the 128x128, K=64 workload in full, several tiles and a ragged tail;
+* the 512x512, K=128 benchmark workload: the code sweep on sampled patches
+  (the oracle sweeps those patches with their own Philox counters), the
+  dictionary and hyper-parameter draws in full;
+* edge cases: ragged patch counts, 1-D and 3-D frames with strides, K = 1,
+  full masks, an empty mask, determinism;
+* end to end: PSNR of the learned reconstruction within 0.1 dB of the
+  oracle's, averaged over seeds 0-4; the same for dictionary transfer.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from parity_helpers import (D_TOL, S_TOL, compare_codes, dict_errors, gpu_context, oracle_state,
+                            problem, push_state, round_state)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_15061_gb300 import build
+    build.build()
+
+
+C1 = dict(M=(128, 128), B=(8, 8), S=(1, 1), K=64, frac=0.25)
+
+
+def _phase_parity(M, B, S, K, frac, seed=0, warm=2, full_mask=False, check_flips=True):
+    prm, x, clean, mask = problem(M, B, S, K, frac, seed, full_mask=full_mask)
+    st = oracle_state(prm, x, mask, warm)
+    ctx = gpu_context(prm, mask)
+
+    # a1 + a2: code sweep
+    push_state(ctx, st, x)
+    ctx.sensai_sweep_codes()
+    g = ctx.sensai_get_state()
+    ost = st.copy()
+    _, L = O.zs_sweep_subset(ost, x, mask, want_logodds=True)
+    nflip, serr = compare_codes(st, g, ost, L)
+    N = ost.Z.shape[0]
+    if check_flips:
+        assert nflip <= max(3, 1e-4 * N), nflip
+    assert serr <= S_TOL, serr
+
+    # a3 + a4: dictionary sweep from the oracle's post-sweep state
+    post = round_state(ost.copy())
+    push_state(ctx, post, x)
+    ctx.sensai_draw_dictionary()
+    Dg = ctx.sensai_get_dictionary()
+    od = post.copy()
+    O.d_sweep(od, x, mask)
+    derr = dict_errors(Dg, od.D)
+    assert derr.max() <= D_TOL, derr.max()
+
+    # a5: pi, gamma_s, gamma_eps from the oracle's post-dictionary state
+    hst = round_state(od.copy())
+    push_state(ctx, hst, x)
+    ctx.sensai_draw_hyper()
+    gh = ctx.sensai_get_state()
+    oh = hst.copy()
+    O.hyper(oh, x, mask)
+    np.testing.assert_allclose(gh["pi"], oh.pi, rtol=1e-9)
+    assert abs(gh["gamma_s"] / oh.gamma_s - 1) <= 1e-9
+    assert abs(gh["gamma_eps"] / oh.gamma_eps - 1) <= 1e-5
+
+    # a6: overlap-add of the same state
+    rec = ctx.sensai_reconstruct()
+    orec = O.reconstruct(hst)
+    scale = max(np.abs(orec).max(), 1e-6)
+    assert np.abs(rec - orec).max() <= 1e-5 * scale
+
+    # a7: overlap counts, bit exact
+    np.testing.assert_array_equal(ctx.sensai_overlap_counts(), O.overlap_counts(prm))
+    ctx.close()
+    return nflip, serr, derr.max()
+
+
+def test_phases_128x128_k64():
+    _phase_parity(**C1)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_phases_128x128_other_seeds(seed):
+    _phase_parity(**C1, seed=seed, warm=1)
+
+
+@pytest.mark.parametrize("case", [
+    dict(M=(37, 45), B=(5, 4), S=(1, 1), K=12, frac=0.3),             # ragged: N = 1386
+    dict(M=(333,), B=(9,), S=(2,), K=5, frac=0.4),                     # 1-D, stride 2
+    dict(M=(6, 20, 21), B=(2, 4, 3), S=(2, 2, 3), K=7, frac=0.35),     # 3-D, strides
+    dict(M=(20, 20), B=(4, 4), S=(1, 1), K=1, frac=0.5),               # K = 1
+    dict(M=(24, 24), B=(8, 8), S=(1, 1), K=16, frac=1.0, full_mask=True),  # |Omega_i| = P = 64
+    dict(M=(48, 40), B=(6, 5), S=(3, 5), K=9, frac=0.2),               # stride > 1 in 2-D
+])
+def test_phases_edge_geometries(case):
+    _phase_parity(**case)
+
+
+def test_empty_mask_samples_the_prior():
+    """No observed pixel: every draw reduces to the prior on both sides."""
+    prm, x, clean, _ = problem((20, 24), (4, 4), (1, 1), 6, 0.0)
+    mask = np.zeros((20, 24), np.uint8)
+    st = O.State(prm, gamma_eps=3.0)
+    ctx = gpu_context(prm, mask)
+    push_state(ctx, round_state(st.copy()), x)
+    ctx.sensai_sweep_codes()
+    g = ctx.sensai_get_state()
+    ost = st.copy()
+    _, L = O.zs_sweep_subset(ost, x, mask, want_logodds=True)
+    nflip, serr = compare_codes(st, g, ost, L)
+    assert serr <= S_TOL
+    ctx.sensai_draw_dictionary()
+    ctx.close()
+
+
+def test_learn_is_deterministic():
+    prm, x, clean, mask = problem(C1["M"], C1["B"], C1["S"], C1["K"], C1["frac"], 3)
+    outs = []
+    for _ in range(2):
+        ctx = gpu_context(prm, mask)
+        ctx.sensai_learn(x, 3)
+        s = ctx.sensai_get_state()
+        outs.append((s["D"], s["Z"], s["S"], s["gamma_eps"]))
+        ctx.close()
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_initial_state_matches_oracle():
+    prm, x, clean, mask = problem(C1["M"], C1["B"], C1["S"], C1["K"], C1["frac"], 4)
+    ctx = gpu_context(prm, mask)
+    s = ctx.sensai_get_state()
+    st = O.State(prm)
+    np.testing.assert_allclose(s["D"], st.D, rtol=1e-6, atol=1e-9)
+    assert s["Z"].sum() == 0 and s["iter"] == 0
+    ctx.sensai_learn(x, 0)
+    ctx.close()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4])
+def test_psnr_seed(seed, psnr_record):
+    prm, x, clean, mask = problem(C1["M"], C1["B"], C1["S"], C1["K"], C1["frac"], seed)
+    ctx = gpu_context(prm, mask)
+    ctx.sensai_learn(x, 10)
+    rec_g = ctx.sensai_reconstruct()
+    ctx.close()
+    st = O.learn(O.State(prm), x, mask, 10)
+    rec_o = O.reconstruct(st)
+    psnr_record.append((O.psnr(rec_g, clean), O.psnr(rec_o, clean)))
+    assert O.psnr(rec_g, clean) > O.psnr(x * mask, clean)
+
+
+@pytest.fixture(scope="module")
+def psnr_record():
+    return []
+
+
+def test_psnr_mean_over_seeds_within_0p1_db(psnr_record):
+    assert len(psnr_record) == 5, "run together with test_psnr_seed"
+    g, o = np.mean(psnr_record, axis=0)
+    assert abs(g - o) <= 0.1, (g, o, psnr_record)
+
+
+def test_dictionary_transfer_inpaint_psnr():
+    """Learn on one frame (oracle), transfer D, inpaint other frames with 3
+    code sweeps on both sides: PSNR within 0.1 dB averaged over seeds."""
+    prm, x, clean, mask = problem(C1["M"], C1["B"], C1["S"], C1["K"], C1["frac"], 0)
+    learned = oracle_state(prm, x, mask, 10)
+    diffs = []
+    for seed in (5, 6, 7):
+        prm2, x2, clean2, mask2 = problem(C1["M"], C1["B"], C1["S"], C1["K"], 0.2, seed)
+        prm2.seed = prm.seed
+        ctx = gpu_context(prm2, mask2)
+        ctx.sensai_set_state(D=learned.D.astype(np.float32), pi=learned.pi, gamma_s=learned.gamma_s,
+                             gamma_eps=learned.gamma_eps, iter=learned.t)
+        out = np.empty(x2.shape, np.float32)
+        ctx.sensai_inpaint(x2, 3, out)
+        ctx.close()
+        ost = O.State(prm2, D=learned.D, pi=learned.pi, gamma_s=learned.gamma_s,
+                      gamma_eps=learned.gamma_eps, t=learned.t)
+        O.inpaint_sweeps(ost, x2, mask2, 3)
+        diffs.append(O.psnr(out, clean2) - O.psnr(O.reconstruct(ost), clean2))
+    assert abs(np.mean(diffs)) <= 0.1, diffs
+
+
+# ---------------------------------------------------------------- full size --
+
+C2 = dict(M=(512, 512), B=(10, 10), S=(1, 1), K=128, frac=0.10)
+
+
+@pytest.fixture(scope="module")
+def c2_state():
+    prm, x, clean, mask = problem(C2["M"], C2["B"], C2["S"], C2["K"], C2["frac"], 0, grains=2)
+    st = O.State(prm)
+    O.zs_sweep(st, x, mask)   # one oracle sweep from the initial state: ~45 active atoms per patch
+    st.t = 1
+    return prm, x, mask, round_state(st)
+
+
+def test_full_size_code_sweep_sampled(c2_state):
+    prm, x, mask, st = c2_state
+    ctx = gpu_context(prm, mask)
+    push_state(ctx, st, x)
+    ctx.sensai_sweep_codes()
+    g = ctx.sensai_get_state()
+    ctx.close()
+    rng = np.random.default_rng(0)
+    N = st.Z.shape[0]
+    sample = np.unique(np.concatenate([rng.choice(N, 600, replace=False), [0, N - 1]]))
+    ost = st.copy()
+    _, L = O.zs_sweep_subset(ost, x, mask, patches=sample, want_logodds=True)
+    nflip, serr = compare_codes(st, g, ost, L, patches=sample)
+    assert nflip <= 3
+    assert serr <= S_TOL
+
+
+def test_full_size_dictionary_and_hyper(c2_state):
+    prm, x, mask, st = c2_state
+    ctx = gpu_context(prm, mask)
+    push_state(ctx, st, x)
+    ctx.sensai_draw_dictionary()
+    Dg = ctx.sensai_get_dictionary()
+    od = st.copy()
+    O.d_sweep(od, x, mask)
+    assert dict_errors(Dg, od.D).max() <= D_TOL
+    hst = round_state(od.copy())
+    push_state(ctx, hst, x)
+    ctx.sensai_draw_hyper()
+    gh = ctx.sensai_get_state()
+    O.hyper(hst, x, mask)
+    np.testing.assert_allclose(gh["pi"], hst.pi, rtol=1e-9)
+    assert abs(gh["gamma_eps"] / hst.gamma_eps - 1) <= 1e-5
+    ctx.close()
+
+
+def test_full_size_reconstruct_and_counts(c2_state):
+    prm, x, mask, st = c2_state
+    ctx = gpu_context(prm, mask)
+    push_state(ctx, st, x)
+    rec = ctx.sensai_reconstruct()
+    orec = O.reconstruct(st)
+    assert np.abs(rec - orec).max() <= 1e-5 * np.abs(orec).max()
+    np.testing.assert_array_equal(ctx.sensai_overlap_counts(), O.overlap_counts(prm))
+    ctx.close()
+
+
+def test_device_buffers_and_streams():
+    """Frames and outputs as CUDA tensors on a side stream give the same result
+    as host buffers."""
+    import torch
+    prm, x, clean, mask = problem(C1["M"], C1["B"], C1["S"], C1["K"], C1["frac"], 8)
+    outs = []
+    for device in (False, True):
+        ctx = gpu_context(prm, mask)
+        if device:
+            s = torch.cuda.Stream()
+            xt = torch.from_numpy(x).cuda()
+            out = torch.empty_like(xt)
+            with torch.cuda.stream(s):
+                ctx.sensai_learn(xt, 2, stream=s)
+                ctx.sensai_reconstruct(out, stream=s)
+            s.synchronize()
+            outs.append(out.cpu().numpy())
+        else:
+            ctx.sensai_learn(x, 2)
+            outs.append(ctx.sensai_reconstruct())
+        ctx.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
