@@ -64,14 +64,15 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def _traffic_record(kernel_file):
+def _traffic_record(kernel_files):
     """dram bytes per launch of the code sweep from the committed ncu summary,
-    valid only while the kernel source is unchanged since the capture."""
+    valid only while the kernel sources are unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "sweep_kernel_stem512_k128_traffic.txt")
-    src = os.path.join(ROOT, "paper_2311_15061_gb300", "csrc", kernel_file)
     try:
         kv = dict(line.split(":", 1) for line in open(path).read().splitlines() if ":" in line)
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        blob = b"".join(open(os.path.join(ROOT, "paper_2311_15061_gb300", "csrc", f), "rb").read()
+                        for f in kernel_files)
+        digest = hashlib.sha256(blob).hexdigest()
         if kv.get("source_sha256", "").strip() != digest:
             return None
         return float(kv["dram_bytes_per_launch"])
@@ -155,7 +156,7 @@ def run_gpu(args):
     w = WORKLOAD
     prm = sensai.make_params(w["M"], w["B"], w["S"], w["K"], seed=w["seed"] + rank)
     ctx = sensai.Context(prm, mask)
-    N, K, iters = ctx.N, ctx.K, w["iters"]
+    N, K, iters = ctx.N, ctx.K, args.iters
     stream = torch.cuda.current_stream()
     frame = torch.from_numpy(x).cuda()
     out = torch.empty_like(frame)
@@ -215,7 +216,7 @@ def run_gpu(args):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SMS * LANES_PER_SM * sm_mhz * 1e6 / 1e12   # T lane-ops/s
     achieved = ops / sweep_n / (sweep_ms / sweep_n / 1e3) / 1e12
-    traffic = _traffic_record("sweep.cu")
+    traffic = _traffic_record(("sweep.cu", "internal.cuh"))
 
     # end to end through the C ABI with pinned host buffers
     xh = torch.from_numpy(x).pin_memory()
@@ -324,6 +325,8 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["sensai", "reference"], default="sensai")
+    ap.add_argument("--iters", type=int, default=WORKLOAD["iters"],
+                    help="Gibbs iterations per step (50 is the workload; fewer only for profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -13,110 +13,170 @@
 // memory for all K atoms.  Each thread owns fixed 32-patch words; per atom it
 // ANDs the atom's activity word with the pixel's observation word, applies
 // the previous atom's update to its own slots and accumulates the two sums,
-// which a fixed-order block reduction (FP64 across threads) turns into one
-// draw.  No global synchronisation, no float atomics; results are
+// which a fixed-order block reduction (FP32 within warps, FP64 across warps)
+// turns into one draw; the K normals are drawn up front.  Two barriers per
+// atom, no global synchronisation, no float atomics: results are
 // deterministic.
 #include "internal.cuh"
 
 namespace sensai {
 
 constexpr int kDictThreads = 1024;
+constexpr int kDictMaxK = 1024;
 
-template <bool SMEM_R>
+// WPT: 32-patch words per thread (NW <= WPT * kDictThreads), kept in registers.
+template <int WPT, bool SMEM_R>
 __global__ void __launch_bounds__(kDictThreads, 1) dict_kernel(const DictArgs a)
 {
     extern __shared__ float rsm[];
-    __shared__ double red[kDictThreads / 32];
+    __shared__ float red_a[kDictThreads / 32], red_b[kDictThreads / 32];
+    __shared__ double xi[kDictMaxK];
     __shared__ float s_delta;
     const int p = blockIdx.x;
     const int K = a.g.K, P = a.g.P, NW = a.g.NW;
     const long long N = a.g.N;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int base = a.Rbase[p];
     const int cnt = a.Rbase[p + 1] - base;
     float* Rp = SMEM_R ? rsm : a.R + base;
-    if (SMEM_R) {
+    if (SMEM_R)
         for (int s = threadIdx.x; s < cnt; s += blockDim.x) rsm[s] = a.R[base + s];
-        __syncthreads();
+    // the K normals of this pixel's draws, off the sequential path
+    const uint2 key = seed_key(a.seed);
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const uint4 blk = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)k, a.t, kTagDict), key);
+        xi[k] = normal64(blk.x, blk.y);
     }
+    __syncthreads();
+
     const uint32_t* Ib = a.Ibits + (long long)p * NW;
     const uint32_t* Ip = a.Ipre + (long long)p * NW;
     const double ge = a.sc->gamma_eps;
-    const uint2 key = seed_key(a.seed);
+    uint32_t ib[WPT], zprev[WPT];
+    int pre[WPT];
+#pragma unroll
+    for (int m = 0; m < WPT; ++m) {
+        const int j = threadIdx.x + m * kDictThreads;
+        ib[m] = j < NW ? Ib[j] : 0u;
+        pre[m] = j < NW ? (int)Ip[j] : 0;
+        zprev[m] = 0u;
+    }
     float delta_prev = 0.0f;
 
     for (int k = 0; k <= K; ++k) {
+        uint32_t zcur[WPT];
+#pragma unroll
+        for (int m = 0; m < WPT; ++m) {
+            const int j = threadIdx.x + m * kDictThreads;
+            zcur[m] = (k < K && ib[m]) ? (a.Zb[(long long)k * NW + j] & ib[m]) : 0u;
+        }
         float acc_a = 0.0f, acc_b = 0.0f;
-        for (int j = threadIdx.x; j < NW; j += blockDim.x) {
-            const uint32_t ib = Ib[j];
-            if (!ib) continue;
-            const int pre = (int)Ip[j];
-            if (k > 0 && delta_prev != 0.0f) {
-                uint32_t bits = a.Zb[(long long)(k - 1) * NW + j] & ib;
+#pragma unroll
+        for (int m = 0; m < WPT; ++m) {
+            const int j = threadIdx.x + m * kDictThreads;
+            uint32_t bits = delta_prev != 0.0f ? zprev[m] : 0u;
+            if (bits) {
                 const float* wrow = a.W + (long long)(k - 1) * N + (long long)j * 32;
-                while (bits) {
+                do {
                     const int b = __ffs(bits) - 1;
                     bits &= bits - 1u;
-                    const int slot = pre + __popc(ib & ((1u << b) - 1u));
-                    Rp[slot] = fmaf(-delta_prev, wrow[b], Rp[slot]);
-                }
+                    const int slot = pre[m] + __popc(ib[m] & ((1u << b) - 1u));
+                    Rp[slot] = fmaf(-delta_prev, __ldg(wrow + b), Rp[slot]);
+                } while (bits);
             }
-            if (k < K) {
-                uint32_t bits = a.Zb[(long long)k * NW + j] & ib;
+            bits = zcur[m];
+            if (bits) {
                 const float* wrow = a.W + (long long)k * N + (long long)j * 32;
-                while (bits) {
+                do {
                     const int b = __ffs(bits) - 1;
                     bits &= bits - 1u;
-                    const int slot = pre + __popc(ib & ((1u << b) - 1u));
-                    const float w = wrow[b];
+                    const int slot = pre[m] + __popc(ib[m] & ((1u << b) - 1u));
+                    const float w = __ldg(wrow + b);
                     acc_a = fmaf(w, Rp[slot], acc_a);
                     acc_b = fmaf(w, w, acc_b);
-                }
+                } while (bits);
             }
+            zprev[m] = zcur[m];
         }
         if (k == K) break;
-        const double sum_wr = block_sum((double)acc_a, red);
-        const double sum_ww = block_sum((double)acc_b, red);
-        if (threadIdx.x == 0) {
-            const float d_old = a.D[(long long)k * P + p];
-            const double num = sum_wr + (double)d_old * sum_ww;   // sum w r^{-k}
-            const double prec = (double)P + ge * sum_ww;
-            const uint4 blk = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)k, a.t, kTagDict), key);
-            const double dnew = ge * num / prec + normal64(blk.x, blk.y) / sqrt(prec);
-            const float dnew_f = (float)dnew;
-            a.D[(long long)k * P + p] = dnew_f;
-            s_delta = dnew_f - d_old;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc_a += __shfl_down_sync(0xffffffffu, acc_a, o);
+            acc_b += __shfl_down_sync(0xffffffffu, acc_b, o);
+        }
+        if (lane == 0) {
+            red_a[warp] = acc_a;
+            red_b[warp] = acc_b;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const int nwarp = blockDim.x >> 5;
+            double va = lane < nwarp ? (double)red_a[lane] : 0.0;
+            double vb = lane < nwarp ? (double)red_b[lane] : 0.0;
+            va = warp_sum(va);
+            vb = warp_sum(vb);
+            if (lane == 0) {
+                const float d_old = a.D[(long long)k * P + p];
+                const double num = va + (double)d_old * vb;   // sum w r^{-k}
+                const double prec = (double)P + ge * vb;
+                const double dnew = ge * num / prec + xi[k] / sqrt(prec);
+                const float dnew_f = (float)dnew;
+                a.D[(long long)k * P + p] = dnew_f;
+                s_delta = dnew_f - d_old;
+            }
         }
         __syncthreads();
         delta_prev = s_delta;
     }
     __syncthreads();
-    double r2 = 0.0;
+    float r2 = 0.0f;
     for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
-        const double v = Rp[s];
-        r2 += v * v;
-        if (SMEM_R) a.R[base + s] = Rp[s];
+        const float v = Rp[s];
+        r2 = fmaf(v, v, r2);
+        if (SMEM_R) a.R[base + s] = v;
     }
-    r2 = block_sum(r2, red);
-    if (threadIdx.x == 0) a.part_r2[p] = r2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r2 += __shfl_down_sync(0xffffffffu, r2, o);
+    if (lane == 0) red_a[warp] = r2;
+    __syncthreads();
+    if (warp == 0) {
+        double v = lane < (int)(blockDim.x >> 5) ? (double)red_a[lane] : 0.0;
+        v = warp_sum(v);
+        if (lane == 0) a.part_r2[p] = v;
+    }
+}
+
+template <int WPT>
+static cudaError_t launch_wpt(const DictArgs& a, size_t smem, bool smem_r, cudaStream_t s)
+{
+    void* args[] = {(void*)&a};
+    void* fn = smem_r ? (void*)dict_kernel<WPT, true> : (void*)dict_kernel<WPT, false>;
+    if (smem_r) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaLaunchKernel(fn, dim3(a.g.P), dim3(kDictThreads), args, smem_r ? smem : 0, s);
 }
 
 cudaError_t launch_dict(const DictArgs& a, int max_slots, cudaStream_t s)
 {
+    if (a.g.K > kDictMaxK) return cudaErrorInvalidValue;
     const size_t smem = sizeof(float) * (size_t)max_slots;
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const size_t reserve = sizeof(double) * (kDictThreads / 32) + 64;
-    void* args[] = {(void*)&a};
-    if (smem + reserve <= (size_t)optin) {
-        void* fn = (void*)dict_kernel<true>;
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        return cudaLaunchKernel(fn, dim3(a.g.P), dim3(kDictThreads), args, smem, s);
-    }
-    return cudaLaunchKernel((void*)dict_kernel<false>, dim3(a.g.P), dim3(kDictThreads), args, 0, s);
+    const size_t fixed = sizeof(double) * kDictMaxK + 2 * sizeof(float) * (kDictThreads / 32) + 64;
+    const bool smem_r = smem + fixed <= (size_t)optin;
+    const int wpt = (a.g.NW + kDictThreads - 1) / kDictThreads;
+    if (wpt <= 1) return launch_wpt<1>(a, smem, smem_r, s);
+    if (wpt <= 2) return launch_wpt<2>(a, smem, smem_r, s);
+    if (wpt <= 4) return launch_wpt<4>(a, smem, smem_r, s);
+    if (wpt <= 8) return launch_wpt<8>(a, smem, smem_r, s);
+    if (wpt <= 16) return launch_wpt<16>(a, smem, smem_r, s);
+    if (wpt <= 32) return launch_wpt<32>(a, smem, smem_r, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace sensai

@@ -99,13 +99,35 @@ __device__ __forceinline__ double normal64(uint32_t x0, uint32_t x1)
     return sqrt(-2.0 * log(uniform64(x0))) * cospi(2.0 * uniform64(x1));
 }
 
-// Box-Muller in FP32 (used for the code draws).
+// Box-Muller in FP32 (used for the code draws): sqrt(-2 ln u1) cos(2 pi u2)
+// with u = (x + 1) 2^-32, evaluated so that no FP32 rounding of the 32-bit
+// words is amplified:
+//  * ln u1 for u1 > 1/2 is log1p(-(1 - u1)), where 1 - u1 = (2^32-1 - x0) 2^-32
+//    is formed in integers (u1 near 1 would otherwise lose all its digits);
+//  * the angle 2 pi (x1 + 1) / 2^32 is split in integers into the nearest
+//    multiple of pi/2 and a remainder d in [-2^29, 2^29), so the cosine is
+//    +-cospi or +-sinpi of d / 2^31 with |d / 2^31| <= 1/4: near the zeros of
+//    the cosine the result keeps full relative precision.
 __device__ __forceinline__ float normal32(uint32_t x0, uint32_t x1)
 {
-    const float scale = 2.3283064365386963e-10f;  // 2^-32
-    const float u1 = fmaf((float)x0, scale, scale);
-    const float u2 = fmaf((float)x1, scale, scale);
-    return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
+    float ln_u1;
+    if (x0 >= 0x80000000u)
+        ln_u1 = log1pf(-(float)(0xFFFFFFFFu - x0) * two_m32);
+    else
+        ln_u1 = logf(fmaf((float)x0, two_m32, two_m32));
+    const uint64_t y = (uint64_t)x1 + 1u;                 // angle = 2 pi y / 2^32
+    const uint32_t quarter = (uint32_t)((y + (1u << 29)) >> 30);   // nearest multiple of pi/2
+    const int32_t d = (int32_t)((int64_t)y - ((int64_t)quarter << 30));
+    const float f = (float)d * 4.656612873077393e-10f;    // d / 2^31, |f| <= 1/4
+    float c;
+    switch (quarter & 3u) {
+        case 0: c = cospif(f); break;
+        case 1: c = -sinpif(f); break;
+        case 2: c = -cospif(f); break;
+        default: c = sinpif(f); break;
+    }
+    return sqrtf(-2.0f * ln_u1) * c;
 }
 
 // Marsaglia-Tsang for shape >= 1; attempt a uses block (c0, c1, t, tag | a << 8):
