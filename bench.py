@@ -41,7 +41,7 @@ WORKLOAD_NAME = ("stem512_k128: 512x512 two-grain synthetic STEM frame, 10% Bern
 METRIC = "patch·atom Gibbs updates/s"
 UNIT = "patch·atom updates/s"
 
-# Algorithmic lane-operations of one code update (roofline):
+# Algorithmic lane-operations of one code update:
 #   2 |Omega_i| FMAs (masked norm + correlation), 75 fixed (Philox4x32-10:
 #   60, log-odds / sigmoid / threshold: 15), 14 more when z = 1 (Box-Muller +
 #   weight), |Omega_i| FMAs when the weight changes (rank-1 residual update).
