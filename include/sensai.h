@@ -185,6 +185,27 @@ sensai_status sensai_get_stats(sensai_ctx* ctx, sensai_stats* stats);
 sensai_status sensai_profile(sensai_ctx* ctx, int32_t enable);
 sensai_status sensai_profile_read(sensai_ctx* ctx, double* ms, int64_t* counts);
 
+/* Overlap-add reconstruction that allocates nothing, for callers that cannot
+ * allocate GPU memory themselves: a plugin inside a host application whose
+ * memory pool owns the device, or a live-acquisition callback with a hard
+ * time budget in which cudaMalloc (which may block and synchronise the
+ * device) is not allowed.  The paper has no counterpart; it computes the same
+ * frame as sensai_reconstruct without a context.
+ *  - params: frame / patch / stride geometry and K (the other fields are
+ *    ignored); the same validity rules as sensai_create.
+ *  - D: K*P floats, S: N*K floats patch-major (S[i*K + k], 0 where atom k
+ *    is inactive in patch i), out: prod(M) floats -- all device pointers on
+ *    the current device, owned by the caller.
+ *  - Scratch is a fixed 16 MiB static device array (4,194,304 floats) that
+ *    every GPU loading the library holds until exit; P * N above that is
+ *    rejected with SENSAI_EINVAL.  No cudaMalloc / cudaFree is called.
+ *  - The first call on a device looks up the array's device address; make
+ *    that first call before any stream capture.  All calls share the array:
+ *    calls that overlap on the GPU race and must be serialised by the caller.
+ *  - Asynchronous on `stream`; errors as for the other entry points. */
+sensai_status sensai_reconstruct_static(const sensai_params* params, const float* D, const float* S,
+                                        float* out, void* stream);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char* sensai_last_error(void);
 

@@ -33,6 +33,10 @@ sensai_status fail(sensai_status st, const char* fmt, ...)
 
 }  // namespace
 
+namespace sensai {
+void record_error(const char* msg) { g_last_error = msg; }
+}  // namespace sensai
+
 struct sensai_ctx {
     int device = 0;
     Geom g{};

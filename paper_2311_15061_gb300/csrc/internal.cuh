@@ -253,6 +253,9 @@ struct HyperArgs {
     uint32_t t;
 };
 
+// Sets the calling thread's message returned by sensai_last_error().
+void record_error(const char* msg);
+
 // Launchers (defined in the .cu files).
 cudaError_t launch_sweep(const SweepArgs& a, int maxobs, int grid, cudaStream_t s);
 int sweep_block_size();

@@ -27,7 +27,7 @@ EXPORTED = [
     "sensai_inpaint", "sensai_sweep_codes", "sensai_draw_dictionary", "sensai_draw_hyper",
     "sensai_reconstruct", "sensai_overlap_counts", "sensai_get_dictionary", "sensai_set_dictionary",
     "sensai_get_state", "sensai_set_state", "sensai_get_stats", "sensai_profile", "sensai_profile_read",
-    "sensai_last_error",
+    "sensai_reconstruct_static", "sensai_last_error",
 ]
 
 
@@ -104,6 +104,7 @@ _SIG = {
     "sensai_get_stats": (_st, [_vp, ctypes.POINTER(sensai_stats)]),
     "sensai_profile": (_st, [_vp, _i32]),
     "sensai_profile_read": (_st, [_vp, _vp, _vp]),
+    "sensai_reconstruct_static": (_st, [ctypes.POINTER(sensai_params), _vp, _vp, _vp, _vp]),
     "sensai_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIG.items():
@@ -281,6 +282,17 @@ class Context:
         st = sensai_stats()
         _check(_lib.sensai_get_stats(self._h, ctypes.byref(st)))
         return st
+
+
+def sensai_reconstruct_static(params, D, S, out, stream=None):
+    """Overlap-add reconstruction without any device allocation (device
+    tensors D: K x P, S: N x K patch-major, out: frame shape)."""
+    for name, t in (("D", D), ("S", S), ("out", out)):
+        if not (hasattr(t, "is_cuda") and t.is_cuda):
+            raise TypeError(f"{name}: need a CUDA float32 tensor")
+    _check(_lib.sensai_reconstruct_static(ctypes.byref(params), _buf(D, np.float32, name="D"),
+                                          _buf(S, np.float32, name="S"), _buf(out, np.float32, name="out"),
+                                          _stream(stream)))
 
 
 def sensai_last_error():
