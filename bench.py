@@ -81,7 +81,11 @@ def _traffic_record(kernel_files):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region.
+
+    Started before the warm-up and armed only once its first sample has
+    arrived, so that nvidia-smi's own start-up never overlaps the timed steps.
+    """
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -90,27 +94,46 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu_index = gpu_index
         self.proc = None
+        self.lines = []
+        self.armed_at = None
+        self._thread = None
 
-    def __enter__(self):
+    def start(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
-        time.sleep(0.3)
+            return self
+
+        def reader():
+            for line in self.proc.stdout:
+                self.lines.append(line)
+
+        self._thread = threading.Thread(target=reader, daemon=True)
+        self._thread.start()
         return self
 
-    def __exit__(self, *exc):
-        self.out = ""
+    def wait_ready(self, timeout=30.0):
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.05)
+        time.sleep(0.2)
+
+    def arm(self):
+        self.armed_at = len(self.lines)
+
+    def stop(self):
+        self.stopped_at = len(self.lines)
         if self.proc is not None:
-            time.sleep(0.2)
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                self.out = ""
+        self.out = "".join(self.lines[self.armed_at or 0:self.stopped_at])
 
     def summary(self):
         rows = []
@@ -169,29 +192,33 @@ def run_gpu(args):
         ctx.sensai_learn(None, iters, stream)
         ctx.sensai_reconstruct(out, stream)
 
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    gpu_index = int(vis) if vis.isdigit() else local
+    clocks = ClockSampler(gpu_index).start()
     for _ in range(args.warmup):
         flush.zero_()
         step()
     torch.cuda.synchronize()
+    clocks.wait_ready()
     if world > 1:
         torch.distributed.barrier()
 
-    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or 0) \
-        if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     launches0 = ctx.sensai_get_stats().kernel_launches
     ctx.sensai_profile(1)
-    with ClockSampler(gpu_index) as clocks:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.zero_()
-            starts[k].record(stream)
-            step()
-            ends[k].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    clocks.arm()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    time.sleep(0.15)
+    clocks.stop()
     if world > 1:
         torch.distributed.barrier()
     stats = ctx.sensai_get_stats()

@@ -65,6 +65,7 @@ struct sensai_ctx {
     uint32_t* Ipre = nullptr;
     int* Icnt = nullptr;
     int* Rbase = nullptr;
+    int* Ilist = nullptr;       // per pixel: patches observing it, in slot order
     int* misc = nullptr;        // [0] max observed per patch, [1] max slots per pixel
     float* x = nullptr;
     float* D = nullptr;
@@ -117,7 +118,7 @@ bool is_device_pointer(const void* p)
 
 void free_all(sensai_ctx* c)
 {
-    void* ptrs[] = {c->mask_bits, c->imgoff, c->nobs, c->obs, c->Ibits, c->Ipre, c->Icnt, c->Rbase,
+    void* ptrs[] = {c->mask_bits, c->imgoff, c->nobs, c->obs, c->Ibits, c->Ipre, c->Icnt, c->Rbase, c->Ilist,
                     c->misc, c->x, c->D, c->W, c->Zb, c->R, c->Y, c->out, c->pi, c->lpi, c->m,
                     c->part_s2, c->part_r2, c->chunk_counter, c->sc};
     for (void* p : ptrs)
@@ -240,7 +241,7 @@ sensai_status run_sweep(sensai_ctx* ctx, cudaStream_t s)
     a.part_r2 = ctx->part_r2;
     a.chunk_counter = ctx->chunk_counter;
     a.sc_out = ctx->sc;
-    a.seed = ctx->prm.seed;
+    a.keys = philox_round_keys(ctx->prm.seed);
     a.t = (uint32_t)ctx->t;
     PhaseTimer timer(ctx, kPhaseCodes, s);
     SENSAI_CUDA(ctx, cudaMemsetAsync(ctx->m, 0, sizeof(int) * ctx->g.K, s));
@@ -264,9 +265,7 @@ sensai_status run_dictionary(sensai_ctx* ctx, cudaStream_t s)
     a.g = ctx->g;
     a.D = ctx->D;
     a.W = ctx->W;
-    a.Zb = ctx->Zb;
-    a.Ibits = ctx->Ibits;
-    a.Ipre = ctx->Ipre;
+    a.Ilist = ctx->Ilist;
     a.Rbase = ctx->Rbase;
     a.R = ctx->R;
     a.sc = ctx->sc;
@@ -318,7 +317,7 @@ sensai_status run_hyper(sensai_ctx* ctx, cudaStream_t s)
 
 sensai_status clear_codes(sensai_ctx* ctx, cudaStream_t s)
 {
-    SENSAI_CUDA(ctx, cudaMemsetAsync(ctx->W, 0, sizeof(float) * (size_t)ctx->g.K * ctx->g.N, s));
+    SENSAI_CUDA(ctx, cudaMemsetAsync(ctx->W, 0, sizeof(float) * (size_t)ctx->g.KB * kAtomBlock * ctx->g.Npad, s));
     SENSAI_CUDA(ctx, cudaMemsetAsync(ctx->Zb, 0, sizeof(uint32_t) * (size_t)ctx->g.K * ctx->g.NW, s));
     ctx->codes_valid = false;
     ctx->resid_valid = false;
@@ -389,6 +388,8 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     g.P = (int)P;
     g.N = N;
     g.NW = (int)((N + 31) / 32);
+    g.Npad = (long long)g.NW * 32;
+    g.KB = (p.K + kAtomBlock - 1) / kAtomBlock;
     g.nframe = nframe;
 
     int device = 0, optin = 0;
@@ -455,11 +456,14 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     CREATE_CUDA(cudaMemcpy(&total, ctx->Rbase + P, sizeof(int), cudaMemcpyDeviceToHost));
     CREATE_CUDA(cudaMemcpy(&ctx->max_slots, ctx->misc + 1, sizeof(int), cudaMemcpyDeviceToHost));
     ctx->n_observed = total;
+    CREATE_CUDA(dalloc(&ctx->Ilist, (size_t)total));
+    CREATE_CUDA(launch_ilist(g, ctx->Ibits, ctx->Ipre, ctx->Rbase, ctx->Ilist, st0));
+    ctx->launches += 1;
 
     CREATE_CUDA(dalloc(&ctx->x, (size_t)nframe));
     CREATE_CUDA(dalloc(&ctx->out, (size_t)nframe));
     CREATE_CUDA(dalloc(&ctx->D, (size_t)g.K * P));
-    CREATE_CUDA(dalloc(&ctx->W, (size_t)g.K * N));
+    CREATE_CUDA(dalloc(&ctx->W, (size_t)g.KB * kAtomBlock * g.Npad));
     CREATE_CUDA(dalloc(&ctx->Zb, (size_t)g.K * g.NW));
     CREATE_CUDA(dalloc(&ctx->R, (size_t)total));
     CREATE_CUDA(dalloc(&ctx->Y, (size_t)P * N));

@@ -1,47 +1,56 @@
 // dict.cu -- the dictionary sweep (the dictionary-learning step of the BPFA
 // section), atoms in order k = 0..K-1, each d_kp from its conjugate Gaussian
 // given every other atom's current value:
-//   Lambda_kp = P + gamma_eps sum_{i: z_ik=1, p in Omega_i} w_ik^2
-//   mu_kp     = gamma_eps / Lambda_kp * sum_{i: z_ik=1, p in Omega_i} w_ik r^{-k}_ip
+//   Lambda_kp = P + gamma_eps sum_{i: p in Omega_i} w_ik^2
+//   mu_kp     = gamma_eps / Lambda_kp * sum_{i: p in Omega_i} w_ik r^{-k}_ip
 //   d_kp      = mu_kp + Lambda_kp^-1/2 BoxMuller(Philox(p, k, t, DICT))
-// with r^{-k} = r + d_k w_k the residual that leaves atom k out; afterwards the
-// residual takes the new atom: r -= (d_new - d_old) w_k.
+// with r^{-k} the residual that leaves atom k out (atoms before k already
+// redrawn); afterwards the residual takes the new atom: r -= (d_new - d_old) w_k.
 //
 // Neither sum couples different pixels p, so the sweep splits into P
 // independent chains of K sequential draws.  GB300 mapping: one CTA per pixel
-// p keeps that pixel's residual slots (one per patch observing p) in shared
-// memory for all K atoms.  Each thread owns fixed 32-patch words; per atom it
-// ANDs the atom's activity word with the pixel's observation word, applies
-// the previous atom's update to its own slots and accumulates the two sums,
-// which a fixed-order block reduction (FP32 within warps, FP64 across warps)
-// turns into one draw; the K normals are drawn up front.  Two barriers per
-// atom, no global synchronisation, no float atomics: results are
-// deterministic.
+// p keeps the residual slots of the patches observing p in shared memory.
+// Atoms go in blocks of 8: one pass over the slots reads each patch's 8
+// weights as one 32-byte sector, applies the previous block's update and
+// accumulates G_k = sum w_k r and the in-block Gram C_kl = sum w_k w_l
+// (l <= k); a fixed-order block reduction (FP32 within warps, FP64 across
+// warps) feeds 8 sequential draws on one thread, exactly the atom-ordered
+// conditionals because
+//   sum w_k r^{-k} = G_k + d_old,k C_kk - sum_{l<k in block} (d_new,l - d_old,l) C_kl.
+// The K normals are drawn up front.  No global synchronisation and no float
+// atomics: results are deterministic.
 #include "internal.cuh"
 
 namespace sensai {
 
-constexpr int kDictThreads = 1024;
+constexpr int kDictThreads = 512;
+constexpr int kDictWarps = kDictThreads / 32;
 constexpr int kDictMaxK = 1024;
+constexpr int kGram = kAtomBlock * (kAtomBlock + 1) / 2;   // 36
+constexpr int kRed = kAtomBlock + kGram;                    // 44 sums per block
 
-// WPT: 32-patch words per thread (NW <= WPT * kDictThreads), kept in registers.
-template <int WPT, bool SMEM_R>
+// RHO: residual slots in shared memory; LIST: slot -> patch list too.
+template <bool RHO, bool LIST>
 __global__ void __launch_bounds__(kDictThreads, 1) dict_kernel(const DictArgs a)
 {
-    extern __shared__ float rsm[];
-    __shared__ float red_a[kDictThreads / 32], red_b[kDictThreads / 32];
+    extern __shared__ float dsm[];
+    __shared__ float red[kDictWarps][kRed];
+    __shared__ double fin[kRed];
     __shared__ double xi[kDictMaxK];
-    __shared__ float s_delta;
+    __shared__ float s_delta[kAtomBlock];
     const int p = blockIdx.x;
-    const int K = a.g.K, P = a.g.P, NW = a.g.NW;
-    const long long N = a.g.N;
+    const int K = a.g.K, P = a.g.P, KB = a.g.KB;
+    const long long Npad = a.g.Npad;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int base = a.Rbase[p];
     const int cnt = a.Rbase[p + 1] - base;
-    float* Rp = SMEM_R ? rsm : a.R + base;
-    if (SMEM_R)
-        for (int s = threadIdx.x; s < cnt; s += blockDim.x) rsm[s] = a.R[base + s];
-    // the K normals of this pixel's draws, off the sequential path
+    float* rho = RHO ? dsm : a.R + base;
+    int* list_s = reinterpret_cast<int*>(dsm + (RHO ? cnt : 0));
+    const int* ilist = LIST ? list_s : a.Ilist + base;
+    for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
+        if (RHO) rho[s] = a.R[base + s];
+        if (LIST) list_s[s] = a.Ilist[base + s];
+    }
     const uint2 key = seed_key(a.seed);
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         const uint4 blk = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)k, a.t, kTagDict), key);
@@ -49,134 +58,146 @@ __global__ void __launch_bounds__(kDictThreads, 1) dict_kernel(const DictArgs a)
     }
     __syncthreads();
 
-    const uint32_t* Ib = a.Ibits + (long long)p * NW;
-    const uint32_t* Ip = a.Ipre + (long long)p * NW;
     const double ge = a.sc->gamma_eps;
-    uint32_t ib[WPT], zprev[WPT];
-    int pre[WPT];
+    const float4* Wv = reinterpret_cast<const float4*>(a.W);
+    float dprev[kAtomBlock];
 #pragma unroll
-    for (int m = 0; m < WPT; ++m) {
-        const int j = threadIdx.x + m * kDictThreads;
-        ib[m] = j < NW ? Ib[j] : 0u;
-        pre[m] = j < NW ? (int)Ip[j] : 0;
-        zprev[m] = 0u;
-    }
-    float delta_prev = 0.0f;
+    for (int kk = 0; kk < kAtomBlock; ++kk) dprev[kk] = 0.0f;
 
-    for (int k = 0; k <= K; ++k) {
-        uint32_t zcur[WPT];
+    for (int kb = 0; kb <= KB; ++kb) {
+        float G[kAtomBlock], C[kGram];
 #pragma unroll
-        for (int m = 0; m < WPT; ++m) {
-            const int j = threadIdx.x + m * kDictThreads;
-            zcur[m] = (k < K && ib[m]) ? (a.Zb[(long long)k * NW + j] & ib[m]) : 0u;
+        for (int v = 0; v < kAtomBlock; ++v) G[v] = 0.0f;
+#pragma unroll
+        for (int v = 0; v < kGram; ++v) C[v] = 0.0f;
+        // two-deep software pipeline over this thread's slots: the next slot's
+        // weights are in flight while the current one is applied
+        const float4* qprev = Wv + (long long)(kb > 0 ? kb - 1 : 0) * Npad * 2;
+        const float4* qcur = Wv + (long long)kb * Npad * 2;
+        const bool has_prev = kb > 0, has_cur = kb < KB;
+        const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        int s = threadIdx.x;
+        float rr = 0.0f;
+        float4 u0 = zero4, u1 = zero4, v0 = zero4, v1 = zero4;
+        if (s < cnt) {
+            const long long i = ilist[s];
+            rr = rho[s];
+            if (has_prev) { u0 = qprev[i * 2]; u1 = qprev[i * 2 + 1]; }
+            if (has_cur) { v0 = qcur[i * 2]; v1 = qcur[i * 2 + 1]; }
         }
-        float acc_a = 0.0f, acc_b = 0.0f;
-#pragma unroll
-        for (int m = 0; m < WPT; ++m) {
-            const int j = threadIdx.x + m * kDictThreads;
-            uint32_t bits = delta_prev != 0.0f ? zprev[m] : 0u;
-            if (bits) {
-                const float* wrow = a.W + (long long)(k - 1) * N + (long long)j * 32;
-                do {
-                    const int b = __ffs(bits) - 1;
-                    bits &= bits - 1u;
-                    const int slot = pre[m] + __popc(ib[m] & ((1u << b) - 1u));
-                    Rp[slot] = fmaf(-delta_prev, __ldg(wrow + b), Rp[slot]);
-                } while (bits);
+        while (s < cnt) {
+            const int sn = s + blockDim.x;
+            float rn = 0.0f;
+            float4 nu0 = zero4, nu1 = zero4, nv0 = zero4, nv1 = zero4;
+            if (sn < cnt) {
+                const long long i = ilist[sn];
+                rn = rho[sn];
+                if (has_prev) { nu0 = qprev[i * 2]; nu1 = qprev[i * 2 + 1]; }
+                if (has_cur) { nv0 = qcur[i * 2]; nv1 = qcur[i * 2 + 1]; }
             }
-            bits = zcur[m];
-            if (bits) {
-                const float* wrow = a.W + (long long)k * N + (long long)j * 32;
-                do {
-                    const int b = __ffs(bits) - 1;
-                    bits &= bits - 1u;
-                    const int slot = pre[m] + __popc(ib[m] & ((1u << b) - 1u));
-                    const float w = __ldg(wrow + b);
-                    acc_a = fmaf(w, Rp[slot], acc_a);
-                    acc_b = fmaf(w, w, acc_b);
-                } while (bits);
+            if (has_prev) {
+                rr = fmaf(-dprev[0], u0.x, rr);
+                rr = fmaf(-dprev[1], u0.y, rr);
+                rr = fmaf(-dprev[2], u0.z, rr);
+                rr = fmaf(-dprev[3], u0.w, rr);
+                rr = fmaf(-dprev[4], u1.x, rr);
+                rr = fmaf(-dprev[5], u1.y, rr);
+                rr = fmaf(-dprev[6], u1.z, rr);
+                rr = fmaf(-dprev[7], u1.w, rr);
+                rho[s] = rr;
             }
-            zprev[m] = zcur[m];
-        }
-        if (k == K) break;
+            if (has_cur) {
+                const float w[kAtomBlock] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            acc_a += __shfl_down_sync(0xffffffffu, acc_a, o);
-            acc_b += __shfl_down_sync(0xffffffffu, acc_b, o);
+                for (int k = 0; k < kAtomBlock; ++k) {
+                    G[k] = fmaf(w[k], rr, G[k]);
+#pragma unroll
+                    for (int l = 0; l <= k; ++l) C[k * (k + 1) / 2 + l] = fmaf(w[k], w[l], C[k * (k + 1) / 2 + l]);
+                }
+            }
+            s = sn;
+            rr = rn;
+            u0 = nu0; u1 = nu1; v0 = nv0; v1 = nv1;
         }
-        if (lane == 0) {
-            red_a[warp] = acc_a;
-            red_b[warp] = acc_b;
+        if (kb == KB) break;
+#pragma unroll
+        for (int v = 0; v < kRed; ++v) {
+            float x = v < kAtomBlock ? G[v] : C[v - kAtomBlock];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) red[warp][v] = x;
         }
         __syncthreads();
-        if (warp == 0) {
-            const int nwarp = blockDim.x >> 5;
-            double va = lane < nwarp ? (double)red_a[lane] : 0.0;
-            double vb = lane < nwarp ? (double)red_b[lane] : 0.0;
-            va = warp_sum(va);
-            vb = warp_sum(vb);
-            if (lane == 0) {
+        if (threadIdx.x < kRed) {
+            double acc = 0.0;
+            for (int w = 0; w < kDictWarps; ++w) acc += (double)red[w][threadIdx.x];
+            fin[threadIdx.x] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int kk = 0; kk < kAtomBlock; ++kk) {
+                const int k = kb * kAtomBlock + kk;
+                if (k >= K) {
+                    s_delta[kk] = 0.0f;
+                    continue;
+                }
                 const float d_old = a.D[(long long)k * P + p];
-                const double num = va + (double)d_old * vb;   // sum w r^{-k}
-                const double prec = (double)P + ge * vb;
+                const double ckk = fin[kAtomBlock + kk * (kk + 1) / 2 + kk];
+                double num = fin[kk] + (double)d_old * ckk;            // sum w_k r^{-k}
+                for (int l = 0; l < kk; ++l) num -= (double)s_delta[l] * fin[kAtomBlock + kk * (kk + 1) / 2 + l];
+                const double prec = (double)P + ge * ckk;
                 const double dnew = ge * num / prec + xi[k] / sqrt(prec);
                 const float dnew_f = (float)dnew;
                 a.D[(long long)k * P + p] = dnew_f;
-                s_delta = dnew_f - d_old;
+                s_delta[kk] = dnew_f - d_old;
             }
         }
         __syncthreads();
-        delta_prev = s_delta;
+#pragma unroll
+        for (int kk = 0; kk < kAtomBlock; ++kk) dprev[kk] = s_delta[kk];
     }
     __syncthreads();
     float r2 = 0.0f;
     for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
-        const float v = Rp[s];
+        const float v = rho[s];
         r2 = fmaf(v, v, r2);
-        if (SMEM_R) a.R[base + s] = v;
+        if (RHO) a.R[base + s] = v;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) r2 += __shfl_down_sync(0xffffffffu, r2, o);
-    if (lane == 0) red_a[warp] = r2;
+    if (lane == 0) red[warp][0] = r2;
     __syncthreads();
-    if (warp == 0) {
-        double v = lane < (int)(blockDim.x >> 5) ? (double)red_a[lane] : 0.0;
-        v = warp_sum(v);
-        if (lane == 0) a.part_r2[p] = v;
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        for (int w = 0; w < kDictWarps; ++w) acc += (double)red[w][0];
+        a.part_r2[p] = acc;
     }
 }
 
-template <int WPT>
-static cudaError_t launch_wpt(const DictArgs& a, size_t smem, bool smem_r, cudaStream_t s)
+template <bool RHO, bool LIST>
+static cudaError_t launch_mode(const DictArgs& a, size_t smem, cudaStream_t s)
 {
+    void* fn = (void*)dict_kernel<RHO, LIST>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     void* args[] = {(void*)&a};
-    void* fn = smem_r ? (void*)dict_kernel<WPT, true> : (void*)dict_kernel<WPT, false>;
-    if (smem_r) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaLaunchKernel(fn, dim3(a.g.P), dim3(kDictThreads), args, smem_r ? smem : 0, s);
+    return cudaLaunchKernel(fn, dim3(a.g.P), dim3(kDictThreads), args, smem, s);
 }
 
 cudaError_t launch_dict(const DictArgs& a, int max_slots, cudaStream_t s)
 {
     if (a.g.K > kDictMaxK) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(float) * (size_t)max_slots;
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const size_t fixed = sizeof(double) * kDictMaxK + 2 * sizeof(float) * (kDictThreads / 32) + 64;
-    const bool smem_r = smem + fixed <= (size_t)optin;
-    const int wpt = (a.g.NW + kDictThreads - 1) / kDictThreads;
-    if (wpt <= 1) return launch_wpt<1>(a, smem, smem_r, s);
-    if (wpt <= 2) return launch_wpt<2>(a, smem, smem_r, s);
-    if (wpt <= 4) return launch_wpt<4>(a, smem, smem_r, s);
-    if (wpt <= 8) return launch_wpt<8>(a, smem, smem_r, s);
-    if (wpt <= 16) return launch_wpt<16>(a, smem, smem_r, s);
-    if (wpt <= 32) return launch_wpt<32>(a, smem, smem_r, s);
-    return cudaErrorInvalidValue;
+    const size_t fixed = sizeof(float) * kDictWarps * kRed + sizeof(double) * (kRed + kDictMaxK) +
+                         sizeof(float) * kAtomBlock + 256;
+    const size_t slots = (size_t)max_slots;
+    if (slots * 8 + fixed <= (size_t)optin) return launch_mode<true, true>(a, slots * 8, s);
+    if (slots * 4 + fixed <= (size_t)optin) return launch_mode<true, false>(a, slots * 4, s);
+    return launch_mode<false, false>(a, 0, s);
 }
 
 }  // namespace sensai

@@ -201,6 +201,22 @@ __global__ void ola_gather_kernel(Geom g, const float* Y, float* out)
     out[u] = acc / (float)count;
 }
 
+// Slot -> patch list of every pixel p: Ilist[Rbase[p] + rank] = the patches
+// observing p in increasing index (one thread per (word, pixel)).
+__global__ void ilist_kernel(Geom g, const uint32_t* Ibits, const uint32_t* Ipre, const int* Rbase, int* Ilist)
+{
+    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.y;
+    if (w >= g.NW) return;
+    uint32_t bits = Ibits[(long long)p * g.NW + w];
+    int slot = Rbase[p] + (int)Ipre[(long long)p * g.NW + w];
+    while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        Ilist[slot++] = (int)(w * 32 + b);
+    }
+}
+
 // Per-patch reconstruction Y[p][i] = sum_k z_ik w_ik d_kp.  One thread per
 // patch, 32 pixels at a time; the dictionary chunk is read with warp-uniform
 // (broadcast) shared-memory loads.
@@ -224,9 +240,8 @@ __global__ void __launch_bounds__(256) patch_recon_kernel(Geom g, const float* D
 #pragma unroll
         for (int q = 0; q < 32; ++q) acc[q] = 0.0f;
         for (int k = 0; k < K; ++k) {
-            const uint32_t zw = Zb[(long long)k * g.NW + chunk];
-            if ((zw >> lane) & 1u) {
-                const float w = W[(long long)k * g.N + i];
+            const float w = W[wblock(g, k / kAtomBlock, i) + k % kAtomBlock];
+            if (w != 0.0f) {
                 const float* dk = Ds + k * ldP + p0;
 #pragma unroll
                 for (int q = 0; q < 32; ++q) acc[q] = fmaf(dk[q], w, acc[q]);
@@ -266,6 +281,13 @@ cudaError_t launch_slots(const Geom& g, const uint32_t* mask_bits, const int* im
     ibits_kernel<<<dim3(blocks_for(g.NW, 256), g.P), 256, 0, s>>>(g, mask_bits, imgoff, Ibits);
     iprefix_kernel<<<g.P, 1024, 0, s>>>(g, Ibits, Ipre, Icnt);
     rbase_kernel<<<1, 32, 0, s>>>(g.P, Icnt, Rbase, max_slots);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ilist(const Geom& g, const uint32_t* Ibits, const uint32_t* Ipre, const int* Rbase, int* Ilist,
+                         cudaStream_t s)
+{
+    ilist_kernel<<<dim3(blocks_for(g.NW, 256), g.P), 256, 0, s>>>(g, Ibits, Ipre, Rbase, Ilist);
     return cudaGetLastError();
 }
 

@@ -135,7 +135,7 @@ __global__ void code_stats_kernel(Geom g, const float* W, const uint32_t* Zb, in
         const uint32_t zw = Zb[(long long)k * g.NW + chunk];
         if (lane == 0 && zw) atomicAdd(&m[k], __popc(zw));
         if ((zw >> lane) & 1u) {
-            const double w = W[(long long)k * g.N + i];
+            const double w = W[wblock(g, k / kAtomBlock, i) + k % kAtomBlock];
             s2 += w * w;
         }
     }
@@ -161,9 +161,10 @@ __global__ void residual_kernel(Geom g, const float* x, const uint16_t* obs, con
         for (int j = 0; j < no; ++j) {
             const int p = obs[(long long)j * g.N + i];
             float r = x[org + imgoff[p]];
-            for (int k = 0; k < g.K; ++k)
-                if ((Zb[(long long)k * g.NW + chunk] >> lane) & 1u)
-                    r = fmaf(-D[(long long)k * g.P + p], W[(long long)k * g.N + i], r);
+            for (int k = 0; k < g.K; ++k) {
+                const float w = W[wblock(g, k / kAtomBlock, i) + k % kAtomBlock];
+                if (w != 0.0f) r = fmaf(-D[(long long)k * g.P + p], w, r);
+            }
             const long long w = (long long)p * g.NW + chunk;
             const int slot = Rbase[p] + (int)Ipre[w] + __popc(Ibits[w] & ((1u << lane) - 1u));
             R[slot] = r;
@@ -226,7 +227,7 @@ __global__ void export_codes_kernel(Geom g, const float* W, const uint32_t* Zb, 
     const int k = (int)(idx % g.K);
     const bool z = (Zb[(long long)k * g.NW + (i >> 5)] >> (i & 31)) & 1u;
     Z[idx] = z ? 1 : 0;
-    S[idx] = z ? W[(long long)k * g.N + i] : 0.0f;
+    S[idx] = z ? W[wblock(g, k / kAtomBlock, i) + k % kAtomBlock] : 0.0f;
 }
 
 // One thread per (atom, 32-patch word).
@@ -242,7 +243,7 @@ __global__ void import_codes_kernel(Geom g, const uint8_t* Z, const float* S, fl
         if (i >= g.N) break;
         const bool z = Z[i * g.K + k] != 0;
         if (z) bits |= 1u << b;
-        W[(long long)k * g.N + i] = z ? S[i * g.K + k] : 0.0f;
+        W[wblock(g, k / kAtomBlock, i) + k % kAtomBlock] = z ? S[i * g.K + k] : 0.0f;
     }
     Zb[idx] = bits;
 }

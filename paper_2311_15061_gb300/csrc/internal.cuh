@@ -32,7 +32,9 @@ struct Geom {
     int ndim;
     int P;                 // pixels per patch
     int K;                 // atoms
+    int KB;                // 8-atom blocks: ceil(K / 8)
     int NW;                // 32-patch words: ceil(N / 32)
+    long long Npad;        // NW * 32
     long long N;           // patches
     long long nframe;      // pixels per frame
     long long M[kMaxDim];  // frame shape
@@ -56,6 +58,17 @@ struct DevScalars {
     int status;        // sticky error word written by kernels (0 = ok)
 };
 
+// Weights are stored in 8-atom blocks per patch, [KB][Npad][8]: the eight
+// weights of patch i for atoms 8 kb .. 8 kb + 7 are one 32-byte sector, and a
+// warp's 32 patches of one block are 1 KB contiguous.  Inactive weights and
+// padding atoms (k >= K) are 0.
+constexpr int kAtomBlock = 8;
+
+__host__ __device__ __forceinline__ long long wblock(const Geom& g, int kb, long long i)
+{
+    return ((long long)kb * g.Npad + i) * kAtomBlock;
+}
+
 // Frame offset of patch i's first pixel.
 __host__ __device__ inline long long patch_origin(const Geom& g, long long i)
 {
@@ -74,11 +87,43 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k.y, (uint32_t)p0);
         k.x += 0x9E3779B9u;
         k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Philox4x32-10 key schedule (k0 + r W0, k1 + r W1 for rounds r = 0..9),
+// computed once on the host so the kernels read it from the constant bank.
+struct PhiloxKeys {
+    uint32_t k0[10];
+    uint32_t k1[10];
+};
+
+inline PhiloxKeys philox_round_keys(unsigned long long seed)
+{
+    PhiloxKeys r;
+    uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        r.k0[i] = a;
+        r.k1[i] = b;
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
+    return r;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& ks)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ ks.k0[round], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ ks.k1[round], (uint32_t)p0);
     }
     return c;
 }
@@ -102,32 +147,59 @@ __device__ __forceinline__ double normal64(uint32_t x0, uint32_t x1)
 // Box-Muller in FP32 (used for the code draws): sqrt(-2 ln u1) cos(2 pi u2)
 // with u = (x + 1) 2^-32, evaluated so that no FP32 rounding of the 32-bit
 // words is amplified:
-//  * ln u1 for u1 > 1/2 is log1p(-(1 - u1)), where 1 - u1 = (2^32-1 - x0) 2^-32
-//    is formed in integers (u1 near 1 would otherwise lose all its digits);
+//  * ln u1: for u1 <= 1/2 the hardware log2 (relative error ~2^-22 there);
+//    for u1 > 1/2, with v = 1 - u1 = (2^32-1 - x0) 2^-32 formed in integers,
+//    ln(1 - v) = -(v + v^2/2 + ... + v^8/8) when v < 1/8 (relative
+//    truncation error below 1e-8) and the hardware log2 of 1 - v otherwise
+//    (there |ln(1 - v)| >= 0.13);
 //  * the angle 2 pi (x1 + 1) / 2^32 is split in integers into the nearest
 //    multiple of pi/2 and a remainder d in [-2^29, 2^29), so the cosine is
-//    +-cospi or +-sinpi of d / 2^31 with |d / 2^31| <= 1/4: near the zeros of
-//    the cosine the result keeps full relative precision.
+//    +-cos or +-sin of t = pi d / 2^31 with |t| <= pi/4, evaluated by their
+//    Taylor series (to t^10 and t^9; remainders below 2e-9).
 __device__ __forceinline__ float normal32(uint32_t x0, uint32_t x1)
 {
     const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
+    const float ln2 = 0.69314718055994531f;
     float ln_u1;
-    if (x0 >= 0x80000000u)
-        ln_u1 = log1pf(-(float)(0xFFFFFFFFu - x0) * two_m32);
-    else
-        ln_u1 = logf(fmaf((float)x0, two_m32, two_m32));
-    const uint64_t y = (uint64_t)x1 + 1u;                 // angle = 2 pi y / 2^32
-    const uint32_t quarter = (uint32_t)((y + (1u << 29)) >> 30);   // nearest multiple of pi/2
-    const int32_t d = (int32_t)((int64_t)y - ((int64_t)quarter << 30));
-    const float f = (float)d * 4.656612873077393e-10f;    // d / 2^31, |f| <= 1/4
-    float c;
-    switch (quarter & 3u) {
-        case 0: c = cospif(f); break;
-        case 1: c = -sinpif(f); break;
-        case 2: c = -cospif(f); break;
-        default: c = sinpif(f); break;
+    if (x0 < 0x80000000u) {
+        ln_u1 = ln2 * __log2f(fmaf((float)x0, two_m32, two_m32));
+    } else {
+        const float v = (float)(0xFFFFFFFFu - x0) * two_m32;
+        if (v < 0.125f) {
+            // -(v + v^2/2 + ... + v^8/8), Horner form
+            float t = fmaf(v, 0.125f, 1.0f / 7.0f);
+            t = fmaf(v, t, 1.0f / 6.0f);
+            t = fmaf(v, t, 0.2f);
+            t = fmaf(v, t, 0.25f);
+            t = fmaf(v, t, 1.0f / 3.0f);
+            t = fmaf(v, t, 0.5f);
+            t = fmaf(v, t, 1.0f);
+            ln_u1 = -v * t;
+        } else {
+            ln_u1 = ln2 * __log2f(1.0f - v);
+        }
     }
-    return sqrtf(-2.0f * ln_u1) * c;
+    const uint64_t y = (uint64_t)x1 + 1u;                               // angle = 2 pi y / 2^32
+    const uint32_t quarter = (uint32_t)((y + (1u << 29)) >> 30);        // nearest multiple of pi/2
+    const int32_t d = (int32_t)((int64_t)y - ((int64_t)quarter << 30));
+    const float t = (float)d * 1.4629180792671596e-09f;                 // pi d / 2^31, |t| <= pi/4
+    const float t2 = t * t;
+    // sin t = t (1 - t^2/6 (1 - t^2/20 (1 - t^2/42 (1 - t^2/72))))
+    float sn = fmaf(-t2, 1.0f / 72.0f, 1.0f);
+    sn = fmaf(-t2 * (1.0f / 42.0f), sn, 1.0f);
+    sn = fmaf(-t2 * (1.0f / 20.0f), sn, 1.0f);
+    sn = fmaf(-t2 * (1.0f / 6.0f), sn, 1.0f);
+    sn *= t;
+    // cos t = 1 - t^2/2 (1 - t^2/12 (1 - t^2/30 (1 - t^2/56 (1 - t^2/90))))
+    float cs = fmaf(-t2, 1.0f / 90.0f, 1.0f);
+    cs = fmaf(-t2 * (1.0f / 56.0f), cs, 1.0f);
+    cs = fmaf(-t2 * (1.0f / 30.0f), cs, 1.0f);
+    cs = fmaf(-t2 * (1.0f / 12.0f), cs, 1.0f);
+    cs = fmaf(-t2 * 0.5f, cs, 1.0f);
+    const float c = (quarter & 1u) ? sn : cs;
+    const float sign = ((quarter + 1u) & 2u) ? -1.0f : 1.0f;   // quarters 1, 2 negative
+    const float m = -2.0f * ln_u1;
+    return sign * c * (m * rsqrtf(fmaxf(m, 1e-30f)));
 }
 
 // Marsaglia-Tsang for shape >= 1; attempt a uses block (c0, c1, t, tag | a << 8):
@@ -205,8 +277,8 @@ struct SweepArgs {
     const uint16_t* nobs;      // [N] observed pixels per patch
     const int* imgoff;         // [P] frame offset of within-patch pixel p
     const float* D;            // [K][P]
-    float* W;                  // [K][N] weights (0 where inactive)
-    uint32_t* Zb;              // [K][NW] activity bits
+    float* W;                  // [KB][Npad][8] weights (0 where inactive)
+    uint32_t* Zb;              // [K][NW] activity bits (written)
     const float* lpi;          // [K] logit(pi_k)
     const DevScalars* sc;
     const uint32_t* Ibits;     // [P][NW] bit i: patch i observes pixel p
@@ -218,17 +290,15 @@ struct SweepArgs {
     double* part_r2;           // [NW] per 32-patch chunk
     unsigned int* chunk_counter;  // work counter, zeroed before each launch
     DevScalars* sc_out;           // change counters (same object as sc)
-    unsigned long long seed;
+    PhiloxKeys keys;              // round keys of the seed
     uint32_t t;
 };
 
 struct DictArgs {
     Geom g;
     float* D;                  // [K][P]
-    const float* W;            // [K][N]
-    const uint32_t* Zb;        // [K][NW]
-    const uint32_t* Ibits;     // [P][NW]
-    const uint32_t* Ipre;      // [P][NW]
+    const float* W;            // [KB][Npad][8]
+    const int* Ilist;          // per pixel p: the patches observing p, in slot order
     const int* Rbase;          // [P + 1]
     float* R;
     const DevScalars* sc;
@@ -267,6 +337,8 @@ cudaError_t launch_geometry(const Geom& g, const uint8_t* mask_bytes, uint32_t* 
                             uint16_t* nobs, int* maxobs, cudaStream_t s);
 cudaError_t launch_slots(const Geom& g, const uint32_t* mask_bits, const int* imgoff, uint16_t* obs,
                          uint32_t* Ibits, uint32_t* Ipre, int* Icnt, int* Rbase, int* max_slots, cudaStream_t s);
+cudaError_t launch_ilist(const Geom& g, const uint32_t* Ibits, const uint32_t* Ipre, const int* Rbase, int* Ilist,
+                         cudaStream_t s);
 cudaError_t launch_overlap_counts(const Geom& g, int* counts, cudaStream_t s);
 cudaError_t launch_reconstruct(const Geom& g, const float* D, const float* W, const uint32_t* Zb, float* Y,
                                float* out, cudaStream_t s);

@@ -14,7 +14,10 @@
 // GB300 mapping: one thread owns one patch; a warp owns 32 consecutive,
 // 32-aligned patches so the atom's activity bits of the warp form one 32-bit
 // word (ballot).  Warps pull 32-patch chunks from a global counter, so the
-// tail of the grid is a single chunk per warp.  The dictionary sits in shared
+// tail of the grid is a single chunk per warp.  Weights are read and written
+// in 8-atom blocks (two 16-byte accesses per lane, 1 KB per warp), the next
+// block prefetched behind the current one, so no global load sits on the
+// per-atom path; per-warp counters replace any block-wide barrier.  The dictionary sits in shared
 // memory as [p][k] with an odd row pitch plus one zero row (p = P) that padded
 // observation slots point at, so the inner loops need no predicates.  The
 // residual of the patch lives in registers (MAXOBS slots, chosen per problem
@@ -27,37 +30,38 @@
 namespace sensai {
 
 constexpr int kSweepThreads = 256;
+constexpr int kSweepWarps = kSweepThreads / 32;
 
 template <int MAXOBS>
 __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_kernel(const SweepArgs a)
 {
     extern __shared__ float smem[];
-    const int K = a.g.K, P = a.g.P;
-    const int ldK = K | 1;
-    const long long N = a.g.N;
+    const int K = a.g.K, P = a.g.P, KB = a.g.KB;
+    const int Kpad = KB * kAtomBlock;
+    const int ldK = Kpad | 1;
+    const long long N = a.g.N, Npad = a.g.Npad;
     const int NW = a.g.NW;
-    float* Ds = smem;                      // (P + 1) x ldK, row P is zero
-    float* lpi = Ds + (P + 1) * ldK;       // K
-    int* cnt = (int*)(lpi + K);            // K
-    __shared__ unsigned int chunk_slot[kSweepThreads / 32];
+    float* Ds = smem;                      // (P + 1) x ldK; row P and atoms >= K are zero
+    float* lpi = Ds + (P + 1) * ldK;       // Kpad
+    int* cntw = (int*)(lpi + Kpad);        // [warp][Kpad] active counts of this warp
+    __shared__ unsigned int chunk_slot[kSweepWarps];
 
     for (int idx = threadIdx.x; idx < (P + 1) * ldK; idx += blockDim.x) {
         const int p = idx / ldK, k = idx - p * ldK;
         Ds[idx] = (p < P && k < K) ? a.D[(long long)k * P + p] : 0.0f;
     }
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        lpi[k] = a.lpi[k];
-        cnt[k] = 0;
-    }
+    for (int k = threadIdx.x; k < Kpad; k += blockDim.x) lpi[k] = k < K ? a.lpi[k] : 0.0f;
+    for (int idx = threadIdx.x; idx < kSweepWarps * Kpad; idx += blockDim.x) cntw[idx] = 0;
     __syncthreads();
 
     const float gs = (float)a.sc->gamma_s;
     const float ge = (float)a.sc->gamma_eps;
     const float half_log_gs = 0.5f * logf(gs);
     const float half_ge2 = 0.5f * ge * ge;
-    const uint2 key = seed_key(a.seed);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned int nchunks = (unsigned int)NW;
+    int* mycnt = cntw + warp * Kpad;
+    const float4* Wr = reinterpret_cast<const float4*>(a.W);
+    float4* Ww = reinterpret_cast<float4*>(a.W);
     unsigned int chg_n = 0, chg_obs = 0, act_n = 0;
 
     for (;;) {
@@ -65,8 +69,8 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
         __syncwarp();
         const unsigned int chunk = chunk_slot[warp];
         __syncwarp();
-        if (chunk >= nchunks) break;
-        const long long i = (long long)chunk * 32 + lane;
+        if (chunk >= (unsigned int)NW) break;
+        const long long i = (long long)chunk * 32 + lane;   // < Npad: weight blocks exist
         const bool valid = i < N;
 
         const int nobs = valid ? (int)a.nobs[i] : 0;
@@ -88,63 +92,85 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
         }
 
         // residual r = x - D w on the observed pixels, from the stored weights
-        for (int k = 0; k < K; ++k) {
-            const uint32_t zw = a.Zb[(long long)k * NW + chunk];
-            if ((zw >> lane) & 1u) {
-                const float w = a.W[(long long)k * N + i];
-                const float* dk = Ds + k;
+        for (int kb = 0; kb < KB; ++kb) {
+            const float4* q = Wr + ((long long)kb * Npad + i) * 2;
+            const float4 u0 = q[0], u1 = q[1];
+            const float wv[kAtomBlock] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
 #pragma unroll
-                for (int j = 0; j < MAXOBS; ++j) {
-                    if (j >= wmax) break;
-                    r[j] = fmaf(-dk[offK[j]], w, r[j]);
+            for (int kk = 0; kk < kAtomBlock; ++kk) {
+                if (wv[kk] != 0.0f) {
+                    const float* dk = Ds + kb * kAtomBlock + kk;
+#pragma unroll
+                    for (int j = 0; j < MAXOBS; ++j) {
+                        if ((j & 3) == 0 && j >= wmax) break;
+                        r[j] = fmaf(-dk[offK[j]], wv[kk], r[j]);
+                    }
                 }
             }
         }
 
         float s2 = 0.0f;
-        for (int k = 0; k < K; ++k) {
-            const float* dk = Ds + k;
-            float n = 0.0f, h = 0.0f;
-#pragma unroll
-            for (int j = 0; j < MAXOBS; ++j) {
-                if (j >= wmax) break;
-                const float d = dk[offK[j]];
-                n = fmaf(d, d, n);
-                h = fmaf(d, r[j], h);
+        float4 n0 = Wr[(long long)i * 2], n1 = Wr[(long long)i * 2 + 1];
+        for (int kb = 0; kb < KB; ++kb) {
+            // the block's weights rotate through w0..w7: each atom consumes w0
+            // and appends its new weight, so after 8 atoms they are in order
+            float w0 = n0.x, w1 = n0.y, w2 = n0.z, w3 = n0.w, w4 = n1.x, w5 = n1.y, w6 = n1.z, w7 = n1.w;
+            if (kb + 1 < KB) {   // prefetch the next block behind this block's work
+                const float4* q = Wr + ((long long)(kb + 1) * Npad + i) * 2;
+                n0 = q[0];
+                n1 = q[1];
             }
-            const uint32_t zw = a.Zb[(long long)k * NW + chunk];
-            const bool zold = (zw >> lane) & 1u;
-            const float w_old = zold ? a.W[(long long)k * N + i] : 0.0f;
-            const float g = fmaf(w_old, n, h);
-            const float lam = fmaf(ge, n, gs);
-            const float rlam = __frcp_rn(lam);
-            const float L = lpi[k] + half_log_gs - 0.5f * __logf(lam) + half_ge2 * g * g * rlam;
-            const float sig = __frcp_rn(1.0f + __expf(-L));
-            const unsigned long long thr = (unsigned long long)(sig * 4294967296.0f);
-            const uint4 blk = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)k, a.t, kTagCodes), key);
-            const bool z = valid && ((unsigned long long)blk.x < thr);
-            float w_new = 0.0f;
-            if (z) {
-                w_new = fmaf(normal32(blk.y, blk.z), sqrtf(rlam), ge * g * rlam);
-                s2 = fmaf(w_new, w_new, s2);
-                act_n += 1;
-            }
-            const float dw = w_new - w_old;
-            if (dw != 0.0f) {
-                chg_n += 1;
-                chg_obs += (unsigned int)nobs;
+            const int kend = min(kAtomBlock, K - kb * kAtomBlock);
+#pragma unroll 1
+            for (int kk = 0; kk < kAtomBlock; ++kk) {
+                const int k = kb * kAtomBlock + kk;
+                float w_new = w0;   // padding atoms keep their zero
+                if (kk < kend) {
+                    const float* dk = Ds + k;
+                    float n = 0.0f, h = 0.0f;
 #pragma unroll
-                for (int j = 0; j < MAXOBS; ++j) {
-                    if (j >= wmax) break;
-                    r[j] = fmaf(-dk[offK[j]], dw, r[j]);
+                    for (int j = 0; j < MAXOBS; ++j) {
+                        if ((j & 3) == 0 && j >= wmax) break;
+                        const float d = dk[offK[j]];
+                        n = fmaf(d, d, n);
+                        h = fmaf(d, r[j], h);
+                    }
+                    const float w_old = w0;
+                    const float g = fmaf(w_old, n, h);
+                    const float lam = fmaf(ge, n, gs);
+                    const float rlam = __fdividef(1.0f, lam);
+                    const float L = lpi[k] + half_log_gs - 0.5f * __logf(lam) + half_ge2 * g * g * rlam;
+                    const float sig = __fdividef(1.0f, 1.0f + __expf(-L));
+                    const unsigned long long thr = (unsigned long long)(sig * 4294967296.0f);
+                    const uint4 blk = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)k, a.t, kTagCodes), a.keys);
+                    const bool z = valid && ((unsigned long long)blk.x < thr);
+                    w_new = 0.0f;
+                    if (z) {
+                        w_new = fmaf(normal32(blk.y, blk.z), sqrtf(rlam), ge * g * rlam);
+                        s2 = fmaf(w_new, w_new, s2);
+                        act_n += 1;
+                    }
+                    const float dw = w_new - w_old;
+                    if (dw != 0.0f) {
+                        chg_n += 1;
+                        chg_obs += (unsigned int)nobs;
+#pragma unroll
+                        for (int j = 0; j < MAXOBS; ++j) {
+                            if ((j & 3) == 0 && j >= wmax) break;
+                            r[j] = fmaf(-dk[offK[j]], dw, r[j]);
+                        }
+                    }
+                    const uint32_t bal = __ballot_sync(0xffffffffu, z);
+                    if (lane == 0) {
+                        a.Zb[(long long)k * NW + chunk] = bal;
+                        mycnt[k] += __popc(bal);
+                    }
                 }
+                w0 = w1; w1 = w2; w2 = w3; w3 = w4; w4 = w5; w5 = w6; w6 = w7; w7 = w_new;
             }
-            const uint32_t bal = __ballot_sync(0xffffffffu, z);
-            if (lane == 0) {
-                a.Zb[(long long)k * NW + chunk] = bal;
-                if (bal) atomicAdd(&cnt[k], __popc(bal));
-            }
-            if (z || zold) a.W[(long long)k * N + i] = w_new;
+            float4* q = Ww + ((long long)kb * Npad + i) * 2;
+            q[0] = make_float4(w0, w1, w2, w3);
+            q[1] = make_float4(w4, w5, w6, w7);
         }
 
         // scatter the residual to the per-pixel slots; squared norm
@@ -154,9 +180,9 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
             if (j >= wmax) break;
             if (j < nobs) {
                 const int p = a.obs[(long long)j * N + i];
-                const long long w = (long long)p * NW + chunk;
-                const uint32_t ib = a.Ibits[w];
-                const int slot = a.Rbase[p] + (int)a.Ipre[w] + __popc(ib & ((1u << lane) - 1u));
+                const long long wd = (long long)p * NW + chunk;
+                const uint32_t ib = a.Ibits[wd];
+                const int slot = a.Rbase[p] + (int)a.Ipre[wd] + __popc(ib & ((1u << lane) - 1u));
                 a.R[slot] = r[j];
                 r2 = fmaf(r[j], r[j], r2);
             }
@@ -168,6 +194,10 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
             a.part_r2[chunk] = r2d;
         }
     }
+    // this warp's counts: per-atom actives and the work counters
+    __syncwarp();
+    for (int k = lane; k < K; k += 32)
+        if (mycnt[k]) atomicAdd(&a.m[k], mycnt[k]);
     unsigned long long cn = chg_n, co = chg_obs, ca = act_n;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -180,17 +210,15 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
         atomicAdd(&a.sc_out->chg_obs, co);
         atomicAdd(&a.sc_out->act_n, ca);
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < K; k += blockDim.x)
-        if (cnt[k]) atomicAdd(&a.m[k], cnt[k]);
 }
 
 int sweep_block_size() { return kSweepThreads; }
 
 int sweep_smem_bytes(const Geom& g)
 {
-    const int ldK = g.K | 1;
-    return (int)(sizeof(float) * ((size_t)(g.P + 1) * ldK + g.K) + sizeof(int) * g.K);
+    const int Kpad = g.KB * kAtomBlock;
+    const int ldK = Kpad | 1;
+    return (int)(sizeof(float) * ((size_t)(g.P + 1) * ldK + Kpad) + sizeof(int) * (size_t)kSweepWarps * Kpad);
 }
 
 template <int MAXOBS>
