@@ -59,7 +59,6 @@ __global__ void __launch_bounds__(kDictThreads, 1) dict_kernel(const DictArgs a)
     __syncthreads();
 
     const double ge = a.sc->gamma_eps;
-    const float4* Wv = reinterpret_cast<const float4*>(a.W);
     float dprev[kAtomBlock];
 #pragma unroll
     for (int kk = 0; kk < kAtomBlock; ++kk) dprev[kk] = 0.0f;
@@ -70,55 +69,51 @@ __global__ void __launch_bounds__(kDictThreads, 1) dict_kernel(const DictArgs a)
         for (int v = 0; v < kAtomBlock; ++v) G[v] = 0.0f;
 #pragma unroll
         for (int v = 0; v < kGram; ++v) C[v] = 0.0f;
-        // two-deep software pipeline over this thread's slots: the next slot's
-        // weights are in flight while the current one is applied
-        const float4* qprev = Wv + (long long)(kb > 0 ? kb - 1 : 0) * Npad * 2;
-        const float4* qcur = Wv + (long long)kb * Npad * 2;
+        // Two register sets (A, B) alternate over this thread's slots: the
+        // loads of one slot are issued before the other slot is computed and
+        // no pending load is ever copied, so two slots are always in flight.
+        const float* qprev = a.W + (long long)(kb > 0 ? kb - 1 : 0) * Npad * kAtomBlock;
+        const float* qcur = a.W + (long long)kb * Npad * kAtomBlock;
         const bool has_prev = kb > 0, has_cur = kb < KB;
-        const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const int stride = blockDim.x;
+        float ra = 0.0f, rb = 0.0f;
+        W8 ua, va, ub, vb;
+#define DICT_LOAD(S_, R_, U, V)                                             \
+        do {                                                                \
+            const long long i_ = ilist[S_];                                 \
+            R_ = rho[S_];                                                   \
+            if (has_prev) U = load_w8(qprev + i_ * kAtomBlock);             \
+            if (has_cur) V = load_w8(qcur + i_ * kAtomBlock);               \
+        } while (0)
+#define DICT_APPLY(S_, R_, U, V)                                            \
+        do {                                                                \
+            if (has_prev) {                                                 \
+                _Pragma("unroll") for (int k = 0; k < kAtomBlock; ++k)      \
+                    R_ = fmaf(-dprev[k], U.v[k], R_);                       \
+                rho[S_] = R_;                                               \
+            }                                                               \
+            if (has_cur) {                                                  \
+                _Pragma("unroll") for (int k = 0; k < kAtomBlock; ++k) {    \
+                    G[k] = fmaf(V.v[k], R_, G[k]);                          \
+                    _Pragma("unroll") for (int l = 0; l <= k; ++l)          \
+                        C[k * (k + 1) / 2 + l] = fmaf(V.v[k], V.v[l], C[k * (k + 1) / 2 + l]); \
+                }                                                           \
+            }                                                               \
+        } while (0)
         int s = threadIdx.x;
-        float rr = 0.0f;
-        float4 u0 = zero4, u1 = zero4, v0 = zero4, v1 = zero4;
-        if (s < cnt) {
-            const long long i = ilist[s];
-            rr = rho[s];
-            if (has_prev) { u0 = qprev[i * 2]; u1 = qprev[i * 2 + 1]; }
-            if (has_cur) { v0 = qcur[i * 2]; v1 = qcur[i * 2 + 1]; }
-        }
+        if (s < cnt) DICT_LOAD(s, ra, ua, va);
         while (s < cnt) {
-            const int sn = s + blockDim.x;
-            float rn = 0.0f;
-            float4 nu0 = zero4, nu1 = zero4, nv0 = zero4, nv1 = zero4;
-            if (sn < cnt) {
-                const long long i = ilist[sn];
-                rn = rho[sn];
-                if (has_prev) { nu0 = qprev[i * 2]; nu1 = qprev[i * 2 + 1]; }
-                if (has_cur) { nv0 = qcur[i * 2]; nv1 = qcur[i * 2 + 1]; }
-            }
-            if (has_prev) {
-                rr = fmaf(-dprev[0], u0.x, rr);
-                rr = fmaf(-dprev[1], u0.y, rr);
-                rr = fmaf(-dprev[2], u0.z, rr);
-                rr = fmaf(-dprev[3], u0.w, rr);
-                rr = fmaf(-dprev[4], u1.x, rr);
-                rr = fmaf(-dprev[5], u1.y, rr);
-                rr = fmaf(-dprev[6], u1.z, rr);
-                rr = fmaf(-dprev[7], u1.w, rr);
-                rho[s] = rr;
-            }
-            if (has_cur) {
-                const float w[kAtomBlock] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-#pragma unroll
-                for (int k = 0; k < kAtomBlock; ++k) {
-                    G[k] = fmaf(w[k], rr, G[k]);
-#pragma unroll
-                    for (int l = 0; l <= k; ++l) C[k * (k + 1) / 2 + l] = fmaf(w[k], w[l], C[k * (k + 1) / 2 + l]);
-                }
-            }
-            s = sn;
-            rr = rn;
-            u0 = nu0; u1 = nu1; v0 = nv0; v1 = nv1;
+            const int sb = s + stride;
+            if (sb < cnt) DICT_LOAD(sb, rb, ub, vb);
+            DICT_APPLY(s, ra, ua, va);
+            if (sb >= cnt) break;
+            const int sa = sb + stride;
+            if (sa < cnt) DICT_LOAD(sa, ra, ua, va);
+            DICT_APPLY(sb, rb, ub, vb);
+            s = sa;
         }
+#undef DICT_LOAD
+#undef DICT_APPLY
         if (kb == KB) break;
 #pragma unroll
         for (int v = 0; v < kRed; ++v) {

@@ -69,6 +69,30 @@ __host__ __device__ __forceinline__ long long wblock(const Geom& g, int kb, long
     return ((long long)kb * g.Npad + i) * kAtomBlock;
 }
 
+// One 32-byte weight record as a single 256-bit access (address 32-byte
+// aligned): one L1 wavefront per lane instead of two.
+struct W8 {
+    float v[kAtomBlock];
+};
+
+__device__ __forceinline__ W8 load_w8(const float* p)
+{
+    W8 r;
+    asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]),
+                   "=f"(r.v[4]), "=f"(r.v[5]), "=f"(r.v[6]), "=f"(r.v[7])
+                 : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ void store_w8(float* p, float a0, float a1, float a2, float a3, float a4, float a5,
+                                         float a6, float a7)
+{
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 :: "l"(p), "f"(a0), "f"(a1), "f"(a2), "f"(a3), "f"(a4), "f"(a5), "f"(a6), "f"(a7)
+                 : "memory");
+}
+
 // Frame offset of patch i's first pixel.
 __host__ __device__ inline long long patch_origin(const Geom& g, long long i)
 {

@@ -60,8 +60,6 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
     const float half_ge2 = 0.5f * ge * ge;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* mycnt = cntw + warp * Kpad;
-    const float4* Wr = reinterpret_cast<const float4*>(a.W);
-    float4* Ww = reinterpret_cast<float4*>(a.W);
     unsigned int chg_n = 0, chg_obs = 0, act_n = 0;
 
     for (;;) {
@@ -93,9 +91,8 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
 
         // residual r = x - D w on the observed pixels, from the stored weights
         for (int kb = 0; kb < KB; ++kb) {
-            const float4* q = Wr + ((long long)kb * Npad + i) * 2;
-            const float4 u0 = q[0], u1 = q[1];
-            const float wv[kAtomBlock] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+            const W8 wb = load_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock);
+            const float* wv = wb.v;
 #pragma unroll
             for (int kk = 0; kk < kAtomBlock; ++kk) {
                 if (wv[kk] != 0.0f) {
@@ -110,16 +107,14 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
         }
 
         float s2 = 0.0f;
-        float4 n0 = Wr[(long long)i * 2], n1 = Wr[(long long)i * 2 + 1];
+        W8 nb = load_w8(a.W + (long long)i * kAtomBlock);
         for (int kb = 0; kb < KB; ++kb) {
             // the block's weights rotate through w0..w7: each atom consumes w0
             // and appends its new weight, so after 8 atoms they are in order
-            float w0 = n0.x, w1 = n0.y, w2 = n0.z, w3 = n0.w, w4 = n1.x, w5 = n1.y, w6 = n1.z, w7 = n1.w;
-            if (kb + 1 < KB) {   // prefetch the next block behind this block's work
-                const float4* q = Wr + ((long long)(kb + 1) * Npad + i) * 2;
-                n0 = q[0];
-                n1 = q[1];
-            }
+            float w0 = nb.v[0], w1 = nb.v[1], w2 = nb.v[2], w3 = nb.v[3];
+            float w4 = nb.v[4], w5 = nb.v[5], w6 = nb.v[6], w7 = nb.v[7];
+            if (kb + 1 < KB)   // prefetch the next block behind this block's work
+                nb = load_w8(a.W + ((long long)(kb + 1) * Npad + i) * kAtomBlock);
             const int kend = min(kAtomBlock, K - kb * kAtomBlock);
 #pragma unroll 1
             for (int kk = 0; kk < kAtomBlock; ++kk) {
@@ -168,9 +163,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
                 }
                 w0 = w1; w1 = w2; w2 = w3; w3 = w4; w4 = w5; w5 = w6; w6 = w7; w7 = w_new;
             }
-            float4* q = Ww + ((long long)kb * Npad + i) * 2;
-            q[0] = make_float4(w0, w1, w2, w3);
-            q[1] = make_float4(w4, w5, w6, w7);
+            store_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock, w0, w1, w2, w3, w4, w5, w6, w7);
         }
 
         // scatter the residual to the per-pixel slots; squared norm
