@@ -81,6 +81,16 @@ struct sensai_ctx {
     double* part_r2 = nullptr;
     unsigned int* chunk_counter = nullptr;
     DevScalars* sc = nullptr;
+    // space-tiled dictionary sweep (cooperative launch), when it fits
+    int* obs_px = nullptr;      // observed frame pixels in raster order
+    long long n_obs_px = 0;
+    float* dpart = nullptr;     // [grid][44][P]
+    float* ddelta = nullptr;    // [P][8]
+    unsigned int* dbar = nullptr;
+    int ds_grid = 0;
+    int ds_tile = 0;
+    int ds_own = 0;
+    size_t ds_smem = 0;
 };
 
 namespace {
@@ -120,7 +130,7 @@ void free_all(sensai_ctx* c)
 {
     void* ptrs[] = {c->mask_bits, c->imgoff, c->nobs, c->obs, c->Ibits, c->Ipre, c->Icnt, c->Rbase, c->Ilist,
                     c->misc, c->x, c->D, c->W, c->Zb, c->R, c->Y, c->out, c->pi, c->lpi, c->m,
-                    c->part_s2, c->part_r2, c->chunk_counter, c->sc};
+                    c->part_s2, c->part_r2, c->chunk_counter, c->sc, c->obs_px, c->dpart, c->ddelta, c->dbar};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -261,6 +271,33 @@ sensai_status run_dictionary(sensai_ctx* ctx, cudaStream_t s)
     if (st != SENSAI_OK) return st;
     st = ensure_residual(ctx, s);
     if (st != SENSAI_OK) return st;
+    if (ctx->ds_grid > 0) {
+        DictSpaceArgs a{};
+        a.g = ctx->g;
+        a.D = ctx->D;
+        a.W = ctx->W;
+        a.Ibits = ctx->Ibits;
+        a.Ipre = ctx->Ipre;
+        a.Rbase = ctx->Rbase;
+        a.R = ctx->R;
+        a.sc = ctx->sc;
+        a.part_r2 = ctx->part_r2;
+        a.part = ctx->dpart;
+        a.delta = ctx->ddelta;
+        a.bar = ctx->dbar;
+        a.obs_px = ctx->obs_px;
+        a.n_obs_px = ctx->n_obs_px;
+        a.max_tile = ctx->ds_tile;
+        a.own_max = ctx->ds_own;
+        a.seed = ctx->prm.seed;
+        a.t = (uint32_t)ctx->t;
+        PhaseTimer timer(ctx, kPhaseDict, s);
+        SENSAI_CUDA(ctx, launch_dict_space(a, ctx->ds_grid, ctx->ds_smem, s));
+        timer.stop();
+        ctx->launches += 1;
+        ctx->n_r2 = ctx->ds_grid;
+        return SENSAI_OK;
+    }
     DictArgs a{};
     a.g = ctx->g;
     a.D = ctx->D;
@@ -471,9 +508,41 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     CREATE_CUDA(dalloc(&ctx->lpi, (size_t)g.K));
     CREATE_CUDA(dalloc(&ctx->m, (size_t)g.K));
     CREATE_CUDA(dalloc(&ctx->part_s2, (size_t)g.NW));
-    CREATE_CUDA(dalloc(&ctx->part_r2, (size_t)(g.NW > P ? g.NW : P)));
+    int sms = 0;
+    CREATE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    {
+        size_t n = (size_t)(g.NW > P ? g.NW : P);
+        if (n < (size_t)sms) n = (size_t)sms;
+        CREATE_CUDA(dalloc(&ctx->part_r2, n));
+    }
     CREATE_CUDA(dalloc(&ctx->chunk_counter, 1));
     CREATE_CUDA(dalloc(&ctx->sc, 1));
+    // space-tiled dictionary sweep: observed pixels, per-CTA sums, barrier
+    {
+        int nobs_px = 0;
+        CREATE_CUDA(dalloc(&ctx->obs_px, (size_t)nframe));
+        CREATE_CUDA(launch_obs_px(nframe, ctx->mask_bits, ctx->obs_px, st0));
+        ctx->launches += 1;
+        CREATE_CUDA(cudaDeviceSynchronize());
+        // count = number of observed pixels (host copy of the mask is the source)
+        for (long long u = 0; u < nframe; ++u) nobs_px += mask[u] != 0;
+        ctx->n_obs_px = nobs_px;
+        const int grid = sms;
+        const int tile = (int)((nobs_px + grid - 1) / grid) + 1;
+        const int own = (int)((P + grid - 1) / grid);
+        const size_t smem = dict_space_smem_bytes(g, tile, tile * (int)P, own);
+        const int ds = (nobs_px > 0) ? dict_space_grid(g, smem, device) : 0;
+        if (ds > 0) {
+            CREATE_CUDA(dalloc(&ctx->dpart, (size_t)ds * 44 * P));
+            CREATE_CUDA(dalloc(&ctx->ddelta, (size_t)P * 8));
+            CREATE_CUDA(dalloc(&ctx->dbar, 2));
+            CREATE_CUDA(cudaMemset(ctx->dbar, 0, 2 * sizeof(unsigned int)));
+            ctx->ds_grid = ds;
+            ctx->ds_tile = tile;
+            ctx->ds_smem = smem;
+            ctx->ds_own = own;
+        }
+    }
     ctx->sweep_grid = sweep_grid_size(g, ctx->maxobs, device);
     if (ctx->sweep_grid < 1) {
         fail(SENSAI_ECUDA, "no launch configuration for the code sweep (max observed %d)", ctx->maxobs);
@@ -742,6 +811,7 @@ sensai_status sensai_get_stats(sensai_ctx* ctx, sensai_stats* stats)
     stats->gamma_s = sc.gamma_s;
     stats->gamma_eps = ctx->ge_set ? sc.gamma_eps : 0.0;
     stats->kernel_launches = ctx->launches;
+    if (sc.status != 0) return fail(SENSAI_ETIMEOUT, "a device-side wait timed out (status %d)", sc.status);
     stats->changed_updates = (int64_t)sc.chg_n;
     stats->changed_observed = (int64_t)sc.chg_obs;
     stats->active_draws = (int64_t)sc.act_n;

@@ -201,6 +201,55 @@ __global__ void ola_gather_kernel(Geom g, const float* Y, float* out)
     out[u] = acc / (float)count;
 }
 
+// Observed frame pixels in raster order (one CTA, chunked block scan).
+__global__ void __launch_bounds__(1024) obs_px_kernel(long long nframe, const uint32_t* mbits, int* obs_px)
+{
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long nmw = (nframe + 31) / 32;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long base = 0; base < nmw; base += blockDim.x) {
+        const long long w = base + threadIdx.x;
+        uint32_t bits = 0u;
+        if (w < nmw) {
+            bits = mbits[w];
+            const long long rem = nframe - w * 32;
+            if (rem < 32) bits &= (1u << rem) - 1u;
+        }
+        const int v = __popc(bits);
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int n = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += n;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = blockDim.x >> 5;
+            int tt = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int n = __shfl_up_sync(0xffffffffu, tt, o);
+                if (lane >= o) tt += n;
+            }
+            if (lane < nw) warp_tot[lane] = tt;
+        }
+        __syncthreads();
+        int pos = carry + (warp > 0 ? warp_tot[warp - 1] : 0) + incl - v;
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1u;
+            obs_px[pos++] = (int)(w * 32 + b);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_tot[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+}
+
 // Slot -> patch list of every pixel p: Ilist[Rbase[p] + rank] = the patches
 // observing p in increasing index (one thread per (word, pixel)).
 __global__ void ilist_kernel(Geom g, const uint32_t* Ibits, const uint32_t* Ipre, const int* Rbase, int* Ilist)
@@ -288,6 +337,12 @@ cudaError_t launch_ilist(const Geom& g, const uint32_t* Ibits, const uint32_t* I
                          cudaStream_t s)
 {
     ilist_kernel<<<dim3(blocks_for(g.NW, 256), g.P), 256, 0, s>>>(g, Ibits, Ipre, Rbase, Ilist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_obs_px(long long nframe, const uint32_t* mbits, int* obs_px, cudaStream_t s)
+{
+    obs_px_kernel<<<1, 1024, 0, s>>>(nframe, mbits, obs_px);
     return cudaGetLastError();
 }
 

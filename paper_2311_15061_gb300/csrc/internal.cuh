@@ -75,10 +75,12 @@ struct W8 {
     float v[kAtomBlock];
 };
 
+// Not volatile: the compiler may schedule these loads early (stores of the
+// same array carry a memory clobber, so no load moves across them).
 __device__ __forceinline__ W8 load_w8(const float* p)
 {
     W8 r;
-    asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+    asm("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                  : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]),
                    "=f"(r.v[4]), "=f"(r.v[5]), "=f"(r.v[6]), "=f"(r.v[7])
                  : "l"(p));
@@ -331,6 +333,27 @@ struct DictArgs {
     uint32_t t;
 };
 
+struct DictSpaceArgs {
+    Geom g;
+    float* D;                  // [K][P]
+    const float* W;            // [KB][Npad][8]
+    const uint32_t* Ibits;     // [P][NW]
+    const uint32_t* Ipre;      // [P][NW]
+    const int* Rbase;          // [P + 1]
+    float* R;                  // residual slots
+    DevScalars* sc;            // gamma_eps in, status out
+    double* part_r2;           // [gridDim.x]
+    float* part;               // [gridDim.x][44][P] per-CTA block sums
+    float* delta;              // [P][8] the block's updates
+    unsigned int* bar;         // grid barrier (count, generation)
+    const int* obs_px;         // observed frame pixels in raster order
+    long long n_obs_px;
+    int max_tile;              // ceil(n_obs_px / gridDim.x)
+    int own_max;               // chains per CTA: ceil(P / gridDim.x)
+    unsigned long long seed;
+    uint32_t t;
+};
+
 struct HyperArgs {
     Geom g;
     const int* m;              // [K]
@@ -357,6 +380,10 @@ int sweep_smem_bytes(const Geom& g);
 int sweep_grid_size(const Geom& g, int maxobs, int device);
 cudaError_t launch_dict(const DictArgs& a, int max_slots, cudaStream_t s);
 cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);
+size_t dict_space_smem_bytes(const Geom& g, int max_tile, int max_pairs, int own_max);
+int dict_space_grid(const Geom& g, size_t smem, int device);
+cudaError_t launch_dict_space(const DictSpaceArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_obs_px(long long nframe, const uint32_t* mbits, int* obs_px, cudaStream_t s);
 cudaError_t launch_geometry(const Geom& g, const uint8_t* mask_bytes, uint32_t* mask_bits, int* imgoff,
                             uint16_t* nobs, int* maxobs, cudaStream_t s);
 cudaError_t launch_slots(const Geom& g, const uint32_t* mask_bits, const int* imgoff, uint16_t* obs,
