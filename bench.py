@@ -281,6 +281,8 @@ def run_gpu(args):
         "wall_s": wall,
         "clocks": clocks.summary(),
     }
+    if not args.no_serving:
+        line["serving"] = run_serving(ctx)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     ctx.close()
@@ -288,6 +290,97 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+SERVE = dict(frames=300, sizes=((256, 256), (512, 512), (1024, 1024)), streams=4, rate_hz=20.0,
+             frac=(0.05, 0.20), sweeps=3, slots=8, saturated_1024=32, seed=7)
+
+
+def _serving_requests(cfg):
+    """The live-feed workload: frames of mixed sizes from a drifting-lattice
+    pool, each with its own random or line-hop mask (5-20%), arriving as four
+    Poisson streams."""
+    from paper_2311_15061_gb300 import synth
+    rng = np.random.default_rng(cfg["seed"])
+    pool = {shp: [synth.stem_frame(shp, cfg["seed"] + j, drift=(0.0, 0.3 * j))[0] for j in range(3)]
+            for shp in cfg["sizes"]}
+    reqs = []
+    t_stream = np.zeros(cfg["streams"])
+    for n in range(cfg["frames"]):
+        sid = n % cfg["streams"]
+        t_stream[sid] += rng.exponential(1.0 / cfg["rate_hz"])
+        shp = cfg["sizes"][int(rng.integers(0, len(cfg["sizes"])))]
+        frac = float(rng.uniform(*cfg["frac"]))
+        mask = (synth.random_mask(shp, frac, cfg["seed"] + n) if n % 2 == 0
+                else synth.line_hop_mask(shp, frac, cfg["seed"] + n))
+        reqs.append(dict(t=float(t_stream[sid]), stream=sid, frame_id=n, shape=shp,
+                         x=pool[shp][n % 3], mask=mask))
+    reqs.sort(key=lambda r: r["t"])
+    return reqs, pool
+
+
+def run_serving(ctx, cfg=SERVE):
+    """Open-loop live serving (Poisson arrivals) and a back-to-back 1024^2 run."""
+    import threading
+    reqs, pool = _serving_requests(cfg)
+    ctx.sensai_serve_start(slots=cfg["slots"], max_pixels=max(a * b for a, b in cfg["sizes"]), max_observed=64)
+    lock = threading.Lock()
+    finished = {}
+
+    def on_done(fid, status, out):
+        with lock:
+            finished[fid] = (time.perf_counter(), status)
+
+    # warm-up: one frame of each size
+    for j, shp in enumerate(cfg["sizes"]):
+        from paper_2311_15061_gb300 import synth
+        ctx.sensai_submit_frame(9, 10_000_000 + j, pool[shp][0], synth.random_mask(shp, 0.1, j), cfg["sweeps"],
+                                done=on_done)
+    ctx.sensai_serve_drain()
+    finished.clear()
+
+    submitted = {}
+    t0 = time.perf_counter()
+    for r in reqs:
+        delay = t0 + r["t"] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        submitted[r["frame_id"]] = (t0 + r["t"], r["shape"])
+        ctx.sensai_submit_frame(r["stream"], r["frame_id"], r["x"], r["mask"], cfg["sweeps"], done=on_done)
+    ctx.sensai_serve_drain()
+    t_end = max(v[0] for v in finished.values())
+    lat = {fid: 1e3 * (finished[fid][0] - submitted[fid][0]) for fid in submitted}
+    ok = all(finished[fid][1] == 0 for fid in submitted)
+    all_lat = np.array(list(lat.values()))
+    by_size = {}
+    for shp in cfg["sizes"]:
+        v = np.array([lat[f] for f, (_, s_) in submitted.items() if s_ == shp])
+        by_size[f"{shp[0]}x{shp[1]}"] = {"frames": int(len(v)), "p50_ms": float(np.percentile(v, 50)),
+                                         "p99_ms": float(np.percentile(v, 99))}
+    mixed = {"frames": len(reqs), "offered_hz": cfg["rate_hz"] * cfg["streams"],
+             "fps": len(reqs) / (t_end - t0), "p50_ms": float(np.percentile(all_lat, 50)),
+             "p99_ms": float(np.percentile(all_lat, 99)), "by_size": by_size, "all_ok": bool(ok)}
+
+    # live 1024^2 feed, back to back: throughput with every slot busy
+    big = cfg["sizes"][-1]
+    finished.clear()
+    from paper_2311_15061_gb300 import synth
+    masks = [synth.random_mask(big, 0.1, 500 + j) for j in range(cfg["saturated_1024"])]
+    t1 = time.perf_counter()
+    for j in range(cfg["saturated_1024"]):
+        ctx.sensai_submit_frame(j % cfg["streams"], 20_000_000 + j, pool[big][j % 3], masks[j], cfg["sweeps"],
+                                done=on_done)
+    ctx.sensai_serve_drain()
+    t2 = max(v[0] for v in finished.values())
+    lat_big = np.array([1e3 * (v[0] - t1) for v in finished.values()])
+    ctx.sensai_serve_stop()
+    sat = {"frames": cfg["saturated_1024"], "fps": cfg["saturated_1024"] / (t2 - t1),
+           "p50_completion_ms": float(np.percentile(lat_big, 50)),
+           "all_ok": all(v[1] == 0 for v in finished.values())}
+    return {"workload": ("300 frames, sizes 256^2/512^2/1024^2, random or line-hop masks 5-20%, "
+                         "4 Poisson streams x 20 Hz, 3 code sweeps + pi/gamma draws per frame, "
+                         "K=128 10x10 dictionary transferred from the learning step, 8 slots"),
+            "mixed": mixed, "live_1024_back_to_back": sat}
 
 
 def _oracle_band(rows):
@@ -355,6 +448,7 @@ def main():
     ap.add_argument("--iters", type=int, default=WORKLOAD["iters"],
                     help="Gibbs iterations per step (50 is the workload; fewer only for profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the live-serving measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

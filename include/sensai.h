@@ -176,6 +176,54 @@ sensai_status sensai_set_state(sensai_ctx* ctx, const sensai_state* state);
 /* Synchronise the last stream used and report the statistics. */
 sensai_status sensai_get_stats(sensai_ctx* ctx, sensai_stats* stats);
 
+/* ---- Live serving (reconstruction of a continuous feed, Sec. "Introduction"
+ * and Sec. "Visitors Experience"; dictionary transfer, Sec. "SenseAI: Feature
+ * Summary").  sensai_serve_start snapshots the context's dictionary, pi,
+ * gamma_s, gamma_eps and iteration index; submitted frames are then inpainted
+ * with that fixed dictionary (codes cleared, `sweeps` iterations of code sweep
+ * + pi / gamma draws, then overlap-add), exactly like sensai_inpaint.
+ *
+ * Each frame has its own shape M (same ndim, patch shape and stride as the
+ * context; (M[d] - B[d]) divisible by the stride) and its own mask.  Its
+ * random numbers are keyed by seed_f = h(h(h(seed) ^ stream_id) ^ frame_id),
+ * h = SplitMix64's finaliser (Steele, Lea & Flood 2014), so a frame's result
+ * does not depend on what else is in flight.
+ *
+ * Admission: `slots` frames may be on the GPU at once, each with its own CUDA
+ * stream and worker thread; a queued frame is admitted in arrival order when
+ * a slot is free and the device bytes of the frames in flight plus its own
+ * stay within `memory_budget`.  Work of different frames overlaps on the
+ * device. */
+typedef void (*sensai_done_fn)(void* user, uint64_t frame_id, int32_t status);
+
+typedef struct {
+    int32_t slots;           /* frames in flight, 1..64 */
+    int64_t max_pixels;      /* largest frame accepted, in pixels */
+    int64_t memory_budget;   /* device bytes for frames in flight; <= 0: slots x largest frame */
+    int32_t max_observed;    /* cap on observed pixels per patch (<= 128); frames above it fail */
+} sensai_serve_params;
+
+/* Start the serving engine on a context (allocates the slots' device memory).
+ * EBUSY if it is already serving. */
+sensai_status sensai_serve_start(sensai_ctx* ctx, const sensai_serve_params* sp);
+
+/* Queue one frame.  `frame` (prod(M) floats), `mask` (prod(M) bytes) and
+ * `out` (prod(M) floats) are host buffers read and written after admission,
+ * so the caller keeps them valid until `done(user, frame_id, status)` runs
+ * (on a worker thread; status is a sensai_status).
+ * Returns EINVAL (nothing queued) for a bad shape or a frame above
+ * max_pixels; ESTATE when the engine is not running. */
+sensai_status sensai_submit_frame(sensai_ctx* ctx, int32_t stream_id, uint64_t frame_id, const float* frame,
+                                  const uint8_t* mask, const int64_t* M, int32_t sweeps, float* out,
+                                  sensai_done_fn done, void* user);
+
+/* Block until every submitted frame has completed; returns the first
+ * failure of a frame since the previous drain (with its message), else OK. */
+sensai_status sensai_serve_drain(sensai_ctx* ctx);
+
+/* Drain, stop the workers and release the slots. */
+sensai_status sensai_serve_stop(sensai_ctx* ctx);
+
 /* Per-phase device timing.  enable = 1 clears the record and starts timing:
  * every later phase records a CUDA event pair on its launching stream;
  * enable = 0 stops.  sensai_profile_read synchronises and returns, for the

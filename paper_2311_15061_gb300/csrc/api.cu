@@ -87,6 +87,7 @@ struct sensai_ctx {
     float* dpart = nullptr;     // [grid][44][P]
     float* ddelta = nullptr;    // [P][8]
     unsigned int* dbar = nullptr;
+    ServeEngine* serve = nullptr;   // live serving engine, when started
     int ds_grid = 0;
     int ds_tile = 0;
     int ds_own = 0;
@@ -469,7 +470,7 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     CREATE_CUDA(dalloc(&ctx->misc, 2));
     CREATE_CUDA(cudaMemcpy(mask_dev, mask, (size_t)nframe, cudaMemcpyHostToDevice));
     CREATE_CUDA(cudaMemset(ctx->misc, 0, 2 * sizeof(int)));
-    CREATE_CUDA(launch_geometry(g, mask_dev, ctx->mask_bits, ctx->imgoff, ctx->nobs, ctx->misc, st0));
+    CREATE_CUDA(launch_geometry(g, mask_dev, ctx->mask_bits, ctx->imgoff, ctx->nobs, ctx->misc, nullptr, st0));
     ctx->launches += 3;
     int misc[2] = {0, 0};
     CREATE_CUDA(cudaMemcpy(misc, ctx->misc, sizeof(misc), cudaMemcpyDeviceToHost));
@@ -559,6 +560,7 @@ void sensai_destroy(sensai_ctx* ctx)
 {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
+    if (ctx->serve) serve_destroy(ctx->serve);
     cudaDeviceSynchronize();
     clear_timers(ctx);
     free_all(ctx);
@@ -815,6 +817,74 @@ sensai_status sensai_get_stats(sensai_ctx* ctx, sensai_stats* stats)
     stats->changed_updates = (int64_t)sc.chg_n;
     stats->changed_observed = (int64_t)sc.chg_obs;
     stats->active_draws = (int64_t)sc.act_n;
+    return SENSAI_OK;
+}
+
+sensai_status sensai_serve_start(sensai_ctx* ctx, const sensai_serve_params* sp)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    if (!sp) return fail(SENSAI_EINVAL, "null serve parameters");
+    if (ctx->serve) return fail(SENSAI_EBUSY, "already serving");
+    if (sp->slots < 1 || sp->slots > 64) return fail(SENSAI_EINVAL, "slots must be 1..64");
+    if (sp->max_pixels < 1 || sp->max_pixels >= (1LL << 31)) return fail(SENSAI_EINVAL, "bad max_pixels");
+    if (sp->max_observed < 1 || sp->max_observed > 128) return fail(SENSAI_EINVAL, "max_observed must be 1..128");
+    if (!ctx->ge_set) return fail(SENSAI_ESTATE, "serving needs a learnt or set state (gamma_eps unset)");
+    SENSAI_CUDA(ctx, cudaDeviceSynchronize());
+    DevScalars sc;
+    SENSAI_CUDA(ctx, cudaMemcpy(&sc, ctx->sc, sizeof(sc), cudaMemcpyDeviceToHost));
+    ServeInit in{};
+    in.device = ctx->device;
+    in.base = ctx->g;
+    in.D = ctx->D;
+    in.pi = ctx->pi;
+    in.gamma_s = sc.gamma_s;
+    in.gamma_eps = sc.gamma_eps;
+    in.a_over_K = ctx->a_over_K;
+    in.b_param = ctx->prm.b;
+    in.c = ctx->prm.c;
+    in.d = ctx->prm.d;
+    in.e = ctx->prm.e;
+    in.f = ctx->prm.f;
+    in.seed = ctx->prm.seed;
+    in.t0 = (uint32_t)ctx->t;
+    in.slots = sp->slots;
+    in.max_pixels = sp->max_pixels;
+    in.memory_budget = sp->memory_budget;
+    in.max_observed = sp->max_observed;
+    ctx->serve = serve_create(in, &st);
+    if (!ctx->serve) return fail(st, "could not allocate the serving slots");
+    return SENSAI_OK;
+}
+
+sensai_status sensai_submit_frame(sensai_ctx* ctx, int32_t stream_id, uint64_t frame_id, const float* frame,
+                                  const uint8_t* mask, const int64_t* M, int32_t sweeps, float* out,
+                                  sensai_done_fn done, void* user)
+{
+    if (!ctx) return fail(SENSAI_EINVAL, "null context");
+    if (!ctx->serve) return fail(SENSAI_ESTATE, "serving engine not started");
+    const sensai_status st = serve_submit(ctx->serve, stream_id, frame_id, frame, mask, M, sweeps, out, done, user);
+    if (st == SENSAI_EINVAL) return fail(st, "bad frame: shape, size above max_pixels or above the memory budget");
+    if (st != SENSAI_OK) return fail(st, "serving engine stopped");
+    return SENSAI_OK;
+}
+
+sensai_status sensai_serve_drain(sensai_ctx* ctx)
+{
+    if (!ctx) return fail(SENSAI_EINVAL, "null context");
+    if (!ctx->serve) return fail(SENSAI_ESTATE, "serving engine not started");
+    std::string msg;
+    const sensai_status st = serve_drain(ctx->serve, &msg);
+    if (st != SENSAI_OK) return fail(st, "%s", msg.c_str());
+    return SENSAI_OK;
+}
+
+sensai_status sensai_serve_stop(sensai_ctx* ctx)
+{
+    if (!ctx) return fail(SENSAI_EINVAL, "null context");
+    if (!ctx->serve) return fail(SENSAI_ESTATE, "serving engine not started");
+    serve_destroy(ctx->serve);
+    ctx->serve = nullptr;
     return SENSAI_OK;
 }
 

@@ -47,15 +47,24 @@ __device__ __forceinline__ bool mask_at(const uint32_t* bits, long long u)
     return (bits[u >> 5] >> (u & 31)) & 1u;
 }
 
-__global__ void count_obs_kernel(Geom g, const uint32_t* mbits, const int* imgoff, uint16_t* nobs, int* maxobs)
+// misc[0] <- max_i |Omega_i|; *total (if given) += sum_i |Omega_i|.
+__global__ void count_obs_kernel(Geom g, const uint32_t* mbits, const int* imgoff, uint16_t* nobs, int* maxobs,
+                                 unsigned long long* total)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.N) return;
-    const long long org = patch_origin(g, i);
     int c = 0;
-    for (int p = 0; p < g.P; ++p) c += mask_at(mbits, org + imgoff[p]);
-    nobs[i] = (uint16_t)c;
-    atomicMax(maxobs, c);
+    if (i < g.N) {
+        const long long org = patch_origin(g, i);
+        for (int p = 0; p < g.P; ++p) c += mask_at(mbits, org + imgoff[p]);
+        nobs[i] = (uint16_t)c;
+        atomicMax(maxobs, c);
+    }
+    if (total) {
+        unsigned long long v = (unsigned long long)c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
+    }
 }
 
 __global__ void fill_obs_kernel(Geom g, const uint32_t* mbits, const int* imgoff, uint16_t* obs)
@@ -314,12 +323,18 @@ static inline unsigned int blocks_for(long long n, int threads)
 }
 
 cudaError_t launch_geometry(const Geom& g, const uint8_t* mask_bytes, uint32_t* mask_bits, int* imgoff,
-                            uint16_t* nobs, int* maxobs, cudaStream_t s)
+                            uint16_t* nobs, int* maxobs, unsigned long long* total, cudaStream_t s)
 {
     const long long nmw = (g.nframe + 31) / 32;
     pack_mask_kernel<<<blocks_for(nmw, 256), 256, 0, s>>>(g.nframe, mask_bytes, mask_bits);
     pixel_offsets_kernel<<<blocks_for(g.P, 256), 256, 0, s>>>(g, imgoff);
-    count_obs_kernel<<<blocks_for(g.N, 256), 256, 0, s>>>(g, mask_bits, imgoff, nobs, maxobs);
+    count_obs_kernel<<<blocks_for(g.N, 256), 256, 0, s>>>(g, mask_bits, imgoff, nobs, maxobs, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_obs(const Geom& g, const uint32_t* mask_bits, const int* imgoff, uint16_t* obs, cudaStream_t s)
+{
+    fill_obs_kernel<<<blocks_for(g.N, 256), 256, 0, s>>>(g, mask_bits, imgoff, obs);
     return cudaGetLastError();
 }
 

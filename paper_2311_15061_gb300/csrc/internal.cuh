@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "sensai.h"
 
 namespace sensai {
@@ -311,6 +313,7 @@ struct SweepArgs {
     const uint32_t* Ipre;      // [P][NW] exclusive popcount prefix of Ibits
     const int* Rbase;          // [P] start of pixel p's residual slots
     float* R;                  // residual, slot Rbase[p] + rank of i among patches observing p
+                               // (null: inpainting only, the residual is not kept)
     int* m;                    // [K] active count per atom (accumulated)
     double* part_s2;           // [NW] per 32-patch chunk
     double* part_r2;           // [NW] per 32-patch chunk
@@ -370,6 +373,31 @@ struct HyperArgs {
     uint32_t t;
 };
 
+// Live serving engine (serve.cu).
+struct ServeEngine;
+struct ServeInit {
+    int device;
+    Geom base;                 // ndim, B, S, K, KB, P of the context (M unused)
+    const float* D;            // device [K][P], copied
+    const double* pi;          // device [K], copied
+    double gamma_s, gamma_eps;
+    double a_over_K, b_param;  // b_param <= 0: b = N / 8 per frame
+    double c, d, e, f;
+    uint64_t seed;
+    uint32_t t0;
+    int slots;
+    long long max_pixels;
+    long long memory_budget;
+    int max_observed;
+};
+ServeEngine* serve_create(const ServeInit& in, sensai_status* status);
+sensai_status serve_submit(ServeEngine* e, int32_t stream_id, uint64_t frame_id, const float* frame,
+                           const uint8_t* mask, const int64_t* M, int32_t sweeps, float* out, sensai_done_fn done,
+                           void* user);
+sensai_status serve_drain(ServeEngine* e, std::string* message);   // first failure since the last drain
+void serve_destroy(ServeEngine* e);
+uint64_t serve_frame_seed(uint64_t seed, int32_t stream_id, uint64_t frame_id);
+
 // Sets the calling thread's message returned by sensai_last_error().
 void record_error(const char* msg);
 
@@ -385,7 +413,8 @@ int dict_space_grid(const Geom& g, size_t smem, int device);
 cudaError_t launch_dict_space(const DictSpaceArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_obs_px(long long nframe, const uint32_t* mbits, int* obs_px, cudaStream_t s);
 cudaError_t launch_geometry(const Geom& g, const uint8_t* mask_bytes, uint32_t* mask_bits, int* imgoff,
-                            uint16_t* nobs, int* maxobs, cudaStream_t s);
+                            uint16_t* nobs, int* maxobs, unsigned long long* total, cudaStream_t s);
+cudaError_t launch_fill_obs(const Geom& g, const uint32_t* mask_bits, const int* imgoff, uint16_t* obs, cudaStream_t s);
 cudaError_t launch_slots(const Geom& g, const uint32_t* mask_bits, const int* imgoff, uint16_t* obs,
                          uint32_t* Ibits, uint32_t* Ipre, int* Icnt, int* Rbase, int* max_slots, cudaStream_t s);
 cudaError_t launch_ilist(const Geom& g, const uint32_t* Ibits, const uint32_t* Ipre, const int* Rbase, int* Ilist,

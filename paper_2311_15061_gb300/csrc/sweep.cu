@@ -172,11 +172,13 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
         for (int j = 0; j < MAXOBS; ++j) {
             if (j >= wmax) break;
             if (j < nobs) {
-                const int p = a.obs[(long long)j * N + i];
-                const long long wd = (long long)p * NW + chunk;
-                const uint32_t ib = a.Ibits[wd];
-                const int slot = a.Rbase[p] + (int)a.Ipre[wd] + __popc(ib & ((1u << lane) - 1u));
-                a.R[slot] = r[j];
+                if (a.R) {
+                    const int p = a.obs[(long long)j * N + i];
+                    const long long wd = (long long)p * NW + chunk;
+                    const uint32_t ib = a.Ibits[wd];
+                    const int slot = a.Rbase[p] + (int)a.Ipre[wd] + __popc(ib & ((1u << lane) - 1u));
+                    a.R[slot] = r[j];
+                }
                 r2 = fmaf(r[j], r[j], r2);
             }
         }

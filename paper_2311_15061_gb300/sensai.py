@@ -27,7 +27,8 @@ EXPORTED = [
     "sensai_inpaint", "sensai_sweep_codes", "sensai_draw_dictionary", "sensai_draw_hyper",
     "sensai_reconstruct", "sensai_overlap_counts", "sensai_get_dictionary", "sensai_set_dictionary",
     "sensai_get_state", "sensai_set_state", "sensai_get_stats", "sensai_profile", "sensai_profile_read",
-    "sensai_reconstruct_static", "sensai_last_error",
+    "sensai_reconstruct_static", "sensai_serve_start", "sensai_submit_frame", "sensai_serve_drain",
+    "sensai_serve_stop", "sensai_last_error",
 ]
 
 
@@ -84,6 +85,17 @@ class sensai_stats(ctypes.Structure):
     ]
 
 
+class sensai_serve_params(ctypes.Structure):
+    _fields_ = [
+        ("slots", ctypes.c_int32),
+        ("max_pixels", ctypes.c_int64),
+        ("memory_budget", ctypes.c_int64),
+        ("max_observed", ctypes.c_int32),
+    ]
+
+
+DONE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32)
+
 _vp, _i32, _st = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int
 _SIG = {
     "sensai_create": (_st, [ctypes.POINTER(sensai_params), _vp, ctypes.POINTER(_vp)]),
@@ -105,6 +117,10 @@ _SIG = {
     "sensai_profile": (_st, [_vp, _i32]),
     "sensai_profile_read": (_st, [_vp, _vp, _vp]),
     "sensai_reconstruct_static": (_st, [ctypes.POINTER(sensai_params), _vp, _vp, _vp, _vp]),
+    "sensai_serve_start": (_st, [_vp, ctypes.POINTER(sensai_serve_params)]),
+    "sensai_submit_frame": (_st, [_vp, _i32, ctypes.c_uint64, _vp, _vp, _vp, _i32, _vp, DONE_FN, _vp]),
+    "sensai_serve_drain": (_st, [_vp]),
+    "sensai_serve_stop": (_st, [_vp]),
     "sensai_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIG.items():
@@ -266,6 +282,52 @@ class Context:
                           host(S, np.float32, self.N * self.K, "S"), host(pi, np.float64, self.K, "pi"),
                           float(gamma_s), float(gamma_eps), int(iter))
         _check(_lib.sensai_set_state(self._h, ctypes.byref(st)))
+
+    # -- live serving -------------------------------------------------------
+    def sensai_serve_start(self, slots=4, max_pixels=1 << 20, memory_budget=0, max_observed=64):
+        """Start the serving engine on this context's current dictionary, pi
+        and precisions."""
+        import threading
+        sp = sensai_serve_params(int(slots), int(max_pixels), int(memory_budget), int(max_observed))
+        self._serve_lock = threading.Lock()
+        self._pending = {}
+        self._cb = DONE_FN(self._on_done)
+        _check(_lib.sensai_serve_start(self._h, ctypes.byref(sp)))
+
+    def _on_done(self, user, frame_id, status):
+        with self._serve_lock:
+            entry = self._pending.pop(int(user), None)
+        if entry is not None and entry[0] is not None:
+            entry[0](int(frame_id), int(status), entry[1])
+
+    def sensai_submit_frame(self, stream_id, frame_id, frame, mask, sweeps, out=None, done=None):
+        """Queue one host frame (any shape valid for the patch geometry).
+        ``done(frame_id, status, out)`` runs on a worker thread when the
+        reconstruction is in ``out``.  Returns ``out``."""
+        frame = np.ascontiguousarray(frame, dtype=np.float32)
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        if frame.shape != mask.shape:
+            raise ValueError("frame and mask shapes differ")
+        if out is None:
+            out = np.empty(frame.shape, dtype=np.float32)
+        M = (ctypes.c_int64 * 4)(*([int(v) for v in frame.shape] + [0] * (4 - frame.ndim)))
+        with self._serve_lock:
+            self._serial = getattr(self, "_serial", 0) + 1
+            token = self._serial
+            self._pending[token] = (done, out, frame, mask, M)
+        st = _lib.sensai_submit_frame(self._h, int(stream_id), int(frame_id), frame.ctypes.data, mask.ctypes.data,
+                                      ctypes.addressof(M), int(sweeps), out.ctypes.data, self._cb, token)
+        if st != SENSAI_OK:
+            with self._serve_lock:
+                self._pending.pop(token, None)
+            _check(st)
+        return out
+
+    def sensai_serve_drain(self):
+        _check(_lib.sensai_serve_drain(self._h))
+
+    def sensai_serve_stop(self):
+        _check(_lib.sensai_serve_stop(self._h))
 
     def sensai_profile(self, enable):
         _check(_lib.sensai_profile(self._h, int(enable)))

@@ -28,7 +28,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["stem_frame", "random_mask", "stem_volume", "sparse_state"]
+__all__ = ["stem_frame", "random_mask", "line_hop_mask", "stem_volume", "sparse_state"]
 
 
 def _lattice_points(shape, spacing, theta, origin):
@@ -118,3 +118,21 @@ def sparse_state(n_patches, P, K, seed=0, *, active=0.08, s_scale=0.5):
     Z = (rng.random((n_patches, K)) < active).astype(np.uint8)
     S = (rng.standard_normal((n_patches, K)) * s_scale).astype(np.float32) * Z
     return D, Z, S.astype(np.float32)
+
+
+def line_hop_mask(shape, frac, seed=0):
+    """Line-hop sampling: in every band of h = round(1/frac) rows, each column
+    keeps exactly one pixel, whose row inside the band follows a +-1 random
+    walk along the columns, clamped to the band."""
+    rng = np.random.default_rng(seed + 0x11E0)
+    rows, cols = shape
+    h = max(1, int(round(1.0 / frac)))
+    mask = np.zeros(shape, dtype=np.uint8)
+    for top in range(0, rows, h):
+        band = min(h, rows - top)
+        r = int(rng.integers(0, band))
+        steps = rng.integers(-1, 2, size=cols)
+        for c in range(cols):
+            r = min(max(r + int(steps[c]), 0), band - 1)
+            mask[top + r, c] = 1
+    return mask
