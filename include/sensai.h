@@ -65,8 +65,18 @@ typedef enum {
 /* Problem definition.  Requirements: 1 <= ndim <= 4; 1 <= B[d] <= M[d];
  * stride[d] >= 1 with (M[d] - B[d]) divisible by stride[d]; 1 <= K <= 1024;
  * P = prod(B) <= 1024; number of patches < 2^31.  a <= 0 selects a = K and
- * b <= 0 selects b = N / 8 (N = number of patches).  c..f > 0.  flags must
- * be 0. */
+ * b <= 0 selects b = N / 8 (N = number of patches).  c..f > 0.  flags:
+ * 0, or SENSAI_FLAG_STREAM_DICTIONARY optionally with SENSAI_SLICE_ATOMS(n);
+ * other bits are EINVAL.
+ *
+ * The code sweep keeps the whole dictionary in shared memory when
+ * (P + 1) * (K rounded up to 8, odd) floats fit (K = 128, P = 100: 52 KB);
+ * otherwise it streams the dictionary through shared memory in slices of
+ * atoms.  SENSAI_FLAG_STREAM_DICTIONARY streams it always;
+ * SENSAI_SLICE_ATOMS(n) fixes the slice at n atoms (n a multiple of 8, no
+ * larger than what fits).  Results do not depend on either. */
+#define SENSAI_FLAG_STREAM_DICTIONARY 0x1
+#define SENSAI_SLICE_ATOMS(n) ((((n) / 8) & 0xff) << 8)
 typedef struct {
     int32_t ndim;
     int64_t M[4];
@@ -110,6 +120,8 @@ typedef struct {
     int64_t changed_updates;   /* code updates whose weight changed, since the last profile start */
     int64_t changed_observed;  /* sum of |Omega_i| over those updates */
     int64_t active_draws;      /* code draws with z = 1, since the last profile start */
+    int32_t slice_atoms;       /* code sweep: 0 = dictionary resident in shared memory, else atoms per streamed slice */
+    int32_t slices;            /* code sweep: streamed slices per pass (0 when resident) */
 } sensai_stats;
 
 /* Create a context on the current CUDA device.  `mask` is prod(M) host bytes

@@ -44,7 +44,8 @@ struct sensai_ctx {
     double a_over_K = 0, b_scaled = 0;
     int maxobs = 0, max_slots = 0;
     long long n_observed = 0;
-    int sweep_grid = 0;
+    SweepPlan sweep_plan{};
+    float* Dsl = nullptr;       // dictionary slices (streamed code sweep only)
     int64_t t = 0;
     bool frame_set = false;
     bool ge_set = false;
@@ -131,7 +132,7 @@ void free_all(sensai_ctx* c)
 {
     void* ptrs[] = {c->mask_bits, c->imgoff, c->nobs, c->obs, c->Ibits, c->Ipre, c->Icnt, c->Rbase, c->Ilist,
                     c->misc, c->x, c->D, c->W, c->Zb, c->R, c->Y, c->out, c->pi, c->lpi, c->m,
-                    c->part_s2, c->part_r2, c->chunk_counter, c->sc, c->obs_px, c->dpart, c->ddelta, c->dbar};
+                    c->part_s2, c->part_r2, c->chunk_counter, c->sc, c->obs_px, c->dpart, c->ddelta, c->dbar, c->Dsl};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -256,7 +257,7 @@ sensai_status run_sweep(sensai_ctx* ctx, cudaStream_t s)
     a.t = (uint32_t)ctx->t;
     PhaseTimer timer(ctx, kPhaseCodes, s);
     SENSAI_CUDA(ctx, cudaMemsetAsync(ctx->m, 0, sizeof(int) * ctx->g.K, s));
-    SENSAI_CUDA(ctx, launch_sweep(a, ctx->maxobs, ctx->sweep_grid, s));
+    SENSAI_CUDA(ctx, launch_code_sweep(a, ctx->sweep_plan, ctx->maxobs, ctx->Dsl, s));
     timer.stop();
     ctx->launches += 1;
     ctx->codes_valid = true;
@@ -395,7 +396,10 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     const sensai_params& p = *prm;
     if (p.ndim < 1 || p.ndim > kMaxDim) return fail(SENSAI_EINVAL, "ndim must be 1..4 (got %d)", p.ndim);
     if (p.K < 1 || p.K > 1024) return fail(SENSAI_EINVAL, "K must be 1..1024 (got %d)", p.K);
-    if (p.flags != 0) return fail(SENSAI_EINVAL, "flags must be 0");
+    const int known_flags = SENSAI_FLAG_STREAM_DICTIONARY | SENSAI_SLICE_ATOMS(2040);
+    if ((p.flags & ~known_flags) != 0) return fail(SENSAI_EINVAL, "unknown flags 0x%x", p.flags);
+    if ((p.flags & ~SENSAI_FLAG_STREAM_DICTIONARY) != 0 && !(p.flags & SENSAI_FLAG_STREAM_DICTIONARY))
+        return fail(SENSAI_EINVAL, "SENSAI_SLICE_ATOMS needs SENSAI_FLAG_STREAM_DICTIONARY");
     if (!(p.c > 0 && p.d > 0 && p.e > 0 && p.f > 0)) return fail(SENSAI_EINVAL, "c, d, e, f must be > 0");
     Geom g{};
     g.ndim = p.ndim;
@@ -430,15 +434,9 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     g.KB = (p.K + kAtomBlock - 1) / kAtomBlock;
     g.nframe = nframe;
 
-    int device = 0, optin = 0;
+    int device = 0;
     cudaError_t e = cudaGetDevice(&device);
     if (e != cudaSuccess) return cuda_failure(nullptr, e, "cudaGetDevice", __LINE__);
-    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    if (e != cudaSuccess) return cuda_failure(nullptr, e, "cudaDeviceGetAttribute", __LINE__);
-    if (sweep_smem_bytes(g) > optin)
-        return fail(SENSAI_EINVAL, "dictionary of K=%d atoms x P=%d pixels does not fit in shared memory", g.K, g.P);
-    if (sizeof(float) * (size_t)g.K * (((size_t)g.P + 31) & ~(size_t)31) > (size_t)optin)
-        return fail(SENSAI_EINVAL, "dictionary of K=%d atoms x P=%d pixels does not fit in shared memory", g.K, g.P);
 
     sensai_ctx* ctx = new (std::nothrow) sensai_ctx();
     if (!ctx) return fail(SENSAI_ENOMEM, "host allocation failed");
@@ -544,10 +542,15 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
             ctx->ds_own = own;
         }
     }
-    ctx->sweep_grid = sweep_grid_size(g, ctx->maxobs, device);
-    if (ctx->sweep_grid < 1) {
-        fail(SENSAI_ECUDA, "no launch configuration for the code sweep (max observed %d)", ctx->maxobs);
-        return bail(SENSAI_ECUDA);
+    {
+        const bool stream = (p.flags & SENSAI_FLAG_STREAM_DICTIONARY) != 0;
+        const int slice = ((p.flags >> 8) & 0xff) * kAtomBlock;
+        if (!plan_sweep(g, ctx->maxobs, device, stream, slice, &ctx->sweep_plan)) {
+            fail(SENSAI_EINVAL, "no launch configuration for the code sweep (K=%d, P=%d, max observed %d, slice %d)",
+                 g.K, g.P, ctx->maxobs, slice);
+            return bail(SENSAI_EINVAL);
+        }
+        if (ctx->sweep_plan.slice_atoms > 0) CREATE_CUDA(dalloc(&ctx->Dsl, (size_t)slice_capacity_floats(g)));
     }
     if (reset_state(ctx, st0) != SENSAI_OK) return bail(SENSAI_ECUDA);
     CREATE_CUDA(cudaDeviceSynchronize());
@@ -817,6 +820,8 @@ sensai_status sensai_get_stats(sensai_ctx* ctx, sensai_stats* stats)
     stats->changed_updates = (int64_t)sc.chg_n;
     stats->changed_observed = (int64_t)sc.chg_obs;
     stats->active_draws = (int64_t)sc.act_n;
+    stats->slice_atoms = ctx->sweep_plan.slice_atoms;
+    stats->slices = ctx->sweep_plan.slices;
     return SENSAI_OK;
 }
 
@@ -852,6 +857,8 @@ sensai_status sensai_serve_start(sensai_ctx* ctx, const sensai_serve_params* sp)
     in.max_pixels = sp->max_pixels;
     in.memory_budget = sp->memory_budget;
     in.max_observed = sp->max_observed;
+    in.stream_dictionary = (ctx->prm.flags & SENSAI_FLAG_STREAM_DICTIONARY) != 0;
+    in.slice_atoms = ((ctx->prm.flags >> 8) & 0xff) * kAtomBlock;
     ctx->serve = serve_create(in, &st);
     if (!ctx->serve) return fail(st, "could not allocate the serving slots");
     return SENSAI_OK;

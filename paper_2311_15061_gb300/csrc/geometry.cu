@@ -278,31 +278,35 @@ __global__ void ilist_kernel(Geom g, const uint32_t* Ibits, const uint32_t* Ipre
 // Per-patch reconstruction Y[p][i] = sum_k z_ik w_ik d_kp.  One thread per
 // patch, 32 pixels at a time; the dictionary chunk is read with warp-uniform
 // (broadcast) shared-memory loads.
-__global__ void __launch_bounds__(256) patch_recon_kernel(Geom g, const float* D, const float* W,
-                                                          const uint32_t* Zb, float* Y)
+__global__ void __launch_bounds__(256) patch_recon_kernel(Geom g, const float* D, const float* W, float* Y)
 {
-    extern __shared__ float Ds[];  // K x ldP, ldP = P rounded up to 32, zero padded
-    const int K = g.K, P = g.P;
-    const int ldP = (P + 31) & ~31;
-    for (int idx = threadIdx.x; idx < K * ldP; idx += blockDim.x) {
-        const int k = idx / ldP, p = idx - k * ldP;
-        Ds[idx] = p < P ? D[(long long)k * P + p] : 0.0f;
-    }
-    __syncthreads();
-    const long long chunk = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    extern __shared__ float Ds[];  // Kpad x 32: columns p0 .. p0 + 31 of D, zero past P and K
+    const int K = g.K, P = g.P, KB = g.KB;
     const int lane = threadIdx.x & 31;
-    if (chunk >= g.NW) return;
+    const long long chunk = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const bool on = chunk < g.NW;
     const long long i = chunk * 32 + lane;
     for (int p0 = 0; p0 < P; p0 += 32) {
+        __syncthreads();   // the previous slab is consumed
+        for (int idx = threadIdx.x; idx < KB * kAtomBlock * 32; idx += blockDim.x) {
+            const int k = idx >> 5, q = idx & 31;
+            Ds[idx] = (k < K && p0 + q < P) ? D[(long long)k * P + p0 + q] : 0.0f;
+        }
+        __syncthreads();
+        if (!on) continue;
         float acc[32];
 #pragma unroll
         for (int q = 0; q < 32; ++q) acc[q] = 0.0f;
-        for (int k = 0; k < K; ++k) {
-            const float w = W[wblock(g, k / kAtomBlock, i) + k % kAtomBlock];
-            if (w != 0.0f) {
-                const float* dk = Ds + k * ldP + p0;
+        for (int kb = 0; kb < KB; ++kb) {
+            const W8 wb = load_w8(W + wblock(g, kb, i));
 #pragma unroll
-                for (int q = 0; q < 32; ++q) acc[q] = fmaf(dk[q], w, acc[q]);
+            for (int kk = 0; kk < kAtomBlock; ++kk) {
+                const float w = wb.v[kk];   // zero for padding atoms
+                if (w != 0.0f) {
+                    const float* dk = Ds + (kb * kAtomBlock + kk) * 32;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) acc[q] = fmaf(dk[q], w, acc[q]);
+                }
             }
         }
         if (i < g.N) {
@@ -370,11 +374,11 @@ cudaError_t launch_overlap_counts(const Geom& g, int* counts, cudaStream_t s)
 cudaError_t launch_reconstruct(const Geom& g, const float* D, const float* W, const uint32_t* Zb, float* Y,
                                float* out, cudaStream_t s)
 {
-    const int ldP = (g.P + 31) & ~31;
-    const int smem = (int)(sizeof(float) * (size_t)g.K * ldP);
+    (void)Zb;
+    const int smem = (int)(sizeof(float) * (size_t)g.KB * kAtomBlock * 32);
     cudaError_t e = cudaFuncSetAttribute((void*)patch_recon_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    patch_recon_kernel<<<blocks_for(g.NW, 8), 256, smem, s>>>(g, D, W, Zb, Y);
+    patch_recon_kernel<<<blocks_for(g.NW, 8), 256, smem, s>>>(g, D, W, Y);
     ola_gather_kernel<<<blocks_for(g.nframe, 256), 256, 0, s>>>(g, Y, out);
     return cudaGetLastError();
 }

@@ -321,6 +321,12 @@ struct SweepArgs {
     DevScalars* sc_out;           // change counters (same object as sc)
     PhiloxKeys keys;              // round keys of the seed
     uint32_t t;
+    // streamed dictionary (sweep_tiled.cu); Dsl null: the whole dictionary
+    // is resident in shared memory (sweep.cu)
+    const float* Dsl = nullptr;   // [slices][slice_stride] slices in shared-memory layout
+    int slice_atoms = 0;          // KS, a multiple of 8
+    int slices = 0;               // ceil(8 KB / KS)
+    long long slice_stride = 0;   // floats per slice, ((P + 1) (KS | 1)) rounded up to 4
 };
 
 struct DictArgs {
@@ -389,6 +395,8 @@ struct ServeInit {
     long long max_pixels;
     long long memory_budget;
     int max_observed;
+    bool stream_dictionary;    // the context's SENSAI_FLAG_STREAM_DICTIONARY
+    int slice_atoms;           // the context's SENSAI_SLICE_ATOMS (0: largest that fits)
 };
 ServeEngine* serve_create(const ServeInit& in, sensai_status* status);
 sensai_status serve_submit(ServeEngine* e, int32_t stream_id, uint64_t frame_id, const float* frame,
@@ -406,6 +414,28 @@ cudaError_t launch_sweep(const SweepArgs& a, int maxobs, int grid, cudaStream_t 
 int sweep_block_size();
 int sweep_smem_bytes(const Geom& g);
 int sweep_grid_size(const Geom& g, int maxobs, int device);
+
+// How a code sweep runs: the whole dictionary resident in shared memory
+// (slice_atoms = 0) or streamed in slices of slice_atoms atoms.
+struct SweepPlan {
+    int grid = 0;
+    int slice_atoms = 0;
+    int slices = 0;
+    long long slice_stride = 0;
+};
+// Resident when it fits (unless force_stream); else the largest slice that
+// fits, or force_slice_atoms (a multiple of 8 no larger than that) if > 0.
+bool plan_sweep(const Geom& g, int maxobs, int device, bool force_stream, int force_slice_atoms, SweepPlan* out);
+long long slice_capacity_floats(const Geom& g);
+// One code sweep by plan; Dsl (slice_capacity_floats floats) is needed when
+// streamed and is refilled from a.D on the stream first.
+cudaError_t launch_code_sweep(SweepArgs a, const SweepPlan& plan, int maxobs, float* Dsl, cudaStream_t s);
+long long slice_stride_floats(const Geom& g, int KS);
+size_t tiled_smem_bytes(const Geom& g, int KS);
+int tiled_slice_atoms(const Geom& g, int maxobs, int device);
+int tiled_grid_size(const Geom& g, int maxobs, int KS, int device);
+cudaError_t launch_slice_dictionary(const Geom& g, const float* D, float* Dsl, int KS, cudaStream_t s);
+cudaError_t launch_sweep_tiled(const SweepArgs& a, int maxobs, int grid, cudaStream_t s);
 cudaError_t launch_dict(const DictArgs& a, int max_slots, cudaStream_t s);
 cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);
 size_t dict_space_smem_bytes(const Geom& g, int max_tile, int max_pairs, int own_max);

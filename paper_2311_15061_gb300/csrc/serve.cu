@@ -79,6 +79,7 @@ struct ServeSlot {
     float* lpi = nullptr;
     float* Y = nullptr;
     float* out = nullptr;
+    float* Dsl = nullptr;                // dictionary slices (streamed code sweep)
     int* h_misc = nullptr;               // pinned readback
     unsigned long long* h_total = nullptr;
     DevScalars* h_sc = nullptr;          // pinned initial scalars
@@ -89,6 +90,8 @@ struct ServeEngine {
     int device = 0;
     Geom base{};                 // ndim, B, S, K, P of the context
     int32_t max_observed = 0;
+    bool stream_dictionary = false;
+    int slice_atoms = 0;
     long long max_pixels = 0;
     long long budget = 0;
     long long in_flight = 0;
@@ -155,7 +158,7 @@ namespace sensai {
 static void free_slot(ServeSlot* s)
 {
     void* dev[] = {s->x, s->mask_bytes, s->mask_bits, s->imgoff, s->nobs, s->obs, s->misc, s->total, s->W, s->Zb,
-                   s->m, s->part_s2, s->part_r2, s->counter, s->sc, s->pi, s->lpi, s->Y, s->out};
+                   s->m, s->part_s2, s->part_r2, s->counter, s->sc, s->pi, s->lpi, s->Y, s->out, s->Dsl};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (s->h_misc) cudaFreeHost(s->h_misc);
@@ -202,6 +205,7 @@ static cudaError_t alloc_slot(ServeEngine* e, ServeSlot* s)
     SLOT_TRY(slot_alloc(&s->pi, (size_t)b.K));
     SLOT_TRY(slot_alloc(&s->lpi, (size_t)b.K));
     SLOT_TRY(slot_alloc(&s->Y, (size_t)b.P * px));
+    SLOT_TRY(slot_alloc(&s->Dsl, (size_t)slice_capacity_floats(b)));
     SLOT_TRY(cudaMallocHost((void**)&s->h_misc, 2 * sizeof(int)));
     SLOT_TRY(cudaMallocHost((void**)&s->h_total, sizeof(unsigned long long)));
     SLOT_TRY(cudaMallocHost((void**)&s->h_sc, sizeof(DevScalars)));
@@ -263,9 +267,9 @@ static sensai_status process_frame(ServeEngine* e, ServeSlot* sl, const ServeReq
     sl->h_sc->ge_set = 1;
     FRAME_TRY(cudaMemcpyAsync(sl->sc, sl->h_sc, sizeof(DevScalars), cudaMemcpyHostToDevice, s));
 
-    const int grid = sweep_grid_size(g, maxobs > 0 ? maxobs : 1, e->device);
-    if (grid < 1) {
-        note_error(e, SENSAI_ECUDA, "no launch configuration", "sweep_grid_size");
+    SweepPlan plan{};
+    if (!plan_sweep(g, maxobs, e->device, e->stream_dictionary, e->slice_atoms, &plan)) {
+        note_error(e, SENSAI_ECUDA, "no launch configuration", "plan_sweep");
         return SENSAI_ECUDA;
     }
     const double b = e->b_param > 0 ? e->b_param : (double)g.N / 8.0;
@@ -290,7 +294,7 @@ static sensai_status process_frame(ServeEngine* e, ServeSlot* sl, const ServeReq
         a.keys = philox_round_keys(fseed);
         a.t = e->t0 + (uint32_t)sw;
         FRAME_TRY(cudaMemsetAsync(sl->m, 0, sizeof(int) * g.K, s));
-        FRAME_TRY(launch_sweep(a, maxobs > 0 ? maxobs : 1, grid, s));
+        FRAME_TRY(launch_code_sweep(a, plan, maxobs, sl->Dsl, s));
         HyperArgs h{};
         h.g = g;
         h.m = sl->m;
@@ -360,6 +364,8 @@ ServeEngine* serve_create(const ServeInit& in, sensai_status* status)
     e->device = in.device;
     e->base = in.base;
     e->max_observed = in.max_observed;
+    e->stream_dictionary = in.stream_dictionary;
+    e->slice_atoms = in.slice_atoms;
     e->max_pixels = in.max_pixels;
     e->a_over_K = in.a_over_K;
     e->b_param = in.b_param;

@@ -15,7 +15,7 @@
 // 32-aligned patches so the atom's activity bits of the warp form one 32-bit
 // word (ballot).  Warps pull 32-patch chunks from a global counter, so the
 // tail of the grid is a single chunk per warp.  Weights are read and written
-// in 8-atom blocks (two 16-byte accesses per lane, 1 KB per warp), the next
+// in 8-atom blocks (one 256-bit access per lane, 1 KB per warp), the next
 // block prefetched behind the current one, so no global load sits on the
 // per-atom path; per-warp counters replace any block-wide barrier.  The dictionary sits in shared
 // memory as [p][k] with an odd row pitch plus one zero row (p = P) that padded
@@ -25,7 +25,7 @@
 // pixels are gathered from the frame and the residual rebuilt from the stored
 // weights at the start of each sweep.  At the end the residual is scattered
 // to the per-pixel slot layout the dictionary kernel consumes.
-#include "internal.cuh"
+#include "sweep_block.cuh"
 
 namespace sensai {
 
@@ -54,13 +54,10 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
     for (int idx = threadIdx.x; idx < kSweepWarps * Kpad; idx += blockDim.x) cntw[idx] = 0;
     __syncthreads();
 
-    const float gs = (float)a.sc->gamma_s;
-    const float ge = (float)a.sc->gamma_eps;
-    const float half_log_gs = 0.5f * logf(gs);
-    const float half_ge2 = 0.5f * ge * ge;
+    const CodeConst c = code_const(a.sc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* mycnt = cntw + warp * Kpad;
-    unsigned int chg_n = 0, chg_obs = 0, act_n = 0;
+    CodeTally tl;
 
     for (;;) {
         if (lane == 0) chunk_slot[warp] = atomicAdd(a.chunk_counter, 1u);
@@ -77,34 +74,12 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
 
         int offK[MAXOBS];
         float r[MAXOBS];
-#pragma unroll
-        for (int j = 0; j < MAXOBS; ++j) {
-            int p = P;
-            float v = 0.0f;
-            if (j < nobs) {
-                p = a.obs[(long long)j * N + i];
-                v = a.x[org + a.imgoff[p]];
-            }
-            offK[j] = p * ldK;
-            r[j] = v;
-        }
+        gather_patch<MAXOBS>(a, i, nobs, org, ldK, offK, r);
 
         // residual r = x - D w on the observed pixels, from the stored weights
-        for (int kb = 0; kb < KB; ++kb) {
-            const W8 wb = load_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock);
-            const float* wv = wb.v;
-#pragma unroll
-            for (int kk = 0; kk < kAtomBlock; ++kk) {
-                if (wv[kk] != 0.0f) {
-                    const float* dk = Ds + kb * kAtomBlock + kk;
-#pragma unroll
-                    for (int j = 0; j < MAXOBS; ++j) {
-                        if ((j & 3) == 0 && j >= wmax) break;
-                        r[j] = fmaf(-dk[offK[j]], wv[kk], r[j]);
-                    }
-                }
-            }
-        }
+        for (int kb = 0; kb < KB; ++kb)
+            rebuild_block<MAXOBS>(Ds + kb * kAtomBlock, offK, r, wmax,
+                                  load_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock));
 
         float s2 = 0.0f;
         W8 nb = load_w8(a.W + (long long)i * kAtomBlock);
@@ -115,96 +90,15 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
             float w4 = nb.v[4], w5 = nb.v[5], w6 = nb.v[6], w7 = nb.v[7];
             if (kb + 1 < KB)   // prefetch the next block behind this block's work
                 nb = load_w8(a.W + ((long long)(kb + 1) * Npad + i) * kAtomBlock);
-            const int kend = min(kAtomBlock, K - kb * kAtomBlock);
-#pragma unroll 1
-            for (int kk = 0; kk < kAtomBlock; ++kk) {
-                const int k = kb * kAtomBlock + kk;
-                float w_new = w0;   // padding atoms keep their zero
-                if (kk < kend) {
-                    const float* dk = Ds + k;
-                    float n = 0.0f, h = 0.0f;
-#pragma unroll
-                    for (int j = 0; j < MAXOBS; ++j) {
-                        if ((j & 3) == 0 && j >= wmax) break;
-                        const float d = dk[offK[j]];
-                        n = fmaf(d, d, n);
-                        h = fmaf(d, r[j], h);
-                    }
-                    const float w_old = w0;
-                    const float g = fmaf(w_old, n, h);
-                    const float lam = fmaf(ge, n, gs);
-                    const float rlam = __fdividef(1.0f, lam);
-                    const float L = lpi[k] + half_log_gs - 0.5f * __logf(lam) + half_ge2 * g * g * rlam;
-                    const float sig = __fdividef(1.0f, 1.0f + __expf(-L));
-                    const unsigned long long thr = (unsigned long long)(sig * 4294967296.0f);
-                    const uint4 blk = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)k, a.t, kTagCodes), a.keys);
-                    const bool z = valid && ((unsigned long long)blk.x < thr);
-                    w_new = 0.0f;
-                    if (z) {
-                        w_new = fmaf(normal32(blk.y, blk.z), sqrtf(rlam), ge * g * rlam);
-                        s2 = fmaf(w_new, w_new, s2);
-                        act_n += 1;
-                    }
-                    const float dw = w_new - w_old;
-                    if (dw != 0.0f) {
-                        chg_n += 1;
-                        chg_obs += (unsigned int)nobs;
-#pragma unroll
-                        for (int j = 0; j < MAXOBS; ++j) {
-                            if ((j & 3) == 0 && j >= wmax) break;
-                            r[j] = fmaf(-dk[offK[j]], dw, r[j]);
-                        }
-                    }
-                    const uint32_t bal = __ballot_sync(0xffffffffu, z);
-                    if (lane == 0) {
-                        a.Zb[(long long)k * NW + chunk] = bal;
-                        mycnt[k] += __popc(bal);
-                    }
-                }
-                w0 = w1; w1 = w2; w2 = w3; w3 = w4; w4 = w5; w5 = w6; w6 = w7; w7 = w_new;
-            }
+            const int kbase = kb * kAtomBlock;
+            code_block<MAXOBS>(Ds + kbase, lpi + kbase, offK, r, wmax, nobs, i, valid, kbase,
+                               min(kAtomBlock, K - kbase), c, a.keys, a.t, a.Zb, NW, chunk, lane, mycnt + kbase,
+                               w0, w1, w2, w3, w4, w5, w6, w7, s2, tl);
             store_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock, w0, w1, w2, w3, w4, w5, w6, w7);
         }
-
-        // scatter the residual to the per-pixel slots; squared norm
-        float r2 = 0.0f;
-#pragma unroll
-        for (int j = 0; j < MAXOBS; ++j) {
-            if (j >= wmax) break;
-            if (j < nobs) {
-                if (a.R) {
-                    const int p = a.obs[(long long)j * N + i];
-                    const long long wd = (long long)p * NW + chunk;
-                    const uint32_t ib = a.Ibits[wd];
-                    const int slot = a.Rbase[p] + (int)a.Ipre[wd] + __popc(ib & ((1u << lane) - 1u));
-                    a.R[slot] = r[j];
-                }
-                r2 = fmaf(r[j], r[j], r2);
-            }
-        }
-        double s2d = warp_sum((double)s2);
-        double r2d = warp_sum((double)r2);
-        if (lane == 0) {
-            a.part_s2[chunk] = s2d;
-            a.part_r2[chunk] = r2d;
-        }
+        finish_patch<MAXOBS>(a, r, wmax, nobs, i, chunk, lane, s2);
     }
-    // this warp's counts: per-atom actives and the work counters
-    __syncwarp();
-    for (int k = lane; k < K; k += 32)
-        if (mycnt[k]) atomicAdd(&a.m[k], mycnt[k]);
-    unsigned long long cn = chg_n, co = chg_obs, ca = act_n;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        cn += __shfl_down_sync(0xffffffffu, cn, o);
-        co += __shfl_down_sync(0xffffffffu, co, o);
-        ca += __shfl_down_sync(0xffffffffu, ca, o);
-    }
-    if (lane == 0 && (cn | ca)) {
-        atomicAdd(&a.sc_out->chg_n, cn);
-        atomicAdd(&a.sc_out->chg_obs, co);
-        atomicAdd(&a.sc_out->act_n, ca);
-    }
+    flush_counts(a, mycnt, lane, tl);
 }
 
 int sweep_block_size() { return kSweepThreads; }
@@ -228,6 +122,8 @@ static void* select_kernel(int maxobs)
     if (maxobs <= 40) return kernel_ptr<40>();
     if (maxobs <= 48) return kernel_ptr<48>();
     if (maxobs <= 64) return kernel_ptr<64>();
+    if (maxobs <= 72) return kernel_ptr<72>();
+    if (maxobs <= 80) return kernel_ptr<80>();
     if (maxobs <= 96) return kernel_ptr<96>();
     if (maxobs <= 128) return kernel_ptr<128>();
     return nullptr;

@@ -82,6 +82,8 @@ class sensai_stats(ctypes.Structure):
         ("changed_updates", ctypes.c_int64),
         ("changed_observed", ctypes.c_int64),
         ("active_draws", ctypes.c_int64),
+        ("slice_atoms", ctypes.c_int32),
+        ("slices", ctypes.c_int32),
     ]
 
 
@@ -164,6 +166,14 @@ def _buf(a, dtype, count=None, name="buffer"):
     if count is not None and a.numel() != count:
         raise ValueError(f"{name}: need {count} elements, got {a.numel()}")
     return a.data_ptr()
+
+
+SENSAI_FLAG_STREAM_DICTIONARY = 0x1
+
+
+def SENSAI_SLICE_ATOMS(n):
+    """flags bits fixing the streamed dictionary slice at n atoms (n a multiple of 8)."""
+    return ((int(n) // 8) & 0xFF) << 8
 
 
 def make_params(M, B, stride, K, *, a=0.0, b=0.0, c=1e-6, d=1e-6, e=1e-6, f=1e-6, seed=0, flags=0):

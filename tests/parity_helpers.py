@@ -45,13 +45,13 @@ def round_state(st):
     return st
 
 
-def gpu_context(prm, mask):
+def gpu_context(prm, mask, flags=0):
     from paper_2311_15061_gb300 import sensai
     M = [prm.M[i] for i in range(prm.ndim)]
     B = [prm.B[i] for i in range(prm.ndim)]
     S = [prm.S[i] for i in range(prm.ndim)]
     p = sensai.make_params(M, B, S, prm.K, a=prm.a, b=prm.b, c=prm.c, d=prm.d, e=prm.e, f=prm.f,
-                           seed=prm.seed)
+                           seed=prm.seed, flags=flags)
     return sensai.Context(p, mask)
 
 

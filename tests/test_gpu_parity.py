@@ -12,6 +12,10 @@ with the tolerances stated in parity_helpers:
   dictionary and hyper-parameter draws in full;
 * edge cases: ragged patch counts, 1-D and 3-D frames with strides, K = 1,
   full masks, an empty mask, determinism;
+* the streamed code sweep (dictionary in atom slices through shared memory):
+  forced on the 128x128 workload with refilled and with resident slices,
+  ragged slices, and the 3-D / 2-D K = 256, P = 256 dictionaries that do not
+  fit in shared memory; learning is bit-identical to the resident sweep;
 * end to end: PSNR of the learned reconstruction within 0.1 dB of the
   oracle's, averaged over seeds 0-4; the same for dictionary transfer.
 """
@@ -37,10 +41,12 @@ def _built():
 C1 = dict(M=(128, 128), B=(8, 8), S=(1, 1), K=64, frac=0.25)
 
 
-def _phase_parity(M, B, S, K, frac, seed=0, warm=2, full_mask=False, check_flips=True):
+def _phase_parity(M, B, S, K, frac, seed=0, warm=2, full_mask=False, check_flips=True, flags=0, slices=None):
     prm, x, clean, mask = problem(M, B, S, K, frac, seed, full_mask=full_mask)
     st = oracle_state(prm, x, mask, warm)
-    ctx = gpu_context(prm, mask)
+    ctx = gpu_context(prm, mask, flags)
+    if slices is not None:   # the code sweep streams the dictionary in this many slices
+        assert ctx.sensai_get_stats().slices == slices
 
     # a1 + a2: code sweep
     push_state(ctx, st, x)
@@ -278,3 +284,64 @@ def test_device_buffers_and_streams():
             outs.append(ctx.sensai_reconstruct())
         ctx.close()
     np.testing.assert_array_equal(outs[0], outs[1])
+
+
+# --- streamed dictionary: the code sweep with the dictionary in atom slices ---
+
+def _stream(n):
+    from paper_2311_15061_gb300 import sensai
+    return sensai.SENSAI_FLAG_STREAM_DICTIONARY | sensai.SENSAI_SLICE_ATOMS(n)
+
+
+@pytest.mark.parametrize("slice_atoms,slices", [(8, 8), (24, 3), (32, 2)])
+def test_streamed_sweep_128x128_k64(slice_atoms, slices):
+    """8 and 3 slices refill the two buffers every use; 2 slices stay resident."""
+    _phase_parity(**C1, warm=1, flags=_stream(slice_atoms), slices=slices)
+
+
+def test_streamed_sweep_ragged_slices():
+    """K = 28 pads to 32 atoms; 16-atom slices, the last one half padding."""
+    _phase_parity(M=(37, 45), B=(5, 4), S=(1, 1), K=28, frac=0.3, flags=_stream(16), slices=2)
+    _phase_parity(M=(37, 45), B=(5, 4), S=(1, 1), K=28, frac=0.3, flags=_stream(8), slices=4)
+
+
+@pytest.mark.parametrize("case", [
+    dict(M=(20, 20, 12), B=(8, 8, 4), S=(1, 1, 2), K=256, frac=0.2),   # 3-D video patches, P = 256
+    dict(M=(48, 48), B=(16, 16), S=(1, 1), K=256, frac=0.1),           # 2-D, P = 256
+])
+def test_large_dictionary_streams(case):
+    """K (P + 1) floats beyond shared memory: streamed without any flag."""
+    prm, x, clean, mask = problem(case["M"], case["B"], case["S"], case["K"], case["frac"])
+    ctx = gpu_context(prm, mask)
+    st = ctx.sensai_get_stats()
+    assert st.slice_atoms > 0 and st.slices >= 3, (st.slice_atoms, st.slices)
+    ctx.close()
+    _phase_parity(**case, warm=1)
+
+
+def test_streamed_learning_is_bit_identical_to_resident():
+    """Same arithmetic in the same order: whole learning runs agree bit for bit."""
+    prm, x, clean, mask = problem((96, 80), (8, 8), (1, 1), 40, 0.25, seed=3)
+    states = []
+    for flags in (0, _stream(8), _stream(16)):
+        ctx = gpu_context(prm, mask, flags)
+        ctx.sensai_learn(x, 3)
+        g = ctx.sensai_get_state()
+        g["rec"] = ctx.sensai_reconstruct()
+        states.append(g)
+        ctx.close()
+    for g in states[1:]:
+        for key in ("D", "Z", "S", "pi", "rec"):
+            np.testing.assert_array_equal(g[key], states[0][key], err_msg=key)
+        assert g["gamma_s"] == states[0]["gamma_s"] and g["gamma_eps"] == states[0]["gamma_eps"]
+
+
+def test_flags_validation():
+    from paper_2311_15061_gb300 import sensai
+    prm, x, clean, mask = problem((40, 40), (8, 8), (1, 1), 16, 0.25)
+    for bad in (0x2, sensai.SENSAI_SLICE_ATOMS(8)):   # unknown bit; slice without streaming
+        with pytest.raises(sensai.SensaiError) as err:
+            gpu_context(prm, mask, bad)
+        assert err.value.status == sensai.SENSAI_EINVAL
+    with pytest.raises(sensai.SensaiError):          # slice larger than the padded K
+        gpu_context(prm, mask, _stream(24))
