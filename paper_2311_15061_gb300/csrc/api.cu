@@ -82,17 +82,9 @@ struct sensai_ctx {
     double* part_r2 = nullptr;
     unsigned int* chunk_counter = nullptr;
     DevScalars* sc = nullptr;
-    // space-tiled dictionary sweep (cooperative launch), when it fits
-    int* obs_px = nullptr;      // observed frame pixels in raster order
-    long long n_obs_px = 0;
-    float* dpart = nullptr;     // [grid][44][P]
-    float* ddelta = nullptr;    // [P][8]
-    unsigned int* dbar = nullptr;
+    int* pos = nullptr;         // [maxobs][N] residual position of each observed pixel of each patch
+    DictSpacePlan ds{};         // space-organised dictionary sweep (cooperative launch), when it runs
     ServeEngine* serve = nullptr;   // live serving engine, when started
-    int ds_grid = 0;
-    int ds_tile = 0;
-    int ds_own = 0;
-    size_t ds_smem = 0;
 };
 
 namespace {
@@ -132,9 +124,10 @@ void free_all(sensai_ctx* c)
 {
     void* ptrs[] = {c->mask_bits, c->imgoff, c->nobs, c->obs, c->Ibits, c->Ipre, c->Icnt, c->Rbase, c->Ilist,
                     c->misc, c->x, c->D, c->W, c->Zb, c->R, c->Y, c->out, c->pi, c->lpi, c->m,
-                    c->part_s2, c->part_r2, c->chunk_counter, c->sc, c->obs_px, c->dpart, c->ddelta, c->dbar, c->Dsl};
+                    c->part_s2, c->part_r2, c->chunk_counter, c->sc, c->pos, c->Dsl};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    ds_free(&c->ds);
 }
 
 enum Phase { kPhaseCodes = 0, kPhaseDict = 1, kPhaseHyper = 2, kPhaseRecon = 3 };
@@ -212,7 +205,7 @@ sensai_status ensure_residual(sensai_ctx* ctx, cudaStream_t s)
 {
     if (ctx->resid_valid) return SENSAI_OK;
     SENSAI_CUDA(ctx, launch_residual(ctx->g, ctx->x, ctx->obs, ctx->nobs, ctx->imgoff, ctx->D, ctx->W, ctx->Zb,
-                                     ctx->Ibits, ctx->Ipre, ctx->Rbase, ctx->R, ctx->part_r2, s));
+                                     ctx->pos, ctx->R, ctx->part_r2, s));
     ctx->launches += 1;
     ctx->resid_valid = true;
     ctx->n_r2 = ctx->g.NW;
@@ -244,9 +237,7 @@ sensai_status run_sweep(sensai_ctx* ctx, cudaStream_t s)
     a.Zb = ctx->Zb;
     a.lpi = ctx->lpi;
     a.sc = ctx->sc;
-    a.Ibits = ctx->Ibits;
-    a.Ipre = ctx->Ipre;
-    a.Rbase = ctx->Rbase;
+    a.pos = ctx->pos;
     a.R = ctx->R;
     a.m = ctx->m;
     a.part_s2 = ctx->part_s2;
@@ -273,31 +264,28 @@ sensai_status run_dictionary(sensai_ctx* ctx, cudaStream_t s)
     if (st != SENSAI_OK) return st;
     st = ensure_residual(ctx, s);
     if (st != SENSAI_OK) return st;
-    if (ctx->ds_grid > 0) {
+    if (ctx->ds.grid > 0) {
         DictSpaceArgs a{};
         a.g = ctx->g;
         a.D = ctx->D;
         a.W = ctx->W;
-        a.Ibits = ctx->Ibits;
-        a.Ipre = ctx->Ipre;
-        a.Rbase = ctx->Rbase;
         a.R = ctx->R;
+        a.pidx = ctx->ds.pidx;
+        a.np = ctx->ds.np;
+        a.base = ctx->ds.base;
         a.sc = ctx->sc;
         a.part_r2 = ctx->part_r2;
-        a.part = ctx->dpart;
-        a.delta = ctx->ddelta;
-        a.bar = ctx->dbar;
-        a.obs_px = ctx->obs_px;
-        a.n_obs_px = ctx->n_obs_px;
-        a.max_tile = ctx->ds_tile;
-        a.own_max = ctx->ds_own;
+        a.part = ctx->ds.part;
+        a.delta = ctx->ds.delta;
+        a.bar = ctx->ds.bar;
+        a.own_max = ctx->ds.own_max;
         a.seed = ctx->prm.seed;
         a.t = (uint32_t)ctx->t;
         PhaseTimer timer(ctx, kPhaseDict, s);
-        SENSAI_CUDA(ctx, launch_dict_space(a, ctx->ds_grid, ctx->ds_smem, s));
+        SENSAI_CUDA(ctx, launch_dict_space(a, ctx->ds, s));
         timer.stop();
         ctx->launches += 1;
-        ctx->n_r2 = ctx->ds_grid;
+        ctx->n_r2 = ctx->ds.grid;
         return SENSAI_OK;
     }
     DictArgs a{};
@@ -492,16 +480,25 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     CREATE_CUDA(cudaMemcpy(&total, ctx->Rbase + P, sizeof(int), cudaMemcpyDeviceToHost));
     CREATE_CUDA(cudaMemcpy(&ctx->max_slots, ctx->misc + 1, sizeof(int), cudaMemcpyDeviceToHost));
     ctx->n_observed = total;
-    CREATE_CUDA(dalloc(&ctx->Ilist, (size_t)total));
-    CREATE_CUDA(launch_ilist(g, ctx->Ibits, ctx->Ipre, ctx->Rbase, ctx->Ilist, st0));
-    ctx->launches += 1;
+    // residual layout: the pairs of the space-organised dictionary sweep when
+    // it runs, else the per-pixel slots of the per-chain kernel
+    CREATE_CUDA(dalloc(&ctx->pos, (size_t)(ctx->maxobs > 0 ? ctx->maxobs : 1) * N));
+    CREATE_CUDA(ds_build(g, mask, ctx->obs, ctx->nobs, device, ctx->pos, &ctx->R, &ctx->ds, st0));
+    if (ctx->ds.grid > 0) {
+        ctx->launches += 2;
+    } else {
+        CREATE_CUDA(dalloc(&ctx->Ilist, (size_t)total));
+        CREATE_CUDA(launch_ilist(g, ctx->Ibits, ctx->Ipre, ctx->Rbase, ctx->Ilist, st0));
+        CREATE_CUDA(dalloc(&ctx->R, (size_t)total));
+        CREATE_CUDA(launch_pos_slots(g, ctx->obs, ctx->nobs, ctx->Ibits, ctx->Ipre, ctx->Rbase, ctx->pos, st0));
+        ctx->launches += 2;
+    }
 
     CREATE_CUDA(dalloc(&ctx->x, (size_t)nframe));
     CREATE_CUDA(dalloc(&ctx->out, (size_t)nframe));
     CREATE_CUDA(dalloc(&ctx->D, (size_t)g.K * P));
     CREATE_CUDA(dalloc(&ctx->W, (size_t)g.KB * kAtomBlock * g.Npad));
     CREATE_CUDA(dalloc(&ctx->Zb, (size_t)g.K * g.NW));
-    CREATE_CUDA(dalloc(&ctx->R, (size_t)total));
     CREATE_CUDA(dalloc(&ctx->Y, (size_t)P * N));
     CREATE_CUDA(dalloc(&ctx->pi, (size_t)g.K));
     CREATE_CUDA(dalloc(&ctx->lpi, (size_t)g.K));
@@ -516,32 +513,6 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     }
     CREATE_CUDA(dalloc(&ctx->chunk_counter, 1));
     CREATE_CUDA(dalloc(&ctx->sc, 1));
-    // space-tiled dictionary sweep: observed pixels, per-CTA sums, barrier
-    {
-        int nobs_px = 0;
-        CREATE_CUDA(dalloc(&ctx->obs_px, (size_t)nframe));
-        CREATE_CUDA(launch_obs_px(nframe, ctx->mask_bits, ctx->obs_px, st0));
-        ctx->launches += 1;
-        CREATE_CUDA(cudaDeviceSynchronize());
-        // count = number of observed pixels (host copy of the mask is the source)
-        for (long long u = 0; u < nframe; ++u) nobs_px += mask[u] != 0;
-        ctx->n_obs_px = nobs_px;
-        const int grid = sms;
-        const int tile = (int)((nobs_px + grid - 1) / grid) + 1;
-        const int own = (int)((P + grid - 1) / grid);
-        const size_t smem = dict_space_smem_bytes(g, tile, tile * (int)P, own);
-        const int ds = (nobs_px > 0) ? dict_space_grid(g, smem, device) : 0;
-        if (ds > 0) {
-            CREATE_CUDA(dalloc(&ctx->dpart, (size_t)ds * 44 * P));
-            CREATE_CUDA(dalloc(&ctx->ddelta, (size_t)P * 8));
-            CREATE_CUDA(dalloc(&ctx->dbar, 2));
-            CREATE_CUDA(cudaMemset(ctx->dbar, 0, 2 * sizeof(unsigned int)));
-            ctx->ds_grid = ds;
-            ctx->ds_tile = tile;
-            ctx->ds_smem = smem;
-            ctx->ds_own = own;
-        }
-    }
     {
         const bool stream = (p.flags & SENSAI_FLAG_STREAM_DICTIONARY) != 0;
         const int slice = ((p.flags >> 8) & 0xff) * kAtomBlock;

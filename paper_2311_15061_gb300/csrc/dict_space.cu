@@ -1,28 +1,39 @@
 // dict_space.cu -- the dictionary sweep organised by space.
 //
-// Same draws as dict.cu (the atom-ordered conjugate Gaussian of every d_kp,
-// in 8-atom blocks with the in-block Gram correction), but the work is split
-// over the frame instead of over pixel chains.  A pair (u, q) -- an observed
+// Same draws as dict.cu: the atom-ordered conjugate Gaussian of every d_kp, in
+// 8-atom blocks with the in-block Gram correction.  The work is split over
+// the frame instead of over pixel chains.  A pair (u, q) -- an observed
 // frame pixel u and a within-patch pixel q such that u - q is a patch origin
-// -- is one residual slot of chain q.  CTA c owns a contiguous range of
-// observed pixels in raster order; inside it, a thread owns one chain q and a
-// sub-range of those pixels, so its pairs are consecutive slots of chain q
-// (slots are ranked by patch index, which grows with u).  For one pixel u the
-// ~P patches covering it form a small neighbourhood of the patch grid, whose
-// 32-byte weight records are contiguous rows that the next pixels reuse: the
-// gathers of the per-chain kernel become local, mostly L1-resident reads, and
-// every SM takes part.
+// -- is one residual slot of chain q.
 //
-// Per 8-atom block: (1) every thread accumulates G_k = sum w_k r and the
-// in-block Gram C_kl over its pairs (after applying the previous block's
-// update); (2) the CTA sums its threads per chain in a fixed order and
-// publishes the partial; (3) grid barrier; (4) CTA c sums the partials of
-// chains c, c + grid, ... over all CTAs in a fixed order (FP64) and draws the
-// block's 8 atoms at those pixels; (5) grid barrier; (6) every thread reads
-// its chain's 8 updates.
+// Layout (planned once per context, on the host and by the two planning
+// kernels below):
+//  * the observed pixels are split into one spatial box per CTA, balanced by
+//    count (recursive bisection).  Inside a box they are ordered tile by tile
+//    (tiles of min(B_d, 8) pixels per dimension), raster order within a tile;
+//  * a thread owns one chain q and every G-th pixel of its CTA's list
+//    (G = 512 / P groups), so at any moment the CTA works on a few
+//    neighbouring pixels.  The ~P patches covering them are a small
+//    neighbourhood of the patch grid whose 32-byte weight records stay in L1;
+//  * pair jp of thread t in CTA c is element base_c + jp * 512 + t of the
+//    residual array R and of the patch-index array pidx.  Threads of a warp
+//    therefore touch consecutive words; the sweep writes its residuals
+//    straight into this layout through a (pixel, patch) -> pair table.
+//
+// Per 8-atom block: (1) every thread applies the previous block's update to
+// its residual pairs (shared memory when they fit, else global memory) and
+// accumulates G_k = sum w_k r and the in-block Gram C_kl over them; (2) the
+// CTA sums its threads per chain in a fixed order and publishes the partial;
+// (3) grid barrier; (4) CTA c sums the partials (stored chain-major, so one
+// owner reads one contiguous block) of chains c, c + grid, ...
+// over all CTAs in a fixed order (FP64) and draws the block's 8 atoms at those
+// pixels; (5) grid barrier; (6) every thread reads its chain's 8 updates.
 // One cooperative launch, one CTA per SM; the barrier spins are bounded and
 // report SENSAI_ETIMEOUT through the status word instead of hanging.
 #include "internal.cuh"
+
+#include <algorithm>
+#include <vector>
 
 namespace sensai {
 
@@ -32,33 +43,28 @@ constexpr int kDSRed = kAtomBlock + kDSGram;                  // 44
 constexpr int kDSRedPad = kDSRed + 1;                          // smem row pitch (odd)
 constexpr long long kBarrierSpins = 1LL << 24;               // x ~64 ns sleep: ~1 s
 
-// Sense-free grid barrier on a (count, generation) pair: the last CTA to
-// arrive resets the count and bumps the generation.  Returns false (and sets
-// *status) if the generation does not move within the spin limit.
-__device__ bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned int nblocks, int* status)
+// Grid barrier on a monotonic arrival counter (zeroed by the host before
+// every launch): barrier number n of the launch waits until the counter reaches
+// (n + 1) * nblocks.  One atomic per CTA and a poll; no reset round trips.
+// Returns false (and sets *status) if it does not complete within the spin
+// limit.
+__device__ bool grid_barrier(unsigned int* count, unsigned int target, int* status)
 {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned int* vgen = gen;
-        const unsigned int g0 = *vgen;
         __threadfence();
-        const unsigned int arrived = atomicAdd(count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == g0) {
-                if (++spins > kBarrierSpins) {
-                    atomicExch(status, (int)SENSAI_ETIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
+        atomicAdd(count, 1u);
+        volatile unsigned int* vc = count;
+        long long spins = 0;
+        while (*vc < target) {
+            if (++spins > kBarrierSpins) {
+                atomicExch(status, (int)SENSAI_ETIMEOUT);
+                ok = 0;
+                break;
             }
+            __nanosleep(32);
         }
         __threadfence();
         ok_s = ok;
@@ -67,16 +73,103 @@ __device__ bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned in
     return ok_s != 0;
 }
 
+// Within-patch multi-index of chain q.
+__device__ __forceinline__ void chain_index(const Geom& g, int q, int* qd)
+{
+    for (int d = g.ndim - 1; d >= 0; --d) {
+        qd[d] = q % g.B[d];
+        q /= g.B[d];
+    }
+}
+
+// Patch whose pixel qd is frame pixel u, or -1.
+__device__ __forceinline__ long long pair_patch(const Geom& g, long long u, const int* qd)
+{
+    int cd[kMaxDim];
+    for (int d = g.ndim - 1; d >= 0; --d) {
+        cd[d] = (int)(u % g.M[d]);
+        u /= g.M[d];
+    }
+    long long i = 0;
+    for (int d = 0; d < g.ndim; ++d) {
+        int av = cd[d] - qd[d];
+        if (av < 0) return -1;
+        if (g.S[d] != 1) {
+            if (av % g.S[d]) return -1;
+            av /= g.S[d];
+        }
+        if (av >= g.G[d]) return -1;
+        i = i * g.G[d] + av;
+    }
+    return i;
+}
+
+// Planning pass 1: pairs per thread and the largest count per CTA.
+__global__ void __launch_bounds__(kDSThreads) ds_count_kernel(Geom g, const int* order, const int* start, int* np,
+                                                              int* npmax)
+{
+    __shared__ int wmax[kDSThreads / 32];
+    const int c = blockIdx.x, t = threadIdx.x;
+    const int G = kDSThreads / g.P;
+    const bool active = t < G * g.P;
+    int n = 0;
+    if (active) {
+        const int grp = t / g.P, q = t % g.P;
+        int qd[kMaxDim];
+        chain_index(g, q, qd);
+        const int lo = start[c], L = start[c + 1] - lo;
+        for (int j = grp; j < L; j += G)
+            if (pair_patch(g, order[lo + j], qd) >= 0) ++n;
+    }
+    np[(size_t)c * kDSThreads + t] = n;
+    const int m = __reduce_max_sync(0xffffffffu, n);
+    if ((t & 31) == 0) wmax[t >> 5] = m;
+    __syncthreads();
+    if (t == 0) {
+        int mx = 0;
+        for (int w = 0; w < kDSThreads / 32; ++w) mx = max(mx, wmax[w]);
+        npmax[c] = mx;
+    }
+}
+
+// Planning pass 2: the patch of every pair and, for the sweep, the pair of
+// every (observed pixel j, patch i): pos[j][i].
+__global__ void __launch_bounds__(kDSThreads) ds_fill_kernel(Geom g, const int* order, const int* start,
+                                                             const long long* base, const uint16_t* obs,
+                                                             const uint16_t* nobs, int* pidx, int* pos)
+{
+    const int c = blockIdx.x, t = threadIdx.x;
+    const int G = kDSThreads / g.P;
+    if (t >= G * g.P) return;
+    const int grp = t / g.P, q = t % g.P;
+    int qd[kMaxDim];
+    chain_index(g, q, qd);
+    const int lo = start[c], L = start[c + 1] - lo;
+    long long idx = base[c] + t;
+    for (int j = grp; j < L; j += G) {
+        const long long i = pair_patch(g, order[lo + j], qd);
+        if (i < 0) continue;
+        pidx[idx] = (int)i;
+        const int no = nobs[i];
+        for (int jj = 0; jj < no; ++jj)
+            if (obs[(long long)jj * g.N + i] == q) {
+                pos[(long long)jj * g.N + i] = (int)idx;
+                break;
+            }
+        idx += kDSThreads;
+    }
+}
+
+template <bool RHO_SMEM>
 __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpaceArgs a)
 {
     extern __shared__ float dyn[];
     __shared__ float dold8[kAtomBlock];
     __shared__ double fin[kDSRed];
     __shared__ double tmp[kDSRed][11];
-    __shared__ int scan_s[kDSThreads / 32];
     __shared__ float r2_s[kDSThreads / 32];
     const Geom& g = a.g;
-    const int P = g.P, K = g.K, KB = g.KB, nd = g.ndim;
+    const int P = g.P, K = g.K, KB = g.KB;
     const long long Npad = g.Npad;
     const int c = blockIdx.x, ncta = gridDim.x;
     const int G = kDSThreads / P;                    // groups of P threads
@@ -84,84 +177,17 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
     const bool active = t < G * P;
     const int grp = active ? t / P : 0, q = active ? t % P : 0;
     const int lane = t & 31, warp = t >> 5;
+    constexpr int T = kDSThreads;
 
-    // this CTA's observed pixels and this thread's sub-range of them
-    const long long n0 = (long long)a.n_obs_px * c / ncta, n1 = (long long)a.n_obs_px * (c + 1) / ncta;
-    const int L = (int)(n1 - n0);
-    const int s0 = (int)((long long)L * grp / G), s1 = active ? (int)((long long)L * (grp + 1) / G) : s0;
-    int* coord = reinterpret_cast<int*>(dyn);                      // [L][nd] multi-indices
-    float* red = reinterpret_cast<float*>(coord + (size_t)a.max_tile * nd);   // [G-1][P][44]
-    float* rho = red + (size_t)(kDSThreads / P - 1) * P * kDSRedPad;          // this CTA's pairs
-    int* pidx = reinterpret_cast<int*>(rho + (size_t)a.max_tile * P);         // their patch indices
-    float* xis = reinterpret_cast<float*>(pidx + (size_t)a.max_tile * P);     // normals of owned chains
-    for (int j = t; j < L; j += blockDim.x) {
-        long long u = a.obs_px[n0 + j];
-        for (int d = nd - 1; d >= 0; --d) {
-            coord[j * nd + d] = (int)(u % g.M[d]);
-            u /= g.M[d];
-        }
-    }
-    int qd[kMaxDim];
-    {
-        int rem = q;
-        for (int d = nd - 1; d >= 0; --d) {
-            qd[d] = rem % g.B[d];
-            rem /= g.B[d];
-        }
-    }
-    __syncthreads();
-
-    // patch index of pair (tile pixel j, chain q), or -1
-    auto patch_of = [&](int j) -> long long {
-        long long i = 0;
-        for (int d = 0; d < nd; ++d) {
-            int av = coord[j * nd + d] - qd[d];
-            if (av < 0) return -1;
-            if (g.S[d] != 1) {
-                if (av % g.S[d]) return -1;
-                av /= g.S[d];
-            }
-            if (av >= g.G[d]) return -1;
-            i = i * g.G[d] + av;
-        }
-        return i;
-    };
-
-    // count this thread's pairs; exclusive scan gives its residual offset
-    int np = 0;
-    long long first_i = -1;
-    for (int j = s0; j < s1; ++j) {
-        const long long i = patch_of(j);
-        if (i >= 0) {
-            if (np == 0) first_i = i;
-            ++np;
-        }
-    }
-    int incl = np;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) scan_s[warp] = incl;
-    __syncthreads();
-    int wbase = 0;
-    for (int w = 0; w < warp; ++w) wbase += scan_s[w];
-    const int ro = wbase + incl - np;           // offset of this thread's pairs in rho
-    int slot0 = 0;
-    if (np > 0) {
-        const long long wd = (long long)q * g.NW + (first_i >> 5);
-        slot0 = a.Rbase[q] + (int)a.Ipre[wd] + __popc(a.Ibits[wd] & ((1u << (first_i & 31)) - 1u));
-        int jp = 0;
-        for (int j = s0; j < s1; ++j) {
-            const long long i = patch_of(j);
-            if (i < 0) continue;
-            rho[ro + jp] = a.R[slot0 + jp];
-            pidx[ro + jp] = (int)i;
-            ++jp;
-        }
-    }
-    // normals of this CTA's chains (c, c + grid, ...), off the sequential path
+    float* red = dyn;                                               // [G-1][P][kDSRedPad]
+    float* xis = red + (size_t)(G - 1) * P * kDSRedPad;            // [own_max][K] normals of owned chains
+    float* rho_s = xis + (size_t)a.own_max * K;                      // [max_np][T] staged residual pairs
+    const long long base = a.base[c];
+    const int np = a.np[(size_t)c * T + t];                         // 0 for idle threads
+    const int* pid = a.pidx + base + t;                             // pair jp: pid[jp * T]
+    float* rho = RHO_SMEM ? rho_s + t : a.R + base + t;            // pair jp: rho[jp * T]
+    if (RHO_SMEM)
+        for (int jp = 0; jp < np; ++jp) rho[(size_t)jp * T] = a.R[base + t + (long long)jp * T];
     for (int idx = t; idx < a.own_max * K; idx += blockDim.x) {
         const int o = idx / K, k = idx % K;
         const int ch = c + o * ncta;
@@ -189,10 +215,14 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
         const bool has_prev = kb > 0, has_cur = kb < KB;
         W8 ua, va, ub, vb;
         float ra = 0.0f, rb = 0.0f;
-#define DS_LOAD(J_, R_, U, V)                                              \
+        // each register set's next patch index is loaded one loop iteration
+        // (two pairs) before the weight loads that use it
+        int pa = np > 0 ? pid[0] : 0, pb = np > 1 ? pid[(size_t)T] : 0;
+#define DS_LOAD(J_, R_, U, V, PX)                                          \
         do {                                                               \
-            const long long i_ = pidx[ro + (J_)];                          \
-            R_ = rho[ro + (J_)];                                           \
+            const long long i_ = PX;                                       \
+            PX = (J_) + 2 < np ? pid[(size_t)((J_) + 2) * T] : 0;          \
+            R_ = rho[(size_t)(J_) * T];                                    \
             if (has_prev) U = load_w8(qprev + i_ * kAtomBlock);            \
             if (has_cur) V = load_w8(qcur + i_ * kAtomBlock);              \
         } while (0)
@@ -201,7 +231,7 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
             if (has_prev) {                                                \
                 _Pragma("unroll") for (int k = 0; k < kAtomBlock; ++k)     \
                     R_ = fmaf(-dq[k], U.v[k], R_);                         \
-                rho[ro + (J_)] = R_;                                       \
+                rho[(size_t)(J_) * T] = R_;                                \
             }                                                              \
             if (has_cur) {                                                 \
                 _Pragma("unroll") for (int k = 0; k < kAtomBlock; ++k) {   \
@@ -212,12 +242,12 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
                 }                                                          \
             }                                                              \
         } while (0)
-        if (np > 0) DS_LOAD(0, ra, ua, va);
+        if (np > 0) DS_LOAD(0, ra, ua, va, pa);
         for (int jp = 0; jp < np; jp += 2) {
-            if (jp + 1 < np) DS_LOAD(jp + 1, rb, ub, vb);
+            if (jp + 1 < np) DS_LOAD(jp + 1, rb, ub, vb, pb);
             DS_APPLY(jp, ra, ua, va);
             if (jp + 1 >= np) break;
-            if (jp + 2 < np) DS_LOAD(jp + 2, ra, ua, va);
+            if (jp + 2 < np) DS_LOAD(jp + 2, ra, ua, va, pa);
             DS_APPLY(jp + 1, rb, ub, vb);
         }
 #undef DS_LOAD
@@ -236,13 +266,13 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
                 for (int v = 0; v < kDSRed; ++v) acc[v] += red[((size_t)(h - 1) * P + q) * kDSRedPad + v];
             }
 #pragma unroll
-            for (int v = 0; v < kDSRed; ++v) a.part[((size_t)c * kDSRed + v) * P + q] = acc[v];
+            for (int v = 0; v < kDSRed; ++v) a.part[((size_t)q * ncta + c) * kDSRed + v] = acc[v];
         }
         __threadfence();
-        if (!grid_barrier(a.bar, a.bar + 1, (unsigned int)ncta, &a.sc->status)) return;
+        if (!grid_barrier(a.bar, (unsigned int)(2 * kb + 1) * ncta, &a.sc->status)) return;
 
         // chains c, c + grid, ...: fixed-order FP64 sums of the CTA partials,
-        // the block's 8 normals in parallel, then the 8 sequential draws
+        // then the 8 sequential draws
         for (int ch = c; ch < P; ch += ncta) {
             // 11 groups of CTAs per value; each thread's loads are issued
             // together (independent), then summed in order
@@ -255,7 +285,7 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
                     float x[16];
 #pragma unroll
                     for (int u = 0; u < 16; ++u)
-                        x[u] = (cb + u < c1) ? __ldcg(&a.part[((size_t)(cb + u) * kDSRed + v) * P + ch]) : 0.0f;
+                        x[u] = (cb + u < c1) ? __ldcg(&a.part[((size_t)ch * ncta + cb + u) * kDSRed + v]) : 0.0f;
 #pragma unroll
                     for (int u = 0; u < 16; ++u) sum += (double)x[u];
                 }
@@ -291,7 +321,7 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
             __syncthreads();
         }
         __threadfence();
-        if (!grid_barrier(a.bar, a.bar + 1, (unsigned int)ncta, &a.sc->status)) return;
+        if (!grid_barrier(a.bar, (unsigned int)(2 * kb + 2) * ncta, &a.sc->status)) return;
         if (active) {
 #pragma unroll
             for (int k = 0; k < kAtomBlock; ++k) dq[k] = __ldcg(&a.delta[q * kAtomBlock + k]);
@@ -300,9 +330,9 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
 
     // write the residual back; this CTA's share of sum ||r||^2
     float r2 = 0.0f;
-    for (int j = 0; j < np; ++j) {
-        const float v = rho[ro + j];
-        a.R[slot0 + j] = v;
+    for (int jp = 0; jp < np; ++jp) {
+        const float v = rho[(size_t)jp * T];
+        if (RHO_SMEM) a.R[base + t + (long long)jp * T] = v;
         r2 = fmaf(v, v, r2);
     }
 #pragma unroll
@@ -316,39 +346,238 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
     }
 }
 
-size_t dict_space_smem_bytes(const Geom& g, int max_tile, int max_pairs, int own_max)
+// ------------------------------------------------------------ host planning --
+
+namespace {
+
+struct Box {
+    int lo[kMaxDim], hi[kMaxDim];
+};
+
+// Calls f(u, coords) for the pixels of [lo, hi) in raster order.
+template <class F>
+void for_box(const Geom& g, const int* lo, const int* hi, F f)
 {
-    const int G = kDSThreads / g.P;
-    return sizeof(int) * (size_t)max_tile * g.ndim + sizeof(float) * (size_t)(G > 0 ? G - 1 : 0) * g.P * kDSRedPad +
-           (sizeof(float) + sizeof(int)) * (size_t)max_pairs + sizeof(float) * (size_t)own_max * g.K;
+    const int nd = g.ndim;
+    int cd[kMaxDim];
+    for (int d = 0; d < nd; ++d) {
+        if (lo[d] >= hi[d]) return;
+        cd[d] = lo[d];
+    }
+    for (;;) {
+        long long u = 0;
+        for (int d = 0; d < nd; ++d) u = u * g.M[d] + cd[d];
+        f(u, cd);
+        int d = nd - 1;
+        while (d >= 0) {
+            if (++cd[d] < hi[d]) break;
+            cd[d] = lo[d];
+            --d;
+        }
+        if (d < 0) return;
+    }
 }
 
-// Grid for the cooperative launch (one CTA per SM) or 0 if it cannot run.
-int dict_space_grid(const Geom& g, size_t smem, int device)
+// Recursive bisection into n boxes with balanced observed counts: cut the
+// longest side where the lower part holds n1 / n of the box's pixels.
+void split_boxes(const Geom& g, const uint8_t* mask, const Box& b, int n, std::vector<Box>& out)
 {
-    if (g.P > kDSThreads) return 0;
-    int optin = 0, sms = 0, coop = 0, per_sm = 0;
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop) return 0;
-    const size_t fixed = sizeof(double) * (kDSRed + kDSRed * 11) + 4 * kAtomBlock + 2 * 4 * (kDSThreads / 32) + 256;
-    if (smem + fixed > (size_t)optin) return 0;
-    if (cudaFuncSetAttribute((void*)dict_space_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (void*)dict_space_kernel, kDSThreads, smem) !=
-            cudaSuccess ||
-        per_sm < 1)
-        return 0;
-    return sms;   // one CTA per SM
+    if (n == 1) {
+        out.push_back(b);
+        return;
+    }
+    int dim = 0;
+    for (int d = 1; d < g.ndim; ++d)
+        if (b.hi[d] - b.lo[d] > b.hi[dim] - b.lo[dim]) dim = d;
+    const int ext = b.hi[dim] - b.lo[dim];
+    const int n1 = n / 2;
+    if (ext < 2) {   // cannot cut: the remaining boxes are empty
+        out.push_back(b);
+        Box e = b;
+        e.hi[dim] = e.lo[dim];
+        for (int k = 1; k < n; ++k) out.push_back(e);
+        return;
+    }
+    std::vector<long long> slab(ext, 0);
+    long long total = 0;
+    for_box(g, b.lo, b.hi, [&](long long u, const int* cd) {
+        if (mask[u]) {
+            ++slab[cd[dim] - b.lo[dim]];
+            ++total;
+        }
+    });
+    const long long target = total * n1 / n;
+    int cut = 1;
+    long long acc = slab[0];
+    while (cut < ext - 1 && acc < target) acc += slab[cut++];
+    Box lo = b, hi = b;
+    lo.hi[dim] = b.lo[dim] + cut;
+    hi.lo[dim] = b.lo[dim] + cut;
+    split_boxes(g, mask, lo, n1, out);
+    split_boxes(g, mask, hi, n - n1, out);
 }
 
-cudaError_t launch_dict_space(const DictSpaceArgs& a, int grid, size_t smem, cudaStream_t s)
+// Observed pixels of each box, tile by tile, raster order inside a tile.
+void order_pixels(const Geom& g, const uint8_t* mask, int ncta, std::vector<int>& order, std::vector<int>& start)
 {
-    cudaError_t e = cudaFuncSetAttribute((void*)dict_space_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    Box all;
+    for (int d = 0; d < g.ndim; ++d) {
+        all.lo[d] = 0;
+        all.hi[d] = (int)g.M[d];
+    }
+    std::vector<Box> boxes;
+    split_boxes(g, mask, all, ncta, boxes);
+    int tile[kMaxDim];
+    for (int d = 0; d < g.ndim; ++d) tile[d] = std::max(1, std::min(g.B[d], 8));
+    order.clear();
+    start.assign(1, 0);
+    for (const Box& b : boxes) {
+        Box tg;   // tile grid of the box
+        for (int d = 0; d < g.ndim; ++d) {
+            tg.lo[d] = 0;
+            tg.hi[d] = b.hi[d] > b.lo[d] ? (b.hi[d] - b.lo[d] + tile[d] - 1) / tile[d] : 0;
+        }
+        for_box(g, tg.lo, tg.hi, [&](long long, const int* tc) {
+            int lo[kMaxDim], hi[kMaxDim];
+            for (int d = 0; d < g.ndim; ++d) {
+                lo[d] = b.lo[d] + tc[d] * tile[d];
+                hi[d] = std::min(b.hi[d], lo[d] + tile[d]);
+            }
+            for_box(g, lo, hi, [&](long long u, const int*) {
+                if (mask[u]) order.push_back((int)u);
+            });
+        });
+        start.push_back((int)order.size());
+    }
+}
+
+size_t ds_fixed_smem()
+{
+    return sizeof(double) * (kDSRed + kDSRed * 11) + 4 * kAtomBlock + 4 * (kDSThreads / 32) + 256;
+}
+
+}  // namespace
+
+void ds_free(DictSpacePlan* p)
+{
+    void* ptrs[] = {p->order, p->start, p->np, p->base, p->pidx, p->part, p->delta, p->bar};
+    for (void* v : ptrs)
+        if (v) cudaFree(v);
+    *p = DictSpacePlan{};
+}
+
+cudaError_t ds_build(const Geom& g, const uint8_t* mask, const uint16_t* obs, const uint16_t* nobs, int device,
+                     int* pos, float** R, DictSpacePlan* plan, cudaStream_t s)
+{
+    *plan = DictSpacePlan{};
+    *R = nullptr;
+    const int P = g.P;
+    if (P > kDSThreads) return cudaSuccess;
+    int optin = 0, sms = 0, coop = 0;
+    cudaError_t e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device)) != cudaSuccess) return e;
+    if (!coop) return cudaSuccess;
+    const int grid = sms;
+    const int G = kDSThreads / P;
+    const int own = (P + grid - 1) / grid;
+    const size_t base_smem = sizeof(float) * ((size_t)(G - 1) * P * kDSRedPad + (size_t)own * g.K);
+    if (base_smem + ds_fixed_smem() > (size_t)optin) return cudaSuccess;
+
+    std::vector<int> order, start;
+    order_pixels(g, mask, grid, order, start);
+    if (order.empty()) return cudaSuccess;
+
+    DictSpacePlan p{};
+#define DS_TRY(x)                  \
+    do {                           \
+        if ((e = (x)) != cudaSuccess) { \
+            ds_free(&p);           \
+            return e;              \
+        }                          \
+    } while (0)
+    DS_TRY(cudaMalloc((void**)&p.order, sizeof(int) * order.size()));
+    DS_TRY(cudaMalloc((void**)&p.start, sizeof(int) * start.size()));
+    DS_TRY(cudaMalloc((void**)&p.np, sizeof(int) * (size_t)grid * kDSThreads));
+    DS_TRY(cudaMalloc((void**)&p.base, sizeof(long long) * (size_t)grid));
+    DS_TRY(cudaMemcpy(p.order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice));
+    DS_TRY(cudaMemcpy(p.start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice));
+    int* npmax_d = nullptr;
+    DS_TRY(cudaMalloc((void**)&npmax_d, sizeof(int) * (size_t)grid));
+    ds_count_kernel<<<grid, kDSThreads, 0, s>>>(g, p.order, p.start, p.np, npmax_d);
+    std::vector<int> npmax(grid);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(npmax.data(), npmax_d, sizeof(int) * grid, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(npmax_d);
+    if (e != cudaSuccess) {
+        ds_free(&p);
+        return e;
+    }
+    std::vector<long long> base(grid);
+    long long total = 0;
+    for (int c = 0; c < grid; ++c) {
+        base[c] = total;
+        total += (long long)npmax[c] * kDSThreads;
+        p.max_np = std::max(p.max_np, npmax[c]);
+    }
+    if (total >= (1LL << 31)) {   // the sweep's pair table holds int32 indices
+        ds_free(&p);
+        return cudaSuccess;
+    }
+    DS_TRY(cudaMemcpy(p.base, base.data(), sizeof(long long) * grid, cudaMemcpyHostToDevice));
+    DS_TRY(cudaMalloc((void**)&p.pidx, sizeof(int) * (size_t)(total > 0 ? total : 1)));
+    float* Rd = nullptr;
+    DS_TRY(cudaMalloc((void**)&Rd, sizeof(float) * (size_t)(total > 0 ? total : 1)));
+    e = cudaMemsetAsync(Rd, 0, sizeof(float) * (size_t)(total > 0 ? total : 1), s);
+    if (e == cudaSuccess) {
+        ds_fill_kernel<<<grid, kDSThreads, 0, s>>>(g, p.order, p.start, p.base, obs, nobs, p.pidx, pos);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(Rd);
+        ds_free(&p);
+        return e;
+    }
+    // stage the residual pairs in shared memory when that leaves >= 64 KB of L1
+    const size_t rho_bytes = sizeof(float) * (size_t)p.max_np * kDSThreads;
+    p.rho_smem = base_smem + rho_bytes + ds_fixed_smem() <= (size_t)160 * 1024;
+    p.smem = base_smem + (p.rho_smem ? rho_bytes : 0);
+    void* fn = p.rho_smem ? (void*)dict_space_kernel<true> : (void*)dict_space_kernel<false>;
+    int per_sm = 0;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kDSThreads, p.smem);
+    if (e == cudaSuccess && per_sm >= 1) {
+        e = cudaMalloc((void**)&p.part, sizeof(float) * (size_t)grid * kDSRed * P);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&p.delta, sizeof(float) * (size_t)P * kAtomBlock);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&p.bar, 2 * sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemset(p.bar, 0, 2 * sizeof(unsigned int));
+    }
+    if (e != cudaSuccess || per_sm < 1) {
+        cudaFree(Rd);
+        ds_free(&p);
+        return e;
+    }
+#undef DS_TRY
+    p.grid = grid;
+    p.own_max = own;
+    p.pairs = total;
+    *plan = p;
+    *R = Rd;
+    return cudaSuccess;
+}
+
+cudaError_t launch_dict_space(const DictSpaceArgs& a, const DictSpacePlan& p, cudaStream_t s)
+{
+    void* fn = p.rho_smem ? (void*)dict_space_kernel<true> : (void*)dict_space_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned int), s);   // the barrier counts from zero each launch
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&a};
-    return cudaLaunchCooperativeKernel((void*)dict_space_kernel, dim3(grid), dim3(kDSThreads), args, smem, s);
+    return cudaLaunchCooperativeKernel(fn, dim3(p.grid), dim3(kDSThreads), args, p.smem, s);
 }
 
 }  // namespace sensai

@@ -210,52 +210,19 @@ __global__ void ola_gather_kernel(Geom g, const float* Y, float* out)
     out[u] = acc / (float)count;
 }
 
-// Observed frame pixels in raster order (one CTA, chunked block scan).
-__global__ void __launch_bounds__(1024) obs_px_kernel(long long nframe, const uint32_t* mbits, int* obs_px)
+// Residual position of observed pixel j of patch i in the per-pixel slot
+// layout: slot Rbase[p] + rank of i among the patches observing p.
+__global__ void pos_slots_kernel(Geom g, const uint16_t* obs, const uint16_t* nobs, const uint32_t* Ibits,
+                                 const uint32_t* Ipre, const int* Rbase, int* pos)
 {
-    __shared__ int warp_tot[32];
-    __shared__ int carry;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long nmw = (nframe + 31) / 32;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (long long base = 0; base < nmw; base += blockDim.x) {
-        const long long w = base + threadIdx.x;
-        uint32_t bits = 0u;
-        if (w < nmw) {
-            bits = mbits[w];
-            const long long rem = nframe - w * 32;
-            if (rem < 32) bits &= (1u << rem) - 1u;
-        }
-        const int v = __popc(bits);
-        int incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int n = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += n;
-        }
-        if (lane == 31) warp_tot[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            const int nw = blockDim.x >> 5;
-            int tt = lane < nw ? warp_tot[lane] : 0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int n = __shfl_up_sync(0xffffffffu, tt, o);
-                if (lane >= o) tt += n;
-            }
-            if (lane < nw) warp_tot[lane] = tt;
-        }
-        __syncthreads();
-        int pos = carry + (warp > 0 ? warp_tot[warp - 1] : 0) + incl - v;
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1u;
-            obs_px[pos++] = (int)(w * 32 + b);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) carry += warp_tot[(blockDim.x >> 5) - 1];
-        __syncthreads();
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    const long long w = i >> 5;
+    const uint32_t below = (1u << (i & 31)) - 1u;
+    for (int j = 0; j < (int)nobs[i]; ++j) {
+        const int p = obs[(long long)j * g.N + i];
+        const long long wd = (long long)p * g.NW + w;
+        pos[(long long)j * g.N + i] = Rbase[p] + (int)Ipre[wd] + __popc(Ibits[wd] & below);
     }
 }
 
@@ -359,9 +326,10 @@ cudaError_t launch_ilist(const Geom& g, const uint32_t* Ibits, const uint32_t* I
     return cudaGetLastError();
 }
 
-cudaError_t launch_obs_px(long long nframe, const uint32_t* mbits, int* obs_px, cudaStream_t s)
+cudaError_t launch_pos_slots(const Geom& g, const uint16_t* obs, const uint16_t* nobs, const uint32_t* Ibits,
+                             const uint32_t* Ipre, const int* Rbase, int* pos, cudaStream_t s)
 {
-    obs_px_kernel<<<1, 1024, 0, s>>>(nframe, mbits, obs_px);
+    pos_slots_kernel<<<blocks_for(g.N, 256), 256, 0, s>>>(g, obs, nobs, Ibits, Ipre, Rbase, pos);
     return cudaGetLastError();
 }
 

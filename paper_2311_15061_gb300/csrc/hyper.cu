@@ -147,8 +147,7 @@ __global__ void code_stats_kernel(Geom g, const float* W, const uint32_t* Zb, in
 // per-chunk squared norm.
 __global__ void residual_kernel(Geom g, const float* x, const uint16_t* obs, const uint16_t* nobs,
                                 const int* imgoff, const float* D, const float* W, const uint32_t* Zb,
-                                const uint32_t* Ibits, const uint32_t* Ipre, const int* Rbase, float* R,
-                                double* part_r2)
+                                const int* pos, float* R, double* part_r2)
 {
     const long long chunk = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -165,9 +164,7 @@ __global__ void residual_kernel(Geom g, const float* x, const uint16_t* obs, con
                 const float w = W[wblock(g, k / kAtomBlock, i) + k % kAtomBlock];
                 if (w != 0.0f) r = fmaf(-D[(long long)k * g.P + p], w, r);
             }
-            const long long w = (long long)p * g.NW + chunk;
-            const int slot = Rbase[p] + (int)Ipre[w] + __popc(Ibits[w] & ((1u << lane) - 1u));
-            R[slot] = r;
+            R[pos[(long long)j * g.N + i]] = r;
             r2 += (double)r * r;
         }
     }
@@ -210,11 +207,9 @@ cudaError_t launch_code_stats(const Geom& g, const float* W, const uint32_t* Zb,
 
 cudaError_t launch_residual(const Geom& g, const float* x, const uint16_t* obs, const uint16_t* nobs,
                             const int* imgoff, const float* D, const float* W, const uint32_t* Zb,
-                            const uint32_t* Ibits, const uint32_t* Ipre, const int* Rbase, float* R,
-                            double* part_r2, cudaStream_t s)
+                            const int* pos, float* R, double* part_r2, cudaStream_t s)
 {
-    residual_kernel<<<blocks_for(g.NW, 8), 256, 0, s>>>(g, x, obs, nobs, imgoff, D, W, Zb, Ibits, Ipre, Rbase,
-                                                        R, part_r2);
+    residual_kernel<<<blocks_for(g.NW, 8), 256, 0, s>>>(g, x, obs, nobs, imgoff, D, W, Zb, pos, R, part_r2);
     return cudaGetLastError();
 }
 

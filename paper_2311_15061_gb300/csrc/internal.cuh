@@ -309,10 +309,8 @@ struct SweepArgs {
     uint32_t* Zb;              // [K][NW] activity bits (written)
     const float* lpi;          // [K] logit(pi_k)
     const DevScalars* sc;
-    const uint32_t* Ibits;     // [P][NW] bit i: patch i observes pixel p
-    const uint32_t* Ipre;      // [P][NW] exclusive popcount prefix of Ibits
-    const int* Rbase;          // [P] start of pixel p's residual slots
-    float* R;                  // residual, slot Rbase[p] + rank of i among patches observing p
+    const int* pos;            // [maxobs][N] residual position of observed pixel j of patch i
+    float* R;                  // residual in the dictionary step's layout, R[pos[j][i]]
                                // (null: inpainting only, the residual is not kept)
     int* m;                    // [K] active count per atom (accumulated)
     double* part_s2;           // [NW] per 32-patch chunk
@@ -342,23 +340,39 @@ struct DictArgs {
     uint32_t t;
 };
 
+// The space-organised dictionary sweep (dict_space.cu), planned per context:
+// pair jp of thread t in CTA c is element base[c] + jp * 512 + t of R and pidx.
+struct DictSpacePlan {
+    int grid = 0;              // CTAs of the cooperative launch; 0: use dict.cu
+    size_t smem = 0;           // dynamic shared memory
+    bool rho_smem = false;     // residual pairs staged in shared memory
+    int own_max = 0;           // chains per CTA: ceil(P / grid)
+    int max_np = 0;            // largest pair count of a thread
+    long long pairs = 0;       // length of R and pidx (padded)
+    int* order = nullptr;      // observed pixels, box by box, tile by tile
+    int* start = nullptr;      // [grid + 1] each CTA's range of order
+    int* np = nullptr;         // [grid][512] pairs per thread
+    long long* base = nullptr; // [grid] first pair of each CTA
+    int* pidx = nullptr;       // patch of every pair
+    float* part = nullptr;     // [P][grid][44] per-CTA block sums, chain-major
+    float* delta = nullptr;    // [P][8] the block's updates
+    unsigned int* bar = nullptr;   // grid barrier arrival counter, zeroed per launch
+};
+
 struct DictSpaceArgs {
     Geom g;
     float* D;                  // [K][P]
     const float* W;            // [KB][Npad][8]
-    const uint32_t* Ibits;     // [P][NW]
-    const uint32_t* Ipre;      // [P][NW]
-    const int* Rbase;          // [P + 1]
-    float* R;                  // residual slots
+    float* R;                  // residual pairs (plan layout)
+    const int* pidx;
+    const int* np;
+    const long long* base;
     DevScalars* sc;            // gamma_eps in, status out
     double* part_r2;           // [gridDim.x]
-    float* part;               // [gridDim.x][44][P] per-CTA block sums
-    float* delta;              // [P][8] the block's updates
-    unsigned int* bar;         // grid barrier (count, generation)
-    const int* obs_px;         // observed frame pixels in raster order
-    long long n_obs_px;
-    int max_tile;              // ceil(n_obs_px / gridDim.x)
-    int own_max;               // chains per CTA: ceil(P / gridDim.x)
+    float* part;
+    float* delta;
+    unsigned int* bar;
+    int own_max;
     unsigned long long seed;
     uint32_t t;
 };
@@ -438,10 +452,15 @@ cudaError_t launch_slice_dictionary(const Geom& g, const float* D, float* Dsl, i
 cudaError_t launch_sweep_tiled(const SweepArgs& a, int maxobs, int grid, cudaStream_t s);
 cudaError_t launch_dict(const DictArgs& a, int max_slots, cudaStream_t s);
 cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);
-size_t dict_space_smem_bytes(const Geom& g, int max_tile, int max_pairs, int own_max);
-int dict_space_grid(const Geom& g, size_t smem, int device);
-cudaError_t launch_dict_space(const DictSpaceArgs& a, int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_obs_px(long long nframe, const uint32_t* mbits, int* obs_px, cudaStream_t s);
+// Builds the plan and its residual array R, filling pos[j][i] for the
+// sweep; plan->grid = 0 (and no allocation) when the kernel cannot run.
+cudaError_t ds_build(const Geom& g, const uint8_t* host_mask, const uint16_t* obs, const uint16_t* nobs, int device,
+                     int* pos, float** R, DictSpacePlan* plan, cudaStream_t s);
+void ds_free(DictSpacePlan* plan);
+// pos[j][i] for the per-chain slot layout of dict.cu.
+cudaError_t launch_pos_slots(const Geom& g, const uint16_t* obs, const uint16_t* nobs, const uint32_t* Ibits,
+                             const uint32_t* Ipre, const int* Rbase, int* pos, cudaStream_t s);
+cudaError_t launch_dict_space(const DictSpaceArgs& a, const DictSpacePlan& plan, cudaStream_t s);
 cudaError_t launch_geometry(const Geom& g, const uint8_t* mask_bytes, uint32_t* mask_bits, int* imgoff,
                             uint16_t* nobs, int* maxobs, unsigned long long* total, cudaStream_t s);
 cudaError_t launch_fill_obs(const Geom& g, const uint32_t* mask_bits, const int* imgoff, uint16_t* obs, cudaStream_t s);
@@ -460,8 +479,7 @@ cudaError_t launch_code_stats(const Geom& g, const float* W, const uint32_t* Zb,
                               cudaStream_t s);
 cudaError_t launch_residual(const Geom& g, const float* x, const uint16_t* obs, const uint16_t* nobs,
                             const int* imgoff, const float* D, const float* W, const uint32_t* Zb,
-                            const uint32_t* Ibits, const uint32_t* Ipre, const int* Rbase, float* R,
-                            double* part_r2, cudaStream_t s);
+                            const int* pos, float* R, double* part_r2, cudaStream_t s);
 cudaError_t launch_export_codes(const Geom& g, const float* W, const uint32_t* Zb, uint8_t* Z, float* S,
                                 cudaStream_t s);
 cudaError_t launch_import_codes(const Geom& g, const uint8_t* Z, const float* S, float* W, uint32_t* Zb,

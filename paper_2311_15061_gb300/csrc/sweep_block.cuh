@@ -93,9 +93,13 @@ __device__ __forceinline__ void code_block(const float* Dcol, const float* lpi_b
             const float rlam = __fdividef(1.0f, lam);
             const float L = lpi_blk[kk] + c.half_log_gs - 0.5f * __logf(lam) + c.half_ge2 * g * g * rlam;
             const float sig = __fdividef(1.0f, 1.0f + __expf(-L));
-            const unsigned long long thr = (unsigned long long)(sig * 4294967296.0f);
+            // z = [x0 < floor(sig 2^32)] in 32-bit integers: the saturating
+            // conversion gives the floor below 2^32, and sig = 1 (threshold
+            // 2^32) accepts every word (a 64-bit conversion would run on the
+            // FP64 pipe)
+            const uint32_t thr = __float2uint_rz(sig * 4294967296.0f);
             const uint4 blk = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)k, t, kTagCodes), keys);
-            const bool z = valid && ((unsigned long long)blk.x < thr);
+            const bool z = valid && (blk.x < thr || sig >= 1.0f);
             w_new = 0.0f;
             if (z) {
                 w_new = fmaf(normal32(blk.y, blk.z), sqrtf(rlam), c.ge * g * rlam);
@@ -126,14 +130,13 @@ __device__ __forceinline__ void code_block(const float* Dcol, const float* lpi_b
     }
 }
 
-// End of a patch's sweep: scatter the residual to the per-pixel slots (when
-// kept) and publish the chunk's sum of s^2 and ||r||^2 (fixed-order warp sums).
+// End of a patch's sweep: scatter the residual to the dictionary step's
+// layout (when kept) and publish the chunk's sum of s^2 and ||r||^2 (fixed-order warp sums).
 template <int MAXOBS>
 __device__ __forceinline__ void finish_patch(const SweepArgs& a, const float (&r)[MAXOBS], int wmax, int nobs,
                                              long long i, unsigned int chunk, int lane, float s2)
 {
     const long long N = a.g.N;
-    const int NW = a.g.NW;
     float r2 = 0.0f;
 #pragma unroll
     for (int g4 = 0; g4 < MAXOBS / 4; ++g4) {
@@ -142,13 +145,7 @@ __device__ __forceinline__ void finish_patch(const SweepArgs& a, const float (&r
         for (int u = 0; u < 4; ++u) {
             const int j = 4 * g4 + u;
             if (j < nobs) {
-                if (a.R) {
-                    const int p = a.obs[(long long)j * N + i];
-                    const long long wd = (long long)p * NW + chunk;
-                    const uint32_t ib = a.Ibits[wd];
-                    const int slot = a.Rbase[p] + (int)a.Ipre[wd] + __popc(ib & ((1u << lane) - 1u));
-                    a.R[slot] = r[j];
-                }
+                if (a.R) a.R[a.pos[(long long)j * N + i]] = r[j];
                 r2 = fmaf(r[j], r[j], r2);
             }
         }
