@@ -66,8 +66,8 @@ typedef enum {
  * stride[d] >= 1 with (M[d] - B[d]) divisible by stride[d]; 1 <= K <= 1024;
  * P = prod(B) <= 1024; number of patches < 2^31.  a <= 0 selects a = K and
  * b <= 0 selects b = N / 8 (N = number of patches).  c..f > 0.  flags:
- * 0, or SENSAI_FLAG_STREAM_DICTIONARY optionally with SENSAI_SLICE_ATOMS(n);
- * other bits are EINVAL.
+ * SENSAI_FLAG_CHAIN_DICTIONARY, SENSAI_FLAG_STREAM_DICTIONARY, and with the
+ * latter SENSAI_SLICE_ATOMS(n); other bits are EINVAL.
  *
  * The code sweep keeps the whole dictionary in shared memory when
  * (P + 1) * (K rounded up to 8, odd) floats fit (K = 128, P = 100: 52 KB);
@@ -76,6 +76,11 @@ typedef enum {
  * SENSAI_SLICE_ATOMS(n) fixes the slice at n atoms (n a multiple of 8, no
  * larger than what fits).  Results do not depend on either. */
 #define SENSAI_FLAG_STREAM_DICTIONARY 0x1
+/* The dictionary draw runs one CTA per within-patch pixel chain instead of
+ * the cooperative space-organised kernel, so that the context can share the
+ * GPU with others (required for sensai_batch_create).  Results are the same
+ * draws up to FP32 summation order. */
+#define SENSAI_FLAG_CHAIN_DICTIONARY 0x2
 #define SENSAI_SLICE_ATOMS(n) ((((n) / 8) & 0xff) << 8)
 typedef struct {
     int32_t ndim;
@@ -235,6 +240,40 @@ sensai_status sensai_serve_drain(sensai_ctx* ctx);
 
 /* Drain, stop the workers and release the slots. */
 sensai_status sensai_serve_stop(sensai_ctx* ctx);
+
+/* ---- Batches: many independent problems learned together -------------------
+ *
+ * The paper processes frames one after another; a batch runs the Gibbs
+ * iterations (the BPFA section's sampler) of n independent contexts together
+ * so that small problems share the GPU.  One iteration of every instance is
+ * captured once into a CUDA graph, each instance on its own branch, and
+ * replayed per iteration.  Each context ends exactly where sensai_learn(iters)
+ * on it alone would: the same kernels, the same draws.
+ *
+ * Contexts must have a frame set (sensai_set_frame or an earlier call with a
+ * frame), share one device, be created with SENSAI_FLAG_CHAIN_DICTIONARY (the
+ * cooperative dictionary kernel cannot share the GPU) and not be serving;
+ * a context may belong to one batch at a time.  The batch does not own the
+ * contexts; destroy it before them.  Errors: EINVAL for bad arguments, the
+ * first instance's error otherwise. */
+typedef struct sensai_batch sensai_batch;
+sensai_status sensai_batch_create(sensai_ctx* const* ctxs, int32_t n, sensai_batch** out);
+
+/* iters Gibbs iterations of every instance, asynchronous on cuda_stream
+ * (ordered after the work already on it, and work enqueued on it afterwards
+ * waits for the batch). */
+sensai_status sensai_batch_learn(sensai_batch* b, int32_t iters, void* cuda_stream);
+
+/* Autotuner: times the batch with the code sweep of each instance limited to
+ * 1/1, 1/2, 1/4, 1/8 and 1/16 of its full grid (narrower grids let more
+ * instances run side by side), iters_per_trial iterations per candidate, and
+ * keeps the fastest; *divisor (may be NULL) receives it.  The trials are real
+ * Gibbs iterations: each candidate runs one warm-up and iters_per_trial timed
+ * iterations, so every instance advances by 5 * (1 + iters_per_trial)
+ * iterations.  Results do not depend on the choice. */
+sensai_status sensai_batch_tune(sensai_batch* b, int32_t iters_per_trial, void* cuda_stream, int32_t* divisor);
+
+void sensai_batch_destroy(sensai_batch* b);
 
 /* Per-phase device timing.  enable = 1 clears the record and starts timing:
  * every later phase records a CUDA event pair on its launching stream;

@@ -4,6 +4,7 @@
 // Host code here only validates arguments, allocates, copies and launches;
 // every arithmetic step of the sampler runs in the kernels of sweep.cu,
 // dict.cu, hyper.cu and geometry.cu.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -83,6 +84,8 @@ struct sensai_ctx {
     unsigned int* chunk_counter = nullptr;
     DevScalars* sc = nullptr;
     int* pos = nullptr;         // [maxobs][N] residual position of each observed pixel of each patch
+    bool t_on_device = false;   // kernels read the iteration index from sc->t_iter (graph capture)
+    int grid_cap = 0;           // > 0: at most this many CTAs for the code sweep (batches)
     DictSpacePlan ds{};         // space-organised dictionary sweep (cooperative launch), when it runs
     ServeEngine* serve = nullptr;   // live serving engine, when started
 };
@@ -246,11 +249,14 @@ sensai_status run_sweep(sensai_ctx* ctx, cudaStream_t s)
     a.sc_out = ctx->sc;
     a.keys = philox_round_keys(ctx->prm.seed);
     a.t = (uint32_t)ctx->t;
+    a.t_dev = ctx->t_on_device;
+    SweepPlan plan = ctx->sweep_plan;
+    if (ctx->grid_cap > 0 && plan.grid > ctx->grid_cap) plan.grid = ctx->grid_cap;
     PhaseTimer timer(ctx, kPhaseCodes, s);
-    SENSAI_CUDA(ctx, cudaMemsetAsync(ctx->m, 0, sizeof(int) * ctx->g.K, s));
-    SENSAI_CUDA(ctx, launch_code_sweep(a, ctx->sweep_plan, ctx->maxobs, ctx->Dsl, s));
+    int nl = 0;
+    SENSAI_CUDA(ctx, launch_code_sweep(a, plan, ctx->maxobs, ctx->Dsl, s, &nl));
     timer.stop();
-    ctx->launches += 1;
+    ctx->launches += nl;
     ctx->codes_valid = true;
     ctx->resid_valid = true;
     ctx->n_r2 = ctx->g.NW;
@@ -299,6 +305,7 @@ sensai_status run_dictionary(sensai_ctx* ctx, cudaStream_t s)
     a.part_r2 = ctx->part_r2;
     a.seed = ctx->prm.seed;
     a.t = (uint32_t)ctx->t;
+    a.t_dev = ctx->t_on_device;
     PhaseTimer timer(ctx, kPhaseDict, s);
     SENSAI_CUDA(ctx, launch_dict(a, ctx->max_slots, s));
     timer.stop();
@@ -335,6 +342,7 @@ sensai_status run_hyper(sensai_ctx* ctx, cudaStream_t s)
     a.sc = ctx->sc;
     a.seed = ctx->prm.seed;
     a.t = (uint32_t)ctx->t;
+    a.t_dev = ctx->t_on_device;
     PhaseTimer timer(ctx, kPhaseHyper, s);
     SENSAI_CUDA(ctx, launch_hyper(a, s));
     timer.stop();
@@ -384,9 +392,9 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     const sensai_params& p = *prm;
     if (p.ndim < 1 || p.ndim > kMaxDim) return fail(SENSAI_EINVAL, "ndim must be 1..4 (got %d)", p.ndim);
     if (p.K < 1 || p.K > 1024) return fail(SENSAI_EINVAL, "K must be 1..1024 (got %d)", p.K);
-    const int known_flags = SENSAI_FLAG_STREAM_DICTIONARY | SENSAI_SLICE_ATOMS(2040);
+    const int known_flags = SENSAI_FLAG_STREAM_DICTIONARY | SENSAI_FLAG_CHAIN_DICTIONARY | SENSAI_SLICE_ATOMS(2040);
     if ((p.flags & ~known_flags) != 0) return fail(SENSAI_EINVAL, "unknown flags 0x%x", p.flags);
-    if ((p.flags & ~SENSAI_FLAG_STREAM_DICTIONARY) != 0 && !(p.flags & SENSAI_FLAG_STREAM_DICTIONARY))
+    if ((p.flags & SENSAI_SLICE_ATOMS(2040)) != 0 && !(p.flags & SENSAI_FLAG_STREAM_DICTIONARY))
         return fail(SENSAI_EINVAL, "SENSAI_SLICE_ATOMS needs SENSAI_FLAG_STREAM_DICTIONARY");
     if (!(p.c > 0 && p.d > 0 && p.e > 0 && p.f > 0)) return fail(SENSAI_EINVAL, "c, d, e, f must be > 0");
     Geom g{};
@@ -483,7 +491,8 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     // residual layout: the pairs of the space-organised dictionary sweep when
     // it runs, else the per-pixel slots of the per-chain kernel
     CREATE_CUDA(dalloc(&ctx->pos, (size_t)(ctx->maxobs > 0 ? ctx->maxobs : 1) * N));
-    CREATE_CUDA(ds_build(g, mask, ctx->obs, ctx->nobs, device, ctx->pos, &ctx->R, &ctx->ds, st0));
+    if (!(p.flags & SENSAI_FLAG_CHAIN_DICTIONARY))
+        CREATE_CUDA(ds_build(g, mask, ctx->obs, ctx->nobs, device, ctx->pos, &ctx->R, &ctx->ds, st0));
     if (ctx->ds.grid > 0) {
         ctx->launches += 2;
     } else {
@@ -896,6 +905,244 @@ sensai_status sensai_profile_read(sensai_ctx* ctx, double* ms, int64_t* counts)
         ms[ph] = total;
         counts[ph] = (int64_t)ctx->timed[ph].size();
     }
+    return SENSAI_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches --
+//
+// One Gibbs iteration of every instance (code sweep with its active counts,
+// dictionary draw, pi / gamma draws) is captured once into a CUDA graph, each
+// instance on its own forked stream so that independent instances run side by
+// side on the GPU.  The graph is replayed once per iteration.  Its kernels
+// read the iteration index from each context's device scalars, and the hyper
+// kernel advances it, so every replay draws with fresh counters.  The results
+// are exactly those of sensai_learn on each context alone.
+
+struct sensai_batch {
+    std::vector<sensai_ctx*> ctx;
+    std::vector<cudaStream_t> streams;   // capture branches, one per instance
+    std::vector<cudaEvent_t> joins;
+    std::vector<long long> launches;     // kernels of one iteration, per instance
+    cudaStream_t origin = nullptr;       // the stream graphs are captured on and replayed from
+    cudaEvent_t fork = nullptr, in = nullptr, out = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int divisor = 1;                     // code-sweep CTAs per instance: full grid / divisor
+};
+
+namespace {
+
+void batch_drop_graph(sensai_batch* b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// Captures one iteration of every instance (the caller has run the eager
+// setup: frame, gamma_eps, residual).
+sensai_status batch_capture(sensai_batch* b)
+{
+    batch_drop_graph(b);
+    const size_t n = b->ctx.size();
+    for (size_t i = 0; i < n; ++i) {
+        sensai_ctx* c = b->ctx[i];
+        c->grid_cap = b->divisor > 1 ? std::max(1, c->sweep_plan.grid / b->divisor) : 0;
+    }
+    cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return cuda_failure(nullptr, e, "cudaStreamBeginCapture", __LINE__);
+    sensai_status st = SENSAI_OK;
+    e = cudaEventRecord(b->fork, b->origin);
+    for (size_t i = 0; i < n && st == SENSAI_OK && e == cudaSuccess; ++i) {
+        sensai_ctx* c = b->ctx[i];
+        const bool prof = c->profiling;
+        const long long l0 = c->launches;
+        c->profiling = false;
+        c->t_on_device = true;
+        e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+        if (e == cudaSuccess) st = run_sweep(c, b->streams[i]);
+        if (e == cudaSuccess && st == SENSAI_OK) st = run_dictionary(c, b->streams[i]);
+        if (e == cudaSuccess && st == SENSAI_OK) st = run_hyper(c, b->streams[i]);
+        c->t_on_device = false;
+        c->profiling = prof;
+        b->launches[i] = c->launches - l0;
+        c->launches = l0;
+        if (e == cudaSuccess && st == SENSAI_OK) e = cudaEventRecord(b->joins[i], b->streams[i]);
+        if (e == cudaSuccess && st == SENSAI_OK) e = cudaStreamWaitEvent(b->origin, b->joins[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(b->origin, &g);
+    if (st != SENSAI_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e == cudaSuccess) e = e_end;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        b->exec = nullptr;
+        return cuda_failure(nullptr, e, "batch graph capture", __LINE__);
+    }
+    b->graph = g;
+    return SENSAI_OK;
+}
+
+// Eager per-instance setup on the origin stream, then the iteration indices.
+sensai_status batch_prepare(sensai_batch* b)
+{
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        sensai_ctx* c = b->ctx[i];
+        sensai_status st = enter(c);
+        if (st != SENSAI_OK) return st;
+        if (!c->frame_set) return fail(SENSAI_ESTATE, "batch instance %zu has no frame", i);
+        if ((st = ensure_gamma_eps(c, b->origin)) != SENSAI_OK) return st;
+        if ((st = ensure_residual(c, b->origin)) != SENSAI_OK) return st;
+        if ((st = ensure_code_stats(c, b->origin)) != SENSAI_OK) return st;
+        SENSAI_CUDA(c, launch_set_iteration(c->sc, (uint32_t)c->t, b->origin));
+        c->launches += 1;
+    }
+    return SENSAI_OK;
+}
+
+void batch_advance(sensai_batch* b, int iters)
+{
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        sensai_ctx* c = b->ctx[i];
+        c->t += iters;
+        c->launches += b->launches[i] * iters;
+        c->codes_valid = true;
+        c->resid_valid = true;
+    }
+}
+
+// Replays the graph iters times on the origin stream, ordered after `user`
+// and before whatever the caller enqueues on `user` next.
+sensai_status batch_replay(sensai_batch* b, int iters, cudaStream_t user)
+{
+    cudaError_t e = cudaEventRecord(b->in, user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->in, 0);
+    if (e != cudaSuccess) return cuda_failure(nullptr, e, "batch stream ordering", __LINE__);
+    sensai_status st = batch_prepare(b);
+    if (st != SENSAI_OK) return st;
+    if (!b->exec && (st = batch_capture(b)) != SENSAI_OK) return st;
+    for (int it = 0; it < iters && e == cudaSuccess; ++it) e = cudaGraphLaunch(b->exec, b->origin);
+    if (e == cudaSuccess) e = cudaEventRecord(b->out, b->origin);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(user, b->out, 0);
+    if (e != cudaSuccess) return cuda_failure(nullptr, e, "cudaGraphLaunch", __LINE__);
+    batch_advance(b, iters);
+    return SENSAI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sensai_batch_destroy(sensai_batch* b)
+{
+    if (!b) return;
+    if (b->origin) cudaStreamSynchronize(b->origin);
+    batch_drop_graph(b);
+    for (cudaStream_t s : b->streams)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t ev : b->joins)
+        if (ev) cudaEventDestroy(ev);
+    cudaEvent_t evs[] = {b->fork, b->in, b->out};
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    for (sensai_ctx* c : b->ctx) c->grid_cap = 0;
+    delete b;
+}
+
+sensai_status sensai_batch_create(sensai_ctx* const* ctxs, int32_t n, sensai_batch** out)
+{
+    if (!ctxs || !out || n < 1) return fail(SENSAI_EINVAL, "need n >= 1 contexts and an output pointer");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return fail(SENSAI_EINVAL, "null context %d", i);
+        if (ctxs[i]->ds.grid > 0)
+            return fail(SENSAI_EINVAL, "context %d uses the cooperative dictionary kernel; create it with "
+                        "SENSAI_FLAG_CHAIN_DICTIONARY", i);
+        if (ctxs[i]->device != ctxs[0]->device) return fail(SENSAI_EINVAL, "contexts on different devices");
+        if (ctxs[i]->serve) return fail(SENSAI_EBUSY, "context %d is serving", i);
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return fail(SENSAI_EINVAL, "context %d appears twice", i);
+    }
+    sensai_status st = enter(ctxs[0]);
+    if (st != SENSAI_OK) return st;
+    sensai_batch* b = new (std::nothrow) sensai_batch();
+    if (!b) return fail(SENSAI_ENOMEM, "host allocation failed");
+    b->ctx.assign(ctxs, ctxs + n);
+    b->streams.assign(n, nullptr);
+    b->joins.assign(n, nullptr);
+    b->launches.assign(n, 0);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->out, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        sensai_batch_destroy(b);
+        return cuda_failure(nullptr, e, "batch resources", __LINE__);
+    }
+    *out = b;
+    return SENSAI_OK;
+}
+
+sensai_status sensai_batch_learn(sensai_batch* b, int32_t iters, void* stream)
+{
+    if (!b) return fail(SENSAI_EINVAL, "null batch");
+    if (iters < 0) return fail(SENSAI_EINVAL, "iters must be >= 0");
+    if (iters == 0) return SENSAI_OK;
+    return batch_replay(b, iters, (cudaStream_t)stream);
+}
+
+sensai_status sensai_batch_tune(sensai_batch* b, int32_t iters_per_trial, void* stream, int32_t* divisor)
+{
+    if (!b) return fail(SENSAI_EINVAL, "null batch");
+    if (iters_per_trial < 1) return fail(SENSAI_EINVAL, "iters_per_trial must be >= 1");
+    const cudaStream_t user = (cudaStream_t)stream;
+    const int candidates[] = {1, 2, 4, 8, 16};
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    if (e != cudaSuccess) return cuda_failure(nullptr, e, "cudaEventCreate", __LINE__);
+    float best_ms = 0.0f;
+    int best = 1;
+    sensai_status st = SENSAI_OK;
+    for (int cand : candidates) {
+        b->divisor = cand;
+        batch_drop_graph(b);
+        // one warm-up replay (captures the graph), then the timed replays
+        if ((st = batch_replay(b, 1, user)) != SENSAI_OK) break;
+        if ((e = cudaEventRecord(t0, b->origin)) != cudaSuccess) break;
+        for (int it = 0; it < iters_per_trial && e == cudaSuccess; ++it) e = cudaGraphLaunch(b->exec, b->origin);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, b->origin);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e != cudaSuccess) break;
+        batch_advance(b, iters_per_trial);
+        if (cand == candidates[0] || ms < best_ms) {
+            best_ms = ms;
+            best = cand;
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (e == cudaSuccess) e = cudaEventRecord(b->out, b->origin);   // the caller's stream follows the trials
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(user, b->out, 0);
+    if (st != SENSAI_OK) return st;
+    if (e != cudaSuccess) return cuda_failure(nullptr, e, "batch tuning", __LINE__);
+    b->divisor = best;
+    batch_drop_graph(b);
+    if (divisor) *divisor = best;
     return SENSAI_OK;
 }
 

@@ -52,8 +52,9 @@ __global__ void __launch_bounds__(kDictThreads, 1) dict_kernel(const DictArgs a)
         if (LIST) list_s[s] = a.Ilist[base + s];
     }
     const uint2 key = seed_key(a.seed);
+    const uint32_t t_it = launch_t(a.t, a.t_dev, a.sc);
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        const uint4 blk = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)k, a.t, kTagDict), key);
+        const uint4 blk = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)k, t_it, kTagDict), key);
         xi[k] = normal64(blk.x, blk.y);
     }
     __syncthreads();

@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(kHyperThreads) hyper_kernel(const HyperArgs a)
 {
     __shared__ double red[kHyperThreads / 32];
     const int K = a.g.K;
+    const uint32_t t_it = launch_t(a.t, a.t_dev, a.sc);
     const double s2 = sum_partials(a.part_s2, a.n_s2, red);
     const double r2 = sum_partials(a.part_r2, a.n_r2, red);
     double mk = 0.0;
@@ -37,21 +38,30 @@ __global__ void __launch_bounds__(kHyperThreads) hyper_kernel(const HyperArgs a)
         mk = (double)a.m[threadIdx.x];
         const double alpha = a.a_over_K + mk;
         const double beta = a.b_scaled + (double)a.g.N - mk;
-        const double pi = beta_draw(alpha, beta, a.seed, threadIdx.x, a.t);
+        const double pi = beta_draw(alpha, beta, a.seed, threadIdx.x, t_it);
         a.pi[threadIdx.x] = pi;
         a.lpi[threadIdx.x] = (float)(log(pi) - log1p(-pi));
     }
     const double mtot = block_sum(mk, red);
     if (threadIdx.x == 0) {
-        const double gs = gamma_draw(a.c + 0.5 * mtot, a.seed, 0, 0, a.t, kTagGs) / (a.d + 0.5 * s2);
-        const double ge = gamma_draw(a.e + 0.5 * (double)a.n_observed, a.seed, 0, 0, a.t, kTagGe)
+        const double gs = gamma_draw(a.c + 0.5 * mtot, a.seed, 0, 0, t_it, kTagGs) / (a.d + 0.5 * s2);
+        const double ge = gamma_draw(a.e + 0.5 * (double)a.n_observed, a.seed, 0, 0, t_it, kTagGe)
                         / (a.f + 0.5 * r2);
         a.sc->gamma_s = gs;
         a.sc->gamma_eps = ge;
         a.sc->sum_s2 = s2;
         a.sc->sum_r2 = r2;
         a.sc->n_active = (long long)mtot;
+        if (a.t_dev) a.sc->t_iter = t_it + 1u;   // the next replay's iteration
     }
+}
+
+__global__ void set_iteration_kernel(DevScalars* sc, uint32_t t) { sc->t_iter = t; }
+
+cudaError_t launch_set_iteration(DevScalars* sc, uint32_t t, cudaStream_t s)
+{
+    set_iteration_kernel<<<1, 1, 0, s>>>(sc, t);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s)

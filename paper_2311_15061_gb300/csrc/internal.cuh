@@ -58,7 +58,15 @@ struct DevScalars {
     unsigned long long act_n;    // code draws with z = 1
     int ge_set;        // gamma_eps initialised from a frame
     int status;        // sticky error word written by kernels (0 = ok)
+    uint32_t t_iter;   // iteration index for kernels replayed from a CUDA graph
 };
+
+// Iteration index of a launch: the argument, or the device copy when the
+// launch is replayed from a captured graph (t_dev set).
+__device__ __forceinline__ uint32_t launch_t(uint32_t t, bool t_dev, const DevScalars* sc)
+{
+    return t_dev ? sc->t_iter : t;
+}
 
 // Weights are stored in 8-atom blocks per patch, [KB][Npad][8]: the eight
 // weights of patch i for atoms 8 kb .. 8 kb + 7 are one 32-byte sector, and a
@@ -312,13 +320,14 @@ struct SweepArgs {
     const int* pos;            // [maxobs][N] residual position of observed pixel j of patch i
     float* R;                  // residual in the dictionary step's layout, R[pos[j][i]]
                                // (null: inpainting only, the residual is not kept)
-    int* m;                    // [K] active count per atom (accumulated)
+    int* m;                    // [K] active count per atom (written after the sweep)
     double* part_s2;           // [NW] per 32-patch chunk
     double* part_r2;           // [NW] per 32-patch chunk
     unsigned int* chunk_counter;  // work counter, zeroed before each launch
     DevScalars* sc_out;           // change counters (same object as sc)
     PhiloxKeys keys;              // round keys of the seed
     uint32_t t;
+    bool t_dev = false;           // take t from sc->t_iter (graph replay)
     // streamed dictionary (sweep_tiled.cu); Dsl null: the whole dictionary
     // is resident in shared memory (sweep.cu)
     const float* Dsl = nullptr;   // [slices][slice_stride] slices in shared-memory layout
@@ -338,6 +347,7 @@ struct DictArgs {
     double* part_r2;           // [P]
     unsigned long long seed;
     uint32_t t;
+    bool t_dev = false;        // take t from sc->t_iter (graph replay)
 };
 
 // The space-organised dictionary sweep (dict_space.cu), planned per context:
@@ -391,6 +401,7 @@ struct HyperArgs {
     DevScalars* sc;
     unsigned long long seed;
     uint32_t t;
+    bool t_dev = false;        // take t from sc->t_iter (graph replay)
 };
 
 // Live serving engine (serve.cu).
@@ -441,9 +452,12 @@ struct SweepPlan {
 // fits, or force_slice_atoms (a multiple of 8 no larger than that) if > 0.
 bool plan_sweep(const Geom& g, int maxobs, int device, bool force_stream, int force_slice_atoms, SweepPlan* out);
 long long slice_capacity_floats(const Geom& g);
-// One code sweep by plan; Dsl (slice_capacity_floats floats) is needed when
-// streamed and is refilled from a.D on the stream first.
-cudaError_t launch_code_sweep(SweepArgs a, const SweepPlan& plan, int maxobs, float* Dsl, cudaStream_t s);
+// One code sweep by plan, then the per-atom active counts a.m from the
+// activity words.  Dsl (slice_capacity_floats floats) is needed when
+// streamed and is refilled from a.D on the stream first.  *nlaunch (if not
+// null) receives the number of kernels launched.
+cudaError_t launch_code_sweep(SweepArgs a, const SweepPlan& plan, int maxobs, float* Dsl, cudaStream_t s,
+                              int* nlaunch);
 long long slice_stride_floats(const Geom& g, int KS);
 size_t tiled_smem_bytes(const Geom& g, int KS);
 int tiled_slice_atoms(const Geom& g, int maxobs, int device);
@@ -452,6 +466,7 @@ cudaError_t launch_slice_dictionary(const Geom& g, const float* D, float* Dsl, i
 cudaError_t launch_sweep_tiled(const SweepArgs& a, int maxobs, int grid, cudaStream_t s);
 cudaError_t launch_dict(const DictArgs& a, int max_slots, cudaStream_t s);
 cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);
+cudaError_t launch_set_iteration(DevScalars* sc, uint32_t t, cudaStream_t s);   // sc->t_iter = t
 // Builds the plan and its residual array R, filling pos[j][i] for the
 // sweep; plan->grid = 0 (and no allocation) when the kernel cannot run.
 cudaError_t ds_build(const Geom& g, const uint8_t* host_mask, const uint16_t* obs, const uint16_t* nobs, int device,

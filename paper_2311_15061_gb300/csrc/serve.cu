@@ -293,8 +293,7 @@ static sensai_status process_frame(ServeEngine* e, ServeSlot* sl, const ServeReq
         a.sc_out = sl->sc;
         a.keys = philox_round_keys(fseed);
         a.t = e->t0 + (uint32_t)sw;
-        FRAME_TRY(cudaMemsetAsync(sl->m, 0, sizeof(int) * g.K, s));
-        FRAME_TRY(launch_code_sweep(a, plan, maxobs, sl->Dsl, s));
+        FRAME_TRY(launch_code_sweep(a, plan, maxobs, sl->Dsl, s, nullptr));
         HyperArgs h{};
         h.g = g;
         h.m = sl->m;

@@ -43,7 +43,6 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
     const int NW = a.g.NW;
     float* Ds = smem;                      // (P + 1) x ldK; row P and atoms >= K are zero
     float* lpi = Ds + (P + 1) * ldK;       // Kpad
-    int* cntw = (int*)(lpi + Kpad);        // [warp][Kpad] active counts of this warp
     __shared__ unsigned int chunk_slot[kSweepWarps];
 
     for (int idx = threadIdx.x; idx < (P + 1) * ldK; idx += blockDim.x) {
@@ -51,12 +50,11 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
         Ds[idx] = (p < P && k < K) ? a.D[(long long)k * P + p] : 0.0f;
     }
     for (int k = threadIdx.x; k < Kpad; k += blockDim.x) lpi[k] = k < K ? a.lpi[k] : 0.0f;
-    for (int idx = threadIdx.x; idx < kSweepWarps * Kpad; idx += blockDim.x) cntw[idx] = 0;
     __syncthreads();
 
     const CodeConst c = code_const(a.sc);
+    const uint32_t t_it = launch_t(a.t, a.t_dev, a.sc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int* mycnt = cntw + warp * Kpad;
     CodeTally tl;
 
     for (;;) {
@@ -92,13 +90,13 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
                 nb = load_w8(a.W + ((long long)(kb + 1) * Npad + i) * kAtomBlock);
             const int kbase = kb * kAtomBlock;
             code_block<MAXOBS>(Ds + kbase, lpi + kbase, offK, r, wmax, nobs, i, valid, kbase,
-                               min(kAtomBlock, K - kbase), c, a.keys, a.t, a.Zb, NW, chunk, lane, mycnt + kbase,
+                               min(kAtomBlock, K - kbase), c, a.keys, t_it, a.Zb, NW, chunk, lane,
                                w0, w1, w2, w3, w4, w5, w6, w7, s2, tl);
             store_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock, w0, w1, w2, w3, w4, w5, w6, w7);
         }
         finish_patch<MAXOBS>(a, r, wmax, nobs, i, chunk, lane, s2);
     }
-    flush_counts(a, mycnt, lane, tl);
+    flush_counts(a, lane, tl);
 }
 
 int sweep_block_size() { return kSweepThreads; }
@@ -107,7 +105,7 @@ int sweep_smem_bytes(const Geom& g)
 {
     const int Kpad = g.KB * kAtomBlock;
     const int ldK = Kpad | 1;
-    return (int)(sizeof(float) * ((size_t)(g.P + 1) * ldK + Kpad) + sizeof(int) * (size_t)kSweepWarps * Kpad);
+    return (int)(sizeof(float) * ((size_t)(g.P + 1) * ldK + Kpad));
 }
 
 template <int MAXOBS>

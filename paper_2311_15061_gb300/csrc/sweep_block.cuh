@@ -65,7 +65,7 @@ __device__ __forceinline__ void code_block(const float* Dcol, const float* lpi_b
                                            float (&r)[MAXOBS], int wmax, int nobs, long long i, bool valid,
                                            int kbase, int kend, const CodeConst& c, const PhiloxKeys& keys,
                                            uint32_t t, uint32_t* Zb, int NW, unsigned int chunk, int lane,
-                                           int* mycnt_blk, float& w0, float& w1, float& w2, float& w3,
+                                           float& w0, float& w1, float& w2, float& w3,
                                            float& w4, float& w5, float& w6, float& w7, float& s2,
                                            CodeTally& tl)
 {
@@ -120,11 +120,11 @@ __device__ __forceinline__ void code_block(const float* Dcol, const float* lpi_b
                     }
                 }
             }
+            // the activity word; per-atom counts are summed from these words
+            // after the sweep (a per-atom shared-memory count here would
+            // serialise the next atom's dictionary loads behind its store)
             const uint32_t bal = __ballot_sync(0xffffffffu, z);
-            if (lane == 0) {
-                Zb[(long long)k * NW + chunk] = bal;
-                mycnt_blk[kk] += __popc(bal);
-            }
+            if (lane == 0) Zb[(long long)k * NW + chunk] = bal;
         }
         w0 = w1; w1 = w2; w2 = w3; w3 = w4; w4 = w5; w5 = w6; w6 = w7; w7 = w_new;
     }
@@ -179,12 +179,9 @@ __device__ __forceinline__ void gather_patch(const SweepArgs& a, long long i, in
     }
 }
 
-// A warp's per-atom active counts and its work counters, once per launch.
-__device__ __forceinline__ void flush_counts(const SweepArgs& a, const int* mycnt, int lane, const CodeTally& tl)
+// A warp's work counters, once per launch.
+__device__ __forceinline__ void flush_counts(const SweepArgs& a, int lane, const CodeTally& tl)
 {
-    __syncwarp();
-    for (int k = lane; k < a.g.K; k += 32)
-        if (mycnt[k]) atomicAdd(&a.m[k], mycnt[k]);
     unsigned long long cn = tl.chg_n, co = tl.chg_obs, ca = tl.act_n;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

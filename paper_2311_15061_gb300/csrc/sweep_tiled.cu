@@ -104,11 +104,9 @@ __global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_t
     float* buf0 = smem;
     float* buf1 = smem + stride;
     float* lpi = smem + 2 * stride;        // Kpad
-    int* cntw = (int*)(lpi + Kpad);        // [warp][Kpad]
     const long long nitems = (NW + kTiledWarps - 1) / kTiledWarps;
 
     for (int k = threadIdx.x; k < Kpad; k += blockDim.x) lpi[k] = k < K ? a.lpi[k] : 0.0f;
-    for (int idx = threadIdx.x; idx < kTiledWarps * Kpad; idx += blockDim.x) cntw[idx] = 0;
     if (threadIdx.x == 0) {
         abort_s = 0;
         mbar_init(&bar[0], 1);
@@ -124,8 +122,8 @@ __global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_t
     __syncthreads();
 
     const CodeConst c = code_const(a.sc);
+    const uint32_t t_it = launch_t(a.t, a.t_dev, a.sc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int* mycnt = cntw + warp * Kpad;
     CodeTally tl;
     // Use q of the slice buffers reads slice q % S from buffer q & 1 (each
     // item makes 2 S consecutive uses).  With S <= 2 both buffers keep their
@@ -179,8 +177,8 @@ __global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_t
                             if (kb + 1 < KB) nb = load_w8(a.W + ((long long)(kb + 1) * Npad + i) * kAtomBlock);
                             const int kbase = kb * kAtomBlock;
                             code_block<MAXOBS>(Dbuf + (kb - kb0) * kAtomBlock, lpi + kbase, offK, r, wmax, nobs, i,
-                                               valid, kbase, min(kAtomBlock, K - kbase), c, a.keys, a.t, a.Zb, NW,
-                                               chunk, lane, mycnt + kbase, w0, w1, w2, w3, w4, w5, w6, w7, s2, tl);
+                                               valid, kbase, min(kAtomBlock, K - kbase), c, a.keys, t_it, a.Zb, NW,
+                                               chunk, lane, w0, w1, w2, w3, w4, w5, w6, w7, s2, tl);
                             store_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock, w0, w1, w2, w3, w4, w5, w6, w7);
                         }
                     }
@@ -205,7 +203,7 @@ __global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_t
                 atomicExch(&a.sc_out->status, (int)SENSAI_ETIMEOUT);
         }
     }
-    flush_counts(a, mycnt, lane, tl);
+    flush_counts(a, lane, tl);
 }
 
 template <int MAXOBS>
@@ -236,7 +234,7 @@ long long slice_stride_floats(const Geom& g, int KS)
 size_t tiled_smem_bytes(const Geom& g, int KS)
 {
     const int Kpad = g.KB * kAtomBlock;
-    return sizeof(float) * (2 * (size_t)slice_stride_floats(g, KS) + Kpad) + sizeof(int) * (size_t)kTiledWarps * Kpad;
+    return sizeof(float) * (2 * (size_t)slice_stride_floats(g, KS) + Kpad);
 }
 
 // Largest slice (a multiple of 8 atoms, at most the padded K) whose two
@@ -337,18 +335,48 @@ bool plan_sweep(const Geom& g, int maxobs, int device, bool force_stream, int fo
     return p.grid > 0;
 }
 
-cudaError_t launch_code_sweep(SweepArgs a, const SweepPlan& plan, int maxobs, float* Dsl, cudaStream_t s)
+// m_k = the number of patches with z_ik = 1: popcounts of atom k's activity
+// words, one CTA per atom, fixed-order block sum.
+__global__ void __launch_bounds__(256) count_active_kernel(Geom g, const uint32_t* Zb, int* m)
+{
+    __shared__ int red[8];
+    const uint32_t* z = Zb + (long long)blockIdx.x * g.NW;
+    int c = 0;
+    for (int w = threadIdx.x; w < g.NW; w += blockDim.x) c += __popc(z[w]);
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int sum = 0;
+        for (int w = 0; w < 8; ++w) sum += red[w];
+        m[blockIdx.x] = sum;
+    }
+}
+
+cudaError_t launch_code_sweep(SweepArgs a, const SweepPlan& plan, int maxobs, float* Dsl, cudaStream_t s,
+                              int* nlaunch)
 {
     if (maxobs < 1) maxobs = 1;
-    if (plan.slice_atoms == 0) return launch_sweep(a, maxobs, plan.grid, s);
-    if (!Dsl) return cudaErrorInvalidValue;
-    cudaError_t e = launch_slice_dictionary(a.g, a.D, Dsl, plan.slice_atoms, s);
+    cudaError_t e;
+    int n = 0;
+    if (plan.slice_atoms == 0) {
+        e = launch_sweep(a, maxobs, plan.grid, s);
+        n = 1;
+    } else {
+        if (!Dsl) return cudaErrorInvalidValue;
+        e = launch_slice_dictionary(a.g, a.D, Dsl, plan.slice_atoms, s);
+        if (e != cudaSuccess) return e;
+        a.Dsl = Dsl;
+        a.slice_atoms = plan.slice_atoms;
+        a.slices = plan.slices;
+        a.slice_stride = plan.slice_stride;
+        e = launch_sweep_tiled(a, maxobs, plan.grid, s);
+        n = 2;
+    }
     if (e != cudaSuccess) return e;
-    a.Dsl = Dsl;
-    a.slice_atoms = plan.slice_atoms;
-    a.slices = plan.slices;
-    a.slice_stride = plan.slice_stride;
-    return launch_sweep_tiled(a, maxobs, plan.grid, s);
+    count_active_kernel<<<a.g.K, 256, 0, s>>>(a.g, a.Zb, a.m);
+    if (nlaunch) *nlaunch = n + 1;
+    return cudaGetLastError();
 }
 
 }  // namespace sensai

@@ -28,7 +28,8 @@ EXPORTED = [
     "sensai_reconstruct", "sensai_overlap_counts", "sensai_get_dictionary", "sensai_set_dictionary",
     "sensai_get_state", "sensai_set_state", "sensai_get_stats", "sensai_profile", "sensai_profile_read",
     "sensai_reconstruct_static", "sensai_serve_start", "sensai_submit_frame", "sensai_serve_drain",
-    "sensai_serve_stop", "sensai_last_error",
+    "sensai_serve_stop", "sensai_batch_create", "sensai_batch_learn", "sensai_batch_tune",
+    "sensai_batch_destroy", "sensai_last_error",
 ]
 
 
@@ -123,6 +124,10 @@ _SIG = {
     "sensai_submit_frame": (_st, [_vp, _i32, ctypes.c_uint64, _vp, _vp, _vp, _i32, _vp, DONE_FN, _vp]),
     "sensai_serve_drain": (_st, [_vp]),
     "sensai_serve_stop": (_st, [_vp]),
+    "sensai_batch_create": (_st, [_vp, _i32, ctypes.POINTER(_vp)]),
+    "sensai_batch_learn": (_st, [_vp, _i32, _vp]),
+    "sensai_batch_tune": (_st, [_vp, _i32, _vp, ctypes.POINTER(_i32)]),
+    "sensai_batch_destroy": (None, [_vp]),
     "sensai_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIG.items():
@@ -169,6 +174,7 @@ def _buf(a, dtype, count=None, name="buffer"):
 
 
 SENSAI_FLAG_STREAM_DICTIONARY = 0x1
+SENSAI_FLAG_CHAIN_DICTIONARY = 0x2
 
 
 def SENSAI_SLICE_ATOMS(n):
@@ -369,3 +375,33 @@ def sensai_reconstruct_static(params, D, S, out, stream=None):
 
 def sensai_last_error():
     return _lib.sensai_last_error().decode()
+
+
+class Batch:
+    """Owns one sensai_batch over Context objects (kept alive here)."""
+
+    def __init__(self, contexts):
+        self.contexts = list(contexts)
+        arr = (_vp * len(self.contexts))(*[c._h for c in self.contexts])
+        h = _vp()
+        _check(_lib.sensai_batch_create(arr, len(self.contexts), ctypes.byref(h)))
+        self._h = h
+
+    def sensai_batch_learn(self, iters, stream=None):
+        _check(_lib.sensai_batch_learn(self._h, int(iters), _stream(stream)))
+
+    def sensai_batch_tune(self, iters_per_trial=1, stream=None):
+        d = _i32(0)
+        _check(_lib.sensai_batch_tune(self._h, int(iters_per_trial), _stream(stream), ctypes.byref(d)))
+        return d.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.sensai_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

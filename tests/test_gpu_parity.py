@@ -339,7 +339,7 @@ def test_streamed_learning_is_bit_identical_to_resident():
 def test_flags_validation():
     from paper_2311_15061_gb300 import sensai
     prm, x, clean, mask = problem((40, 40), (8, 8), (1, 1), 16, 0.25)
-    for bad in (0x2, sensai.SENSAI_SLICE_ATOMS(8)):   # unknown bit; slice without streaming
+    for bad in (0x4, sensai.SENSAI_SLICE_ATOMS(8)):   # unknown bit; slice without streaming
         with pytest.raises(sensai.SensaiError) as err:
             gpu_context(prm, mask, bad)
         assert err.value.status == sensai.SENSAI_EINVAL
