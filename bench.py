@@ -285,6 +285,8 @@ def run_gpu(args):
         line["serving"] = run_serving(ctx)
     if not args.no_video:
         line["video3d"] = run_video3d()
+    if not args.no_batch:
+        line["batch64"] = run_batch64()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     ctx.close()
@@ -431,6 +433,87 @@ def run_video3d(cfg=VIDEO):
     return res
 
 
+BATCH = dict(sizes=(64, 96, 128, 192, 256, 384, 512), per_size=8, cubes=8, cube_shape=(128, 128, 512),
+             cube_B=(4, 4, 32), cube_S=(1, 1, 32), Ks=(64, 128, 256), frac2d=(0.05, 0.30),
+             frac_cube=(0.05, 0.12), iters=20, seed=11)
+
+
+def _batch_instances(cfg=BATCH):
+    """The heterogeneous set: 2-D frames of every size with 8x8 patches and
+    spectrum-image cubes with 4x4x32 patches at stride (1, 1, 32), K cycling
+    through 64 / 128 / 256, Bernoulli masks at per-instance fractions."""
+    from paper_2311_15061_gb300 import synth
+    rng = np.random.default_rng(cfg["seed"])
+    inst = []
+    n = 0
+    for sz in cfg["sizes"]:
+        for j in range(cfg["per_size"]):
+            x, _ = synth.stem_frame((sz, sz), cfg["seed"] + n, grains=1 + (n % 2))
+            frac = float(rng.uniform(*cfg["frac2d"]))
+            inst.append(dict(M=(sz, sz), B=(8, 8), S=(1, 1), K=cfg["Ks"][n % 3], x=x,
+                             mask=synth.random_mask((sz, sz), frac, cfg["seed"] + n)))
+            n += 1
+    cubes = [synth.spectrum_cube(cfg["cube_shape"], cfg["seed"] + 100 + j)[0] for j in range(cfg["cubes"] // 2)]
+    for j in range(cfg["cubes"]):
+        frac = float(rng.uniform(*cfg["frac_cube"]))
+        inst.append(dict(M=cfg["cube_shape"], B=cfg["cube_B"], S=cfg["cube_S"], K=cfg["Ks"][n % 3],
+                         x=cubes[j % len(cubes)], mask=synth.random_mask(cfg["cube_shape"], frac, cfg["seed"] + n)))
+        n += 1
+    return inst
+
+
+def run_batch64(cfg=BATCH):
+    """64 independent instances learned together (sensai_batch_*): one graph
+    replay per Gibbs iteration after autotuning, against the same 20
+    iterations run instance after instance with sensai_learn."""
+    import torch
+    from paper_2311_15061_gb300 import sensai
+    inst = _batch_instances(cfg)
+    ctxs = []
+    for j, c in enumerate(inst):
+        p = sensai.make_params(c["M"], c["B"], c["S"], c["K"], seed=cfg["seed"] + j,
+                               flags=sensai.SENSAI_FLAG_CHAIN_DICTIONARY)
+        ctx = sensai.Context(p, c["mask"])
+        ctx.sensai_set_frame(c["x"])
+        ctxs.append(ctx)
+    updates = float(sum(ctx.N * ctx.K for ctx in ctxs)) * cfg["iters"]
+    stream = torch.cuda.current_stream()
+    batch = sensai.Batch(ctxs)
+    divisor = batch.sensai_batch_tune(1, stream)
+    for ctx in ctxs:
+        ctx.sensai_reset(stream)
+    batch.sensai_batch_learn(1, stream)            # the tuned graph's capture, off the clock
+    for ctx in ctxs:
+        ctx.sensai_reset(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    batch.sensai_batch_learn(cfg["iters"], stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1)
+    batch.close()
+    for ctx in ctxs:
+        ctx.sensai_reset(stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for ctx in ctxs:
+        ctx.sensai_learn(None, cfg["iters"], stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    res = {"workload": ("batch64: 56 synthetic STEM frames 64^2..512^2 (8x8 patches, masks 5-30%) + 8 spectrum "
+                        "cubes 128x128x512 (4x4x32 patches stride (1,1,32), masks 5-12%), K in {64,128,256}, "
+                        "20 Gibbs iterations from the prior"),
+           "instances": len(ctxs), "patch_atom_updates": updates,
+           "value": updates / (batched_ms / 1e3), "unit": UNIT, "ms": batched_ms,
+           "sequential_value": updates / (seq_ms / 1e3), "sequential_ms": seq_ms,
+           "speedup_vs_sequential": seq_ms / batched_ms, "tuned_sweep_grid_divisor": divisor}
+    for ctx in ctxs:
+        ctx.close()
+    return res
+
+
 def _oracle_band(rows):
     """The workload restricted to the first ``rows`` frame rows."""
     import oracle as O
@@ -498,6 +581,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the live-serving measurement")
     ap.add_argument("--no-video", action="store_true", help="skip the 3-D video measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -23,12 +23,18 @@ Recipe (all NumPy ``default_rng(seed)``, PCG64):
   counts ~ Poisson(dose * I / mean(I)); frame = counts / max(counts); the clean
   reference is put on the same scale;
 * masks: Bernoulli(frac) per pixel (``kind="random"``).
+
+Spectrum images (``spectrum_cube``, the paper's spectral cubes in Sec.
+"N-Dimensional Inpainting") are (H, W, C) cubes: at every pixel a smooth
+decaying background plus Gaussian peaks at fixed channels, whose amplitudes
+vary smoothly across the field of view (sums of a few random 2-D Gaussian
+blobs), with Poisson noise at a mean dose and the same [0, 1] scaling.
 """
 from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["stem_frame", "random_mask", "line_hop_mask", "stem_volume", "sparse_state"]
+__all__ = ["stem_frame", "random_mask", "line_hop_mask", "stem_volume", "spectrum_cube", "sparse_state"]
 
 
 def _lattice_points(shape, spacing, theta, origin):
@@ -97,6 +103,39 @@ def stem_volume(shape=(32, 64, 64), seed=0, *, drift_per_frame=0.3, **kw):
         n, c = stem_frame((h, w), seed=seed, drift=(0.0, drift_per_frame * f), **kw)
         noisy[f], clean[f] = n, c
     return noisy, clean
+
+
+def spectrum_cube(shape=(128, 128, 512), seed=0, *, peaks=6, width=6.0, dose=20.0):
+    """Return ``(noisy, clean)`` float32 spectrum images of shape (H, W, C).
+
+    Per pixel: background b(y, x) exp(-c / 200) plus ``peaks`` Gaussian peaks
+    at channels drawn once (sigma ``width`` channels) with amplitude maps
+    a_j(y, x); each map is a sum of 3 random Gaussian blobs.  Poisson noise at
+    a mean of ``dose`` counts per voxel, scaled by the maximum count.
+    """
+    rng = np.random.default_rng(seed)
+    h, w, nc = shape
+    yy, xx = np.meshgrid(np.arange(h, dtype=np.float64), np.arange(w, dtype=np.float64), indexing="ij")
+
+    def blob_map():
+        m = np.zeros((h, w))
+        for _ in range(3):
+            cy, cx = rng.uniform(0, h), rng.uniform(0, w)
+            sy = rng.uniform(0.1, 0.4) * h
+            m += rng.uniform(0.3, 1.0) * np.exp(-((yy - cy) ** 2 + (xx - cx) ** 2) / (2.0 * sy * sy))
+        return m
+
+    c = np.arange(nc, dtype=np.float64)
+    intensity = (0.2 + 0.3 * blob_map())[:, :, None] * np.exp(-c / 200.0)[None, None, :]
+    centers = rng.uniform(0.1 * nc, 0.9 * nc, size=peaks)
+    for cj in centers:
+        profile = np.exp(-((c - cj) ** 2) / (2.0 * width * width))
+        intensity += blob_map()[:, :, None] * profile[None, None, :]
+    intensity += 1e-3
+    lam = dose * intensity / intensity.mean()
+    counts = rng.poisson(lam).astype(np.float64)
+    scale = max(counts.max(), 1.0)
+    return (counts / scale).astype(np.float32), (lam / scale).astype(np.float32)
 
 
 def random_mask(shape, frac, seed=0):
