@@ -435,7 +435,7 @@ def run_video3d(cfg=VIDEO):
 
 BATCH = dict(sizes=(64, 96, 128, 192, 256, 384, 512), per_size=8, cubes=8, cube_shape=(128, 128, 512),
              cube_B=(4, 4, 32), cube_S=(1, 1, 32), Ks=(64, 128, 256), frac2d=(0.05, 0.30),
-             frac_cube=(0.05, 0.12), iters=20, seed=11)
+             frac_cube=(0.05, 0.30), iters=20, seed=11)
 
 
 def _batch_instances(cfg=BATCH):
@@ -503,7 +503,7 @@ def run_batch64(cfg=BATCH):
     torch.cuda.synchronize()
     seq_ms = e0.elapsed_time(e1)
     res = {"workload": ("batch64: 56 synthetic STEM frames 64^2..512^2 (8x8 patches, masks 5-30%) + 8 spectrum "
-                        "cubes 128x128x512 (4x4x32 patches stride (1,1,32), masks 5-12%), K in {64,128,256}, "
+                        "cubes 128x128x512 (4x4x32 patches stride (1,1,32), masks 5-30%), K in {64,128,256}, "
                         "20 Gibbs iterations from the prior"),
            "instances": len(ctxs), "patch_atom_updates": updates,
            "value": updates / (batched_ms / 1e3), "unit": UNIT, "ms": batched_ms,

@@ -64,7 +64,8 @@ typedef enum {
 
 /* Problem definition.  Requirements: 1 <= ndim <= 4; 1 <= B[d] <= M[d];
  * stride[d] >= 1 with (M[d] - B[d]) divisible by stride[d]; 1 <= K <= 1024;
- * P = prod(B) <= 1024; number of patches < 2^31.  a <= 0 selects a = K and
+ * P = prod(B) <= 1024; number of patches < 2^31; at most 256 observed pixels
+ * in any patch (above 96 a patch's pixels are split over a lane pair).  a <= 0 selects a = K and
  * b <= 0 selects b = N / 8 (N = number of patches).  c..f > 0.  flags:
  * SENSAI_FLAG_CHAIN_DICTIONARY, SENSAI_FLAG_STREAM_DICTIONARY, and with the
  * latter SENSAI_SLICE_ATOMS(n); other bits are EINVAL.
@@ -217,7 +218,7 @@ typedef struct {
     int32_t slots;           /* frames in flight, 1..64 */
     int64_t max_pixels;      /* largest frame accepted, in pixels */
     int64_t memory_budget;   /* device bytes for frames in flight; <= 0: slots x largest frame */
-    int32_t max_observed;    /* cap on observed pixels per patch (<= 128); frames above it fail */
+    int32_t max_observed;    /* cap on observed pixels per patch (<= 256); frames above it fail */
 } sensai_serve_params;
 
 /* Start the serving engine on a context (allocates the slots' device memory).

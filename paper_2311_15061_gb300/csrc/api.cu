@@ -53,6 +53,7 @@ struct sensai_ctx {
     bool codes_valid = false;   // m / part_s2 describe the current codes
     bool resid_valid = false;   // R / part_r2 describe the current residual
     int n_r2 = 0;               // valid entries of part_r2
+    int n_s2 = 0;               // valid entries of part_s2
     bool broken = false;
     cudaStream_t last_stream = nullptr;
     long long launches = 0;     // kernels launched by this context
@@ -221,6 +222,7 @@ sensai_status ensure_code_stats(sensai_ctx* ctx, cudaStream_t s)
     SENSAI_CUDA(ctx, launch_code_stats(ctx->g, ctx->W, ctx->Zb, ctx->m, ctx->part_s2, s));
     ctx->launches += 1;
     ctx->codes_valid = true;
+    ctx->n_s2 = ctx->g.NW;
     return SENSAI_OK;
 }
 
@@ -259,7 +261,8 @@ sensai_status run_sweep(sensai_ctx* ctx, cudaStream_t s)
     ctx->launches += nl;
     ctx->codes_valid = true;
     ctx->resid_valid = true;
-    ctx->n_r2 = ctx->g.NW;
+    ctx->n_s2 = ctx->g.NW * plan.lanes;   // one partial per work unit
+    ctx->n_r2 = ctx->g.NW * plan.lanes;
     return SENSAI_OK;
 }
 
@@ -327,7 +330,7 @@ sensai_status run_hyper(sensai_ctx* ctx, cudaStream_t s)
     a.g = ctx->g;
     a.m = ctx->m;
     a.part_s2 = ctx->part_s2;
-    a.n_s2 = ctx->g.NW;
+    a.n_s2 = ctx->n_s2;
     a.part_r2 = ctx->part_r2;
     a.n_r2 = ctx->n_r2;
     a.n_observed = ctx->n_observed;
@@ -471,8 +474,8 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     cudaFree(mask_dev);
     mask_dev = nullptr;
     ctx->maxobs = misc[0];
-    if (ctx->maxobs > 128) {
-        fail(SENSAI_EINVAL, "a patch observes %d pixels; at most 128 observed pixels per patch are supported",
+    if (ctx->maxobs > 256) {
+        fail(SENSAI_EINVAL, "a patch observes %d pixels; at most 256 observed pixels per patch are supported",
              ctx->maxobs);
         return bail(SENSAI_EINVAL);
     }
@@ -512,11 +515,11 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     CREATE_CUDA(dalloc(&ctx->pi, (size_t)g.K));
     CREATE_CUDA(dalloc(&ctx->lpi, (size_t)g.K));
     CREATE_CUDA(dalloc(&ctx->m, (size_t)g.K));
-    CREATE_CUDA(dalloc(&ctx->part_s2, (size_t)g.NW));
+    CREATE_CUDA(dalloc(&ctx->part_s2, (size_t)2 * g.NW));   // per 16- or 32-patch work unit
     int sms = 0;
     CREATE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     {
-        size_t n = (size_t)(g.NW > P ? g.NW : P);
+        size_t n = (size_t)(2 * (size_t)g.NW > (size_t)P ? 2 * (size_t)g.NW : (size_t)P);
         if (n < (size_t)sms) n = (size_t)sms;
         CREATE_CUDA(dalloc(&ctx->part_r2, n));
     }
@@ -813,7 +816,7 @@ sensai_status sensai_serve_start(sensai_ctx* ctx, const sensai_serve_params* sp)
     if (ctx->serve) return fail(SENSAI_EBUSY, "already serving");
     if (sp->slots < 1 || sp->slots > 64) return fail(SENSAI_EINVAL, "slots must be 1..64");
     if (sp->max_pixels < 1 || sp->max_pixels >= (1LL << 31)) return fail(SENSAI_EINVAL, "bad max_pixels");
-    if (sp->max_observed < 1 || sp->max_observed > 128) return fail(SENSAI_EINVAL, "max_observed must be 1..128");
+    if (sp->max_observed < 1 || sp->max_observed > 256) return fail(SENSAI_EINVAL, "max_observed must be 1..256");
     if (!ctx->ge_set) return fail(SENSAI_ESTATE, "serving needs a learnt or set state (gamma_eps unset)");
     SENSAI_CUDA(ctx, cudaDeviceSynchronize());
     DevScalars sc;

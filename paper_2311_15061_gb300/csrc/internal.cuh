@@ -439,11 +439,15 @@ cudaError_t launch_sweep(const SweepArgs& a, int maxobs, int grid, cudaStream_t 
 int sweep_block_size();
 int sweep_smem_bytes(const Geom& g);
 int sweep_grid_size(const Geom& g, int maxobs, int device);
+cudaError_t preload_sweep_variants();   // load every code-sweep kernel variant now
+int sweep_lanes(int maxobs);            // lanes per patch for a largest |Omega_i|: 1, or 2 above 96
+cudaError_t preload_tiled_variants();
 
 // How a code sweep runs: the whole dictionary resident in shared memory
 // (slice_atoms = 0) or streamed in slices of slice_atoms atoms.
 struct SweepPlan {
     int grid = 0;
+    int lanes = 1;             // lanes per patch (2 above 96 observed pixels)
     int slice_atoms = 0;
     int slices = 0;
     long long slice_stride = 0;

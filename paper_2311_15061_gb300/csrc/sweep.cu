@@ -32,8 +32,8 @@ namespace sensai {
 constexpr int kSweepThreads = 256;
 constexpr int kSweepWarps = kSweepThreads / 32;
 
-template <int MAXOBS>
-__global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_kernel(const SweepArgs a)
+template <int MAXOBS, int LANES>
+__global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 && LANES == 1 ? 2 : 1)) sweep_kernel(const SweepArgs a)
 {
     extern __shared__ float smem[];
     const int K = a.g.K, P = a.g.P, KB = a.g.KB;
@@ -55,24 +55,27 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
     const CodeConst c = code_const(a.sc);
     const uint32_t t_it = launch_t(a.t, a.t_dev, a.sc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int half = LANES == 1 ? 0 : (lane & 1);
+    const unsigned int units = (unsigned int)NW * LANES;   // 32-patch chunks, or 16-patch halves
     CodeTally tl;
 
     for (;;) {
         if (lane == 0) chunk_slot[warp] = atomicAdd(a.chunk_counter, 1u);
         __syncwarp();
-        const unsigned int chunk = chunk_slot[warp];
+        const unsigned int unit = chunk_slot[warp];
         __syncwarp();
-        if (chunk >= (unsigned int)NW) break;
-        const long long i = (long long)chunk * 32 + lane;   // < Npad: weight blocks exist
+        if (unit >= units) break;
+        const long long i = (long long)unit * PatchLanes<LANES>::kPatchesPerWarp + lane / LANES;   // < Npad
         const bool valid = i < N;
 
         const int nobs = valid ? (int)a.nobs[i] : 0;
-        const int wmax = __reduce_max_sync(0xffffffffu, nobs);
+        const int nl = LANES == 1 ? nobs : (nobs + 1 - half) / 2;   // this lane's pixels
+        const int wmax = __reduce_max_sync(0xffffffffu, nl);
         const long long org = valid ? patch_origin(a.g, i) : 0;
 
         int offK[MAXOBS];
         float r[MAXOBS];
-        gather_patch<MAXOBS>(a, i, nobs, org, ldK, offK, r);
+        gather_patch<MAXOBS, LANES>(a, i, nl, org, ldK, offK, r, half);
 
         // residual r = x - D w on the observed pixels, from the stored weights
         for (int kb = 0; kb < KB; ++kb)
@@ -89,12 +92,12 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_k
             if (kb + 1 < KB)   // prefetch the next block behind this block's work
                 nb = load_w8(a.W + ((long long)(kb + 1) * Npad + i) * kAtomBlock);
             const int kbase = kb * kAtomBlock;
-            code_block<MAXOBS>(Ds + kbase, lpi + kbase, offK, r, wmax, nobs, i, valid, kbase,
-                               min(kAtomBlock, K - kbase), c, a.keys, t_it, a.Zb, NW, chunk, lane,
-                               w0, w1, w2, w3, w4, w5, w6, w7, s2, tl);
-            store_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock, w0, w1, w2, w3, w4, w5, w6, w7);
+            code_block<MAXOBS, LANES>(Ds + kbase, lpi + kbase, offK, r, wmax, nobs, i, valid, kbase,
+                                      min(kAtomBlock, K - kbase), c, a.keys, t_it, a.Zb, NW, unit, lane,
+                                      w0, w1, w2, w3, w4, w5, w6, w7, s2, tl);
+            if (half == 0) store_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock, w0, w1, w2, w3, w4, w5, w6, w7);
         }
-        finish_patch<MAXOBS>(a, r, wmax, nobs, i, chunk, lane, s2);
+        finish_patch<MAXOBS, LANES>(a, r, wmax, nl, i, unit, lane, s2);
     }
     flush_counts(a, lane, tl);
 }
@@ -108,11 +111,19 @@ int sweep_smem_bytes(const Geom& g)
     return (int)(sizeof(float) * ((size_t)(g.P + 1) * ldK + Kpad));
 }
 
-template <int MAXOBS>
-static void* kernel_ptr() { return (void*)sweep_kernel<MAXOBS>; }
+template <int MAXOBS, int LANES = 1>
+static void* kernel_ptr() { return (void*)sweep_kernel<MAXOBS, LANES>; }
+
+int sweep_lanes(int maxobs) { return maxobs > 96 ? 2 : 1; }
 
 static void* select_kernel(int maxobs)
 {
+    if (maxobs > 96) {   // two lanes per patch: per-lane capacity 64 / 96 / 128
+        if (maxobs <= 128) return kernel_ptr<64, 2>();
+        if (maxobs <= 192) return kernel_ptr<96, 2>();
+        if (maxobs <= 256) return kernel_ptr<128, 2>();
+        return nullptr;
+    }
     if (maxobs <= 8) return kernel_ptr<8>();
     if (maxobs <= 16) return kernel_ptr<16>();
     if (maxobs <= 24) return kernel_ptr<24>();
@@ -122,9 +133,20 @@ static void* select_kernel(int maxobs)
     if (maxobs <= 64) return kernel_ptr<64>();
     if (maxobs <= 72) return kernel_ptr<72>();
     if (maxobs <= 80) return kernel_ptr<80>();
-    if (maxobs <= 96) return kernel_ptr<96>();
-    if (maxobs <= 128) return kernel_ptr<128>();
-    return nullptr;
+    return kernel_ptr<96>();
+}
+
+// Loads every variant now: with lazy module loading the first launch of a
+// variant would otherwise pay for it (a latency spike when serving).
+cudaError_t preload_sweep_variants()
+{
+    const int obs[] = {8, 16, 24, 32, 40, 48, 64, 72, 80, 96, 128, 192, 256};
+    for (int m : obs) {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, select_kernel(m));
+        if (e != cudaSuccess) return e;
+    }
+    return preload_tiled_variants();
 }
 
 int sweep_grid_size(const Geom& g, int maxobs, int device)
@@ -137,9 +159,9 @@ int sweep_grid_size(const Geom& g, int maxobs, int device)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSweepThreads, smem) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
     if (per_sm < 1) return 0;
-    long long chunks = g.NW;
+    long long units = (long long)g.NW * sweep_lanes(maxobs);
     long long warps_per_cta = kSweepThreads / 32;
-    long long want = (chunks + warps_per_cta - 1) / warps_per_cta;
+    long long want = (units + warps_per_cta - 1) / warps_per_cta;
     long long grid = (long long)per_sm * sms;
     return (int)(grid < want ? grid : want);
 }

@@ -29,6 +29,28 @@ __device__ __forceinline__ CodeConst code_const(const DevScalars* sc)
     return c;
 }
 
+// Lanes per patch.  Above 96 observed pixels a patch's pixels are split over
+// a lane pair (pixel j on lane j % 2) so that each lane's residual still fits
+// in registers.  The pair's partial sums are combined by one shuffle; both
+// lanes then make the same draw, and only the even lane stores and counts.
+// A warp then owns 16 patches, half of a 32-patch activity word.
+template <int LANES>
+struct PatchLanes {
+    static_assert(LANES == 1 || LANES == 2, "1 or 2 lanes per patch");
+    static constexpr int kPatchesPerWarp = 32 / LANES;
+};
+
+// The 16 even-lane bits of a ballot, in order (lane 2m -> bit m).
+__device__ __forceinline__ uint32_t even_lane_bits(uint32_t b)
+{
+    b &= 0x55555555u;
+    b = (b | (b >> 1)) & 0x33333333u;
+    b = (b | (b >> 2)) & 0x0F0F0F0Fu;
+    b = (b | (b >> 4)) & 0x00FF00FFu;
+    b = (b | (b >> 8)) & 0x0000FFFFu;
+    return b;
+}
+
 // Work tallies of one thread (changed updates, their |Omega_i|, z = 1 draws).
 struct CodeTally {
     unsigned int chg_n = 0, chg_obs = 0, act_n = 0;
@@ -60,11 +82,13 @@ __device__ __forceinline__ void rebuild_block(const float* Dcol, const int (&off
 // The block's atoms kbase .. kbase + kend - 1 in order; w0..w7 hold the
 // block's stored weights on entry and its new weights on return (padding
 // atoms keep their zero).  Dcol points at the block's first atom column.
-template <int MAXOBS>
+// MAXOBS is per lane; unit is the warp's work unit (a 32-patch chunk, or with
+// two lanes per patch a 16-patch half chunk).
+template <int MAXOBS, int LANES = 1>
 __device__ __forceinline__ void code_block(const float* Dcol, const float* lpi_blk, const int (&offK)[MAXOBS],
                                            float (&r)[MAXOBS], int wmax, int nobs, long long i, bool valid,
                                            int kbase, int kend, const CodeConst& c, const PhiloxKeys& keys,
-                                           uint32_t t, uint32_t* Zb, int NW, unsigned int chunk, int lane,
+                                           uint32_t t, uint32_t* Zb, int NW, unsigned int unit, int lane,
                                            float& w0, float& w1, float& w2, float& w3,
                                            float& w4, float& w5, float& w6, float& w7, float& s2,
                                            CodeTally& tl)
@@ -87,6 +111,11 @@ __device__ __forceinline__ void code_block(const float* Dcol, const float* lpi_b
                     h = fmaf(d, r[j], h);
                 }
             }
+            if (LANES == 2) {   // a + b on one lane, b + a on the other: identical sums
+                n += __shfl_xor_sync(0xffffffffu, n, 1);
+                h += __shfl_xor_sync(0xffffffffu, h, 1);
+            }
+            const bool owner = LANES == 1 || (lane & 1) == 0;
             const float w_old = w0;
             const float g = fmaf(w_old, n, h);
             const float lam = fmaf(c.ge, n, c.gs);
@@ -103,13 +132,17 @@ __device__ __forceinline__ void code_block(const float* Dcol, const float* lpi_b
             w_new = 0.0f;
             if (z) {
                 w_new = fmaf(normal32(blk.y, blk.z), sqrtf(rlam), c.ge * g * rlam);
-                s2 = fmaf(w_new, w_new, s2);
-                tl.act_n += 1;
+                if (owner) {
+                    s2 = fmaf(w_new, w_new, s2);
+                    tl.act_n += 1;
+                }
             }
             const float dw = w_new - w_old;
             if (dw != 0.0f) {
-                tl.chg_n += 1;
-                tl.chg_obs += (unsigned int)nobs;
+                if (owner) {
+                    tl.chg_n += 1;
+                    tl.chg_obs += (unsigned int)nobs;
+                }
 #pragma unroll
                 for (int g4 = 0; g4 < MAXOBS / 4; ++g4) {
                     if (4 * g4 >= wmax) break;
@@ -124,7 +157,12 @@ __device__ __forceinline__ void code_block(const float* Dcol, const float* lpi_b
             // after the sweep (a per-atom shared-memory count here would
             // serialise the next atom's dictionary loads behind its store)
             const uint32_t bal = __ballot_sync(0xffffffffu, z);
-            if (lane == 0) Zb[(long long)k * NW + chunk] = bal;
+            if (LANES == 1) {
+                if (lane == 0) Zb[(long long)k * NW + unit] = bal;
+            } else if (lane == 0) {   // this half of the chunk's word (little-endian: patches 0-15 low)
+                reinterpret_cast<uint16_t*>(Zb)[((long long)k * NW + (unit >> 1)) * 2 + (unit & 1)] =
+                    (uint16_t)even_lane_bits(bal);
+            }
         }
         w0 = w1; w1 = w2; w2 = w3; w3 = w4; w4 = w5; w5 = w6; w6 = w7; w7 = w_new;
     }
@@ -132,50 +170,54 @@ __device__ __forceinline__ void code_block(const float* Dcol, const float* lpi_b
 
 // End of a patch's sweep: scatter the residual to the dictionary step's
 // layout (when kept) and publish the chunk's sum of s^2 and ||r||^2 (fixed-order warp sums).
-template <int MAXOBS>
+// nobs is this lane's count of observed pixels (its pixel jj is the patch's
+// pixel jj * LANES + half); the partials are per work unit.
+template <int MAXOBS, int LANES = 1>
 __device__ __forceinline__ void finish_patch(const SweepArgs& a, const float (&r)[MAXOBS], int wmax, int nobs,
-                                             long long i, unsigned int chunk, int lane, float s2)
+                                             long long i, unsigned int unit, int lane, float s2)
 {
     const long long N = a.g.N;
+    const int half = LANES == 1 ? 0 : (lane & 1);
     float r2 = 0.0f;
 #pragma unroll
     for (int g4 = 0; g4 < MAXOBS / 4; ++g4) {
         if (4 * g4 >= wmax) break;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int j = 4 * g4 + u;
-            if (j < nobs) {
-                if (a.R) a.R[a.pos[(long long)j * N + i]] = r[j];
-                r2 = fmaf(r[j], r[j], r2);
+            const int jj = 4 * g4 + u;
+            if (jj < nobs) {
+                if (a.R) a.R[a.pos[(long long)(jj * LANES + half) * N + i]] = r[jj];
+                r2 = fmaf(r[jj], r[jj], r2);
             }
         }
     }
     double s2d = warp_sum((double)s2);
     double r2d = warp_sum((double)r2);
     if (lane == 0) {
-        a.part_s2[chunk] = s2d;
-        a.part_r2[chunk] = r2d;
+        a.part_s2[unit] = s2d;
+        a.part_r2[unit] = r2d;
     }
 }
 
 // Observed pixels of patch i: within-patch offsets into a [p][ld] shared
 // dictionary (padding slots point at the zero row p = P) and the frame values.
-template <int MAXOBS>
+// nobs: this lane's count; its pixel jj is the patch's pixel jj * LANES + half.
+template <int MAXOBS, int LANES = 1>
 __device__ __forceinline__ void gather_patch(const SweepArgs& a, long long i, int nobs, long long org, int ld,
-                                             int (&offK)[MAXOBS], float (&r)[MAXOBS])
+                                             int (&offK)[MAXOBS], float (&r)[MAXOBS], int half)
 {
     const long long N = a.g.N;
     const int P = a.g.P;
 #pragma unroll
-    for (int j = 0; j < MAXOBS; ++j) {
+    for (int jj = 0; jj < MAXOBS; ++jj) {
         int p = P;
         float v = 0.0f;
-        if (j < nobs) {
-            p = a.obs[(long long)j * N + i];
+        if (jj < nobs) {
+            p = a.obs[(long long)(jj * LANES + half) * N + i];
             v = a.x[org + a.imgoff[p]];
         }
-        offK[j] = p * ld;
-        r[j] = v;
+        offK[jj] = p * ld;
+        r[jj] = v;
     }
 }
 

@@ -23,6 +23,8 @@ constexpr int kTiledThreads = 256;
 constexpr int kTiledWarps = kTiledThreads / 32;
 constexpr long long kMbarSpins = 1LL << 20;   // try_wait polls before giving up
 
+__global__ void count_active_kernel(Geom g, const uint32_t* Zb, int* m);
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -87,8 +89,8 @@ __global__ void slice_dictionary_kernel(Geom g, const float* D, float* Dsl, int 
     }
 }
 
-template <int MAXOBS>
-__global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_tiled_kernel(const SweepArgs a)
+template <int MAXOBS, int LANES>
+__global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 && LANES == 1 ? 2 : 1)) sweep_tiled_kernel(const SweepArgs a)
 {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -104,7 +106,8 @@ __global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_t
     float* buf0 = smem;
     float* buf1 = smem + stride;
     float* lpi = smem + 2 * stride;        // Kpad
-    const long long nitems = (NW + kTiledWarps - 1) / kTiledWarps;
+    const unsigned int units = (unsigned int)NW * LANES;   // 32-patch chunks, or 16-patch halves
+    const long long nitems = (units + kTiledWarps - 1) / kTiledWarps;
 
     for (int k = threadIdx.x; k < Kpad; k += blockDim.x) lpi[k] = k < K ? a.lpi[k] : 0.0f;
     if (threadIdx.x == 0) {
@@ -124,6 +127,7 @@ __global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_t
     const CodeConst c = code_const(a.sc);
     const uint32_t t_it = launch_t(a.t, a.t_dev, a.sc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int half = LANES == 1 ? 0 : (lane & 1);
     CodeTally tl;
     // Use q of the slice buffers reads slice q % S from buffer q & 1 (each
     // item makes 2 S consecutive uses).  With S <= 2 both buffers keep their
@@ -137,17 +141,18 @@ __global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_t
         const unsigned int item = item_s;
         __syncthreads();
         if (item >= (unsigned int)nitems) break;
-        const unsigned int chunk = item * kTiledWarps + warp;
-        const bool warp_on = chunk < (unsigned int)NW;
-        const long long i = (long long)chunk * 32 + lane;
+        const unsigned int unit = item * kTiledWarps + warp;
+        const bool warp_on = unit < units;
+        const long long i = (long long)unit * PatchLanes<LANES>::kPatchesPerWarp + lane / LANES;
         const bool valid = warp_on && i < N;
         const int nobs = valid ? (int)a.nobs[i] : 0;
-        const int wmax = __reduce_max_sync(0xffffffffu, nobs);
+        const int nl = LANES == 1 ? nobs : (nobs + 1 - half) / 2;   // this lane's pixels
+        const int wmax = __reduce_max_sync(0xffffffffu, nl);
         const long long org = valid ? patch_origin(a.g, i) : 0;
 
         int offK[MAXOBS];
         float r[MAXOBS];
-        gather_patch<MAXOBS>(a, valid ? i : 0, nobs, org, ldS, offK, r);
+        gather_patch<MAXOBS, LANES>(a, valid ? i : 0, nl, org, ldS, offK, r, half);
 
         float s2 = 0.0f;
         W8 nb;
@@ -176,10 +181,12 @@ __global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_t
                             float w4 = nb.v[4], w5 = nb.v[5], w6 = nb.v[6], w7 = nb.v[7];
                             if (kb + 1 < KB) nb = load_w8(a.W + ((long long)(kb + 1) * Npad + i) * kAtomBlock);
                             const int kbase = kb * kAtomBlock;
-                            code_block<MAXOBS>(Dbuf + (kb - kb0) * kAtomBlock, lpi + kbase, offK, r, wmax, nobs, i,
-                                               valid, kbase, min(kAtomBlock, K - kbase), c, a.keys, t_it, a.Zb, NW,
-                                               chunk, lane, w0, w1, w2, w3, w4, w5, w6, w7, s2, tl);
-                            store_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock, w0, w1, w2, w3, w4, w5, w6, w7);
+                            code_block<MAXOBS, LANES>(Dbuf + (kb - kb0) * kAtomBlock, lpi + kbase, offK, r, wmax,
+                                                      nobs, i, valid, kbase, min(kAtomBlock, K - kbase), c, a.keys,
+                                                      t_it, a.Zb, NW, unit, lane, w0, w1, w2, w3, w4, w5, w6, w7,
+                                                      s2, tl);
+                            if (half == 0)
+                                store_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock, w0, w1, w2, w3, w4, w5, w6, w7);
                         }
                     }
                 }
@@ -191,7 +198,7 @@ __global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_t
             }
         }
         if (!ok) break;
-        if (warp_on) finish_patch<MAXOBS>(a, r, wmax, nobs, i, chunk, lane, s2);
+        if (warp_on) finish_patch<MAXOBS, LANES>(a, r, wmax, nl, i, unit, lane, s2);
     }
     // The copies still in flight land before the CTA exits: uses q and q + 1
     // when buffers are refilled, else the initial copies not yet waited for.
@@ -206,11 +213,17 @@ __global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 ? 2 : 1)) sweep_t
     flush_counts(a, lane, tl);
 }
 
-template <int MAXOBS>
-static void* tiled_ptr() { return (void*)sweep_tiled_kernel<MAXOBS>; }
+template <int MAXOBS, int LANES = 1>
+static void* tiled_ptr() { return (void*)sweep_tiled_kernel<MAXOBS, LANES>; }
 
 static void* select_tiled(int maxobs)
 {
+    if (maxobs > 96) {   // two lanes per patch: per-lane capacity 64 / 96 / 128
+        if (maxobs <= 128) return tiled_ptr<64, 2>();
+        if (maxobs <= 192) return tiled_ptr<96, 2>();
+        if (maxobs <= 256) return tiled_ptr<128, 2>();
+        return nullptr;
+    }
     if (maxobs <= 8) return tiled_ptr<8>();
     if (maxobs <= 16) return tiled_ptr<16>();
     if (maxobs <= 24) return tiled_ptr<24>();
@@ -220,9 +233,21 @@ static void* select_tiled(int maxobs)
     if (maxobs <= 64) return tiled_ptr<64>();
     if (maxobs <= 72) return tiled_ptr<72>();
     if (maxobs <= 80) return tiled_ptr<80>();
-    if (maxobs <= 96) return tiled_ptr<96>();
-    if (maxobs <= 128) return tiled_ptr<128>();
-    return nullptr;
+    return tiled_ptr<96>();
+}
+
+cudaError_t preload_tiled_variants()
+{
+    const int obs[] = {8, 16, 24, 32, 40, 48, 64, 72, 80, 96, 128, 192, 256};
+    for (int m : obs) {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, select_tiled(m));
+        if (e != cudaSuccess) return e;
+    }
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, (void*)slice_dictionary_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (void*)count_active_kernel);
+    return e;
 }
 
 long long slice_stride_floats(const Geom& g, int KS)
@@ -245,7 +270,7 @@ int tiled_slice_atoms(const Geom& g, int maxobs, int device)
     if (cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess)
         return 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return 0;
-    const int ctas = maxobs <= 48 ? 2 : 1;
+    const int ctas = maxobs <= 48 ? 2 : 1;   // the variant's occupancy (two-lane variants: 1)
     const size_t reserve = 1024 + 64;   // per-CTA system reserve and the static barriers
     size_t budget = (size_t)per_sm_smem / ctas;
     budget = budget > reserve ? budget - reserve : 0;
@@ -279,7 +304,7 @@ int tiled_grid_size(const Geom& g, int maxobs, int KS, int device)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTiledThreads, smem) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
     if (per_sm < 1) return 0;
-    const long long items = (g.NW + kTiledWarps - 1) / kTiledWarps;
+    const long long items = ((long long)g.NW * sweep_lanes(maxobs) + kTiledWarps - 1) / kTiledWarps;
     const long long grid = (long long)per_sm * sms;
     return (int)(grid < items ? grid : items);
 }
@@ -317,6 +342,7 @@ bool plan_sweep(const Geom& g, int maxobs, int device, bool force_stream, int fo
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return false;
     if (!force_stream && sweep_smem_bytes(g) <= optin) {
         p.grid = sweep_grid_size(g, maxobs, device);
+        p.lanes = sweep_lanes(maxobs);
         *out = p;
         return p.grid > 0;
     }
@@ -331,6 +357,7 @@ bool plan_sweep(const Geom& g, int maxobs, int device, bool force_stream, int fo
     p.slices = (Kpad + KS - 1) / KS;
     p.slice_stride = slice_stride_floats(g, KS);
     p.grid = tiled_grid_size(g, maxobs, KS, device);
+    p.lanes = sweep_lanes(maxobs);
     *out = p;
     return p.grid > 0;
 }

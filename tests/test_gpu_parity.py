@@ -345,3 +345,18 @@ def test_flags_validation():
         assert err.value.status == sensai.SENSAI_EINVAL
     with pytest.raises(sensai.SensaiError):          # slice larger than the padded K
         gpu_context(prm, mask, _stream(24))
+
+
+# --- two lanes per patch: more than 96 observed pixels ---
+
+@pytest.mark.parametrize("case", [
+    dict(M=(40, 40), B=(12, 12), S=(1, 1), K=16, frac=1.0, full_mask=True),   # |Omega_i| = 144: 2 x 96
+    dict(M=(30, 33), B=(11, 11), S=(1, 1), K=12, frac=1.0, full_mask=True),   # |Omega_i| = 121: 2 x 64
+    dict(M=(12, 12, 64), B=(4, 4, 32), S=(1, 1, 32), K=32, frac=0.3),        # spectrum-cube patches, P = 512
+])
+def test_two_lanes_per_patch(case):
+    _phase_parity(**case, warm=1)
+
+
+def test_two_lanes_streamed():
+    _phase_parity(M=(12, 12, 64), B=(4, 4, 32), S=(1, 1, 32), K=32, frac=0.3, warm=1, flags=_stream(16), slices=2)
