@@ -276,6 +276,16 @@ sensai_status sensai_batch_tune(sensai_batch* b, int32_t iters_per_trial, void* 
 
 void sensai_batch_destroy(sensai_batch* b);
 
+/* Failure detection self-test.  Every device-side wait of the library (the
+ * dictionary kernel's grid barrier, the streamed sweep's mbarrier waits) gives
+ * up after about one second, sets SENSAI_ETIMEOUT in the context's status
+ * word and returns, instead of hanging the GPU.  This runs one such wait on a
+ * condition that nothing satisfies (which = 0: grid barrier, 1: mbarrier) on
+ * the current device.  It returns SENSAI_ETIMEOUT when the wait gave up as
+ * designed (the expected result; the device stays usable), SENSAI_OK if it
+ * did not give up, SENSAI_EINVAL for another `which`.  Takes ~1 s. */
+sensai_status sensai_selftest_wait(int32_t which);
+
 /* Per-phase device timing.  enable = 1 clears the record and starts timing:
  * every later phase records a CUDA event pair on its launching stream;
  * enable = 0 stops.  sensai_profile_read synchronises and returns, for the

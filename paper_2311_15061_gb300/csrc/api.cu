@@ -1150,3 +1150,24 @@ sensai_status sensai_batch_tune(sensai_batch* b, int32_t iters_per_trial, void* 
 }
 
 }  // extern "C"
+
+extern "C" sensai_status sensai_selftest_wait(int32_t which)
+{
+    if (which != 0 && which != 1) return fail(SENSAI_EINVAL, "which must be 0 (grid barrier) or 1 (mbarrier)");
+    int* status = nullptr;
+    unsigned int* count = nullptr;
+    cudaError_t e = cudaMalloc((void**)&status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&count, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(status, 0, sizeof(int));
+    if (e == cudaSuccess)
+        e = which == 0 ? launch_barrier_timeout_selftest(count, status, nullptr) : launch_mbar_timeout_selftest(status, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int st = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (status) cudaFree(status);
+    if (count) cudaFree(count);
+    if (e != cudaSuccess) return cuda_failure(nullptr, e, "wait self-test", __LINE__);
+    if (st == SENSAI_ETIMEOUT) return fail(SENSAI_ETIMEOUT, "the bounded %s wait gave up as designed",
+                                          which == 0 ? "grid-barrier" : "mbarrier");
+    return SENSAI_OK;
+}

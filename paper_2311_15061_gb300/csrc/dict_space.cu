@@ -57,9 +57,10 @@ __device__ bool grid_barrier(unsigned int* count, unsigned int target, int* stat
         __threadfence();
         atomicAdd(count, 1u);
         volatile unsigned int* vc = count;
+        const unsigned long long t0 = global_ns();
         long long spins = 0;
         while (*vc < target) {
-            if (++spins > kBarrierSpins) {
+            if (++spins > kBarrierSpins || ((spins & 255) == 0 && global_ns() - t0 > kWaitLimitNs)) {
                 atomicExch(status, (int)SENSAI_ETIMEOUT);
                 ok = 0;
                 break;
@@ -71,6 +72,22 @@ __device__ bool grid_barrier(unsigned int* count, unsigned int target, int* stat
     }
     __syncthreads();
     return ok_s != 0;
+}
+
+// Self-test of the bounded grid barrier: one CTA waits for an arrival count
+// that nothing reaches (target = 2 with one CTA) and must give up with
+// SENSAI_ETIMEOUT in *status.
+__global__ void barrier_timeout_selftest_kernel(unsigned int* count, int* status)
+{
+    grid_barrier(count, 2u, status);
+}
+
+cudaError_t launch_barrier_timeout_selftest(unsigned int* count, int* status, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    barrier_timeout_selftest_kernel<<<1, 64, 0, s>>>(count, status);
+    return cudaGetLastError();
 }
 
 // Within-patch multi-index of chain q.

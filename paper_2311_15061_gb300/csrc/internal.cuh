@@ -61,6 +61,16 @@ struct DevScalars {
     uint32_t t_iter;   // iteration index for kernels replayed from a CUDA graph
 };
 
+// Nanoseconds since an arbitrary origin (the GPU's global timer); bounds the
+// device-side waits by time as well as by poll count.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s: every device wait gives up after this
+
 // Iteration index of a launch: the argument, or the device copy when the
 // launch is replayed from a captured graph (t_dev set).
 __device__ __forceinline__ uint32_t launch_t(uint32_t t, bool t_dev, const DevScalars* sc)
@@ -471,6 +481,9 @@ cudaError_t launch_sweep_tiled(const SweepArgs& a, int maxobs, int grid, cudaStr
 cudaError_t launch_dict(const DictArgs& a, int max_slots, cudaStream_t s);
 cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);
 cudaError_t launch_set_iteration(DevScalars* sc, uint32_t t, cudaStream_t s);   // sc->t_iter = t
+// Self-tests of the bounded device waits (each gives up after ~1 s).
+cudaError_t launch_barrier_timeout_selftest(unsigned int* count, int* status, cudaStream_t s);
+cudaError_t launch_mbar_timeout_selftest(int* status, cudaStream_t s);
 // Builds the plan and its residual array R, filling pos[j][i] for the
 // sweep; plan->grid = 0 (and no allocation) when the kernel cannot run.
 cudaError_t ds_build(const Geom& g, const uint8_t* host_mask, const uint16_t* obs, const uint16_t* nobs, int device,

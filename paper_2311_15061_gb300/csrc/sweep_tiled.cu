@@ -63,12 +63,33 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// Wait for phase `parity` of the barrier; false after kMbarSpins polls.
+// Wait for phase `parity` of the barrier; false after kMbarSpins polls or
+// kWaitLimitNs, whichever comes first.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
 {
-    for (long long spins = 0; spins < kMbarSpins; ++spins)
+    const unsigned long long t0 = global_ns();
+    for (long long spins = 0; spins < kMbarSpins; ++spins) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((spins & 63) == 63 && global_ns() - t0 > kWaitLimitNs) break;
+    }
     return false;
+}
+
+// Self-test of the bounded wait: an mbarrier that nothing completes.  One
+// thread; writes SENSAI_ETIMEOUT to *status when the wait gives up.
+__global__ void mbar_timeout_selftest_kernel(int* status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *status = mbar_wait(&bar, 0) ? (int)SENSAI_OK : (int)SENSAI_ETIMEOUT;
+}
+
+cudaError_t launch_mbar_timeout_selftest(int* status, cudaStream_t s)
+{
+    mbar_timeout_selftest_kernel<<<1, 32, 0, s>>>(status);
+    return cudaGetLastError();
 }
 
 // Slice s of the dictionary in its shared-memory layout: [P + 1][ldS], entry

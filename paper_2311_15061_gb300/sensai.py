@@ -29,7 +29,7 @@ EXPORTED = [
     "sensai_get_state", "sensai_set_state", "sensai_get_stats", "sensai_profile", "sensai_profile_read",
     "sensai_reconstruct_static", "sensai_serve_start", "sensai_submit_frame", "sensai_serve_drain",
     "sensai_serve_stop", "sensai_batch_create", "sensai_batch_learn", "sensai_batch_tune",
-    "sensai_batch_destroy", "sensai_last_error",
+    "sensai_batch_destroy", "sensai_selftest_wait", "sensai_last_error",
 ]
 
 
@@ -128,6 +128,7 @@ _SIG = {
     "sensai_batch_learn": (_st, [_vp, _i32, _vp]),
     "sensai_batch_tune": (_st, [_vp, _i32, _vp, ctypes.POINTER(_i32)]),
     "sensai_batch_destroy": (None, [_vp]),
+    "sensai_selftest_wait": (_st, [_i32]),
     "sensai_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIG.items():
@@ -405,3 +406,8 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def sensai_selftest_wait(which):
+    """Status of the bounded-wait self-test (SENSAI_ETIMEOUT is the expected result)."""
+    return _lib.sensai_selftest_wait(int(which))
