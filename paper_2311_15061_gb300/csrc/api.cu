@@ -328,6 +328,7 @@ sensai_status run_hyper(sensai_ctx* ctx, cudaStream_t s)
     if (st != SENSAI_OK) return st;
     HyperArgs a{};
     a.g = ctx->g;
+    a.Zb = ctx->Zb;
     a.m = ctx->m;
     a.part_s2 = ctx->part_s2;
     a.n_s2 = ctx->n_s2;
@@ -349,7 +350,7 @@ sensai_status run_hyper(sensai_ctx* ctx, cudaStream_t s)
     PhaseTimer timer(ctx, kPhaseHyper, s);
     SENSAI_CUDA(ctx, launch_hyper(a, s));
     timer.stop();
-    ctx->launches += 1;
+    ctx->launches += 2;
     return SENSAI_OK;
 }
 

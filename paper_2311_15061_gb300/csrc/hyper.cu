@@ -26,34 +26,80 @@ __device__ double sum_partials(const double* v, int n, double* red)
     return block_sum(acc, red);
 }
 
-__global__ void __launch_bounds__(kHyperThreads) hyper_kernel(const HyperArgs a)
+// pi_k ~ Beta(a/K + m_k, b(K-1)/K + N - m_k), one CTA per atom: m_k is the
+// popcount of atom k's activity words (fixed-order sum), and the Beta draw's
+// two Gamma draws run on two warps (the value is beta_draw's).  Spreading the
+// atoms over the SMs matters: FP64 throughput per SM is low on this part.
+__global__ void __launch_bounds__(256) pi_kernel(const HyperArgs a)
+{
+    __shared__ int red[8];
+    __shared__ double g2_s;
+    const int k = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t t_it = launch_t(a.t, a.t_dev, a.sc);
+    const uint32_t* z = a.Zb + (long long)k * a.g.NW;
+    int c = 0;
+    for (int w = threadIdx.x; w < a.g.NW; w += blockDim.x) c += __popc(z[w]);
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) red[warp] = c;
+    __syncthreads();
+    int mk = 0;
+    for (int w = 0; w < 8; ++w) mk += red[w];
+    const double alpha = a.a_over_K + (double)mk;
+    const double beta = a.b_scaled + (double)a.g.N - (double)mk;
+    if (threadIdx.x == 32) g2_s = gamma_draw(beta, a.seed, (uint32_t)k, 0, t_it, kTagPiB);
+    double g1 = 0.0;
+    if (threadIdx.x == 0) g1 = gamma_draw(alpha, a.seed, (uint32_t)k, 0, t_it, kTagPiA);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double pi = g1 / (g1 + g2_s);
+        a.pi[k] = pi;
+        a.lpi[k] = (float)(log(pi) - log1p(-pi));
+        a.m[k] = mk;
+    }
+}
+
+// gamma_s and gamma_eps from fixed-order FP64 sums of the per-unit partials;
+// the two Gamma draws on two warps.  Last kernel of an iteration: advances the
+// replay iteration index.
+__global__ void __launch_bounds__(kHyperThreads) gamma_kernel(const HyperArgs a)
 {
     __shared__ double red[kHyperThreads / 32];
+    __shared__ double ge_s;
     const int K = a.g.K;
     const uint32_t t_it = launch_t(a.t, a.t_dev, a.sc);
     const double s2 = sum_partials(a.part_s2, a.n_s2, red);
     const double r2 = sum_partials(a.part_r2, a.n_r2, red);
     double mk = 0.0;
-    if ((int)threadIdx.x < K) {
-        mk = (double)a.m[threadIdx.x];
-        const double alpha = a.a_over_K + mk;
-        const double beta = a.b_scaled + (double)a.g.N - mk;
-        const double pi = beta_draw(alpha, beta, a.seed, threadIdx.x, t_it);
-        a.pi[threadIdx.x] = pi;
-        a.lpi[threadIdx.x] = (float)(log(pi) - log1p(-pi));
-    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x) mk += (double)a.m[k];
     const double mtot = block_sum(mk, red);
+    __shared__ double bc[3];
     if (threadIdx.x == 0) {
-        const double gs = gamma_draw(a.c + 0.5 * mtot, a.seed, 0, 0, t_it, kTagGs) / (a.d + 0.5 * s2);
-        const double ge = gamma_draw(a.e + 0.5 * (double)a.n_observed, a.seed, 0, 0, t_it, kTagGe)
-                        / (a.f + 0.5 * r2);
+        bc[0] = s2;
+        bc[1] = r2;
+        bc[2] = mtot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 32)
+        ge_s = gamma_draw(a.e + 0.5 * (double)a.n_observed, a.seed, 0, 0, t_it, kTagGe) / (a.f + 0.5 * bc[1]);
+    double gs = 0.0;
+    if (threadIdx.x == 0) gs = gamma_draw(a.c + 0.5 * bc[2], a.seed, 0, 0, t_it, kTagGs) / (a.d + 0.5 * bc[0]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
         a.sc->gamma_s = gs;
-        a.sc->gamma_eps = ge;
-        a.sc->sum_s2 = s2;
-        a.sc->sum_r2 = r2;
-        a.sc->n_active = (long long)mtot;
+        a.sc->gamma_eps = ge_s;
+        a.sc->sum_s2 = bc[0];
+        a.sc->sum_r2 = bc[1];
+        a.sc->n_active = (long long)bc[2];
         if (a.t_dev) a.sc->t_iter = t_it + 1u;   // the next replay's iteration
     }
+}
+
+cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s)
+{
+    pi_kernel<<<a.g.K, 256, 0, s>>>(a);
+    gamma_kernel<<<1, kHyperThreads, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 __global__ void set_iteration_kernel(DevScalars* sc, uint32_t t) { sc->t_iter = t; }
@@ -64,11 +110,6 @@ cudaError_t launch_set_iteration(DevScalars* sc, uint32_t t, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s)
-{
-    hyper_kernel<<<1, kHyperThreads, 0, s>>>(a);
-    return cudaGetLastError();
-}
 
 // d_kp ~ N(0, 1/P) from counter (p, k, 0, INIT).
 __global__ void init_dictionary_kernel(Geom g, float* D, unsigned long long seed)

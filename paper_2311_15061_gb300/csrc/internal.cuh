@@ -330,7 +330,7 @@ struct SweepArgs {
     const int* pos;            // [maxobs][N] residual position of observed pixel j of patch i
     float* R;                  // residual in the dictionary step's layout, R[pos[j][i]]
                                // (null: inpainting only, the residual is not kept)
-    int* m;                    // [K] active count per atom (written after the sweep)
+    int* m;                    // [K] active count per atom (written by the pi draws)
     double* part_s2;           // [NW] per 32-patch chunk
     double* part_r2;           // [NW] per 32-patch chunk
     unsigned int* chunk_counter;  // work counter, zeroed before each launch
@@ -399,7 +399,8 @@ struct DictSpaceArgs {
 
 struct HyperArgs {
     Geom g;
-    const int* m;              // [K]
+    const uint32_t* Zb;        // [K][NW] activity words (the counts m_k come from them)
+    int* m;                    // [K] active counts, written by the pi draws
     const double* part_s2;
     int n_s2;
     const double* part_r2;
@@ -466,8 +467,7 @@ struct SweepPlan {
 // fits, or force_slice_atoms (a multiple of 8 no larger than that) if > 0.
 bool plan_sweep(const Geom& g, int maxobs, int device, bool force_stream, int force_slice_atoms, SweepPlan* out);
 long long slice_capacity_floats(const Geom& g);
-// One code sweep by plan, then the per-atom active counts a.m from the
-// activity words.  Dsl (slice_capacity_floats floats) is needed when
+// One code sweep by plan.  Dsl (slice_capacity_floats floats) is needed when
 // streamed and is refilled from a.D on the stream first.  *nlaunch (if not
 // null) receives the number of kernels launched.
 cudaError_t launch_code_sweep(SweepArgs a, const SweepPlan& plan, int maxobs, float* Dsl, cudaStream_t s,
@@ -479,7 +479,7 @@ int tiled_grid_size(const Geom& g, int maxobs, int KS, int device);
 cudaError_t launch_slice_dictionary(const Geom& g, const float* D, float* Dsl, int KS, cudaStream_t s);
 cudaError_t launch_sweep_tiled(const SweepArgs& a, int maxobs, int grid, cudaStream_t s);
 cudaError_t launch_dict(const DictArgs& a, int max_slots, cudaStream_t s);
-cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);
+cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);   // two kernels: pi draws, then gammas
 cudaError_t launch_set_iteration(DevScalars* sc, uint32_t t, cudaStream_t s);   // sc->t_iter = t
 // Self-tests of the bounded device waits (each gives up after ~1 s).
 cudaError_t launch_barrier_timeout_selftest(unsigned int* count, int* status, cudaStream_t s);

@@ -296,6 +296,7 @@ static sensai_status process_frame(ServeEngine* e, ServeSlot* sl, const ServeReq
         FRAME_TRY(launch_code_sweep(a, plan, maxobs, sl->Dsl, s, nullptr));
         HyperArgs h{};
         h.g = g;
+        h.Zb = sl->Zb;
         h.m = sl->m;
         h.part_s2 = sl->part_s2;
         h.n_s2 = g.NW * plan.lanes;

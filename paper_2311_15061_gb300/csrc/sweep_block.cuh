@@ -153,9 +153,8 @@ __device__ __forceinline__ void code_block(const float* Dcol, const float* lpi_b
                     }
                 }
             }
-            // the activity word; per-atom counts are summed from these words
-            // after the sweep (a per-atom shared-memory count here would
-            // serialise the next atom's dictionary loads behind its store)
+            // the activity word; the pi draws sum the per-atom counts from
+            // these words
             const uint32_t bal = __ballot_sync(0xffffffffu, z);
             if (LANES == 1) {
                 if (lane == 0) Zb[(long long)k * NW + unit] = bal;

@@ -23,8 +23,6 @@ constexpr int kTiledThreads = 256;
 constexpr int kTiledWarps = kTiledThreads / 32;
 constexpr long long kMbarSpins = 1LL << 20;   // try_wait polls before giving up
 
-__global__ void count_active_kernel(Geom g, const uint32_t* Zb, int* m);
-
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -266,9 +264,7 @@ cudaError_t preload_tiled_variants()
         if (e != cudaSuccess) return e;
     }
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, (void*)slice_dictionary_kernel);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (void*)count_active_kernel);
-    return e;
+    return cudaFuncGetAttributes(&fa, (void*)slice_dictionary_kernel);
 }
 
 long long slice_stride_floats(const Geom& g, int KS)
@@ -383,24 +379,6 @@ bool plan_sweep(const Geom& g, int maxobs, int device, bool force_stream, int fo
     return p.grid > 0;
 }
 
-// m_k = the number of patches with z_ik = 1: popcounts of atom k's activity
-// words, one CTA per atom, fixed-order block sum.
-__global__ void __launch_bounds__(256) count_active_kernel(Geom g, const uint32_t* Zb, int* m)
-{
-    __shared__ int red[8];
-    const uint32_t* z = Zb + (long long)blockIdx.x * g.NW;
-    int c = 0;
-    for (int w = threadIdx.x; w < g.NW; w += blockDim.x) c += __popc(z[w]);
-    c = __reduce_add_sync(0xffffffffu, c);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int sum = 0;
-        for (int w = 0; w < 8; ++w) sum += red[w];
-        m[blockIdx.x] = sum;
-    }
-}
-
 cudaError_t launch_code_sweep(SweepArgs a, const SweepPlan& plan, int maxobs, float* Dsl, cudaStream_t s,
                               int* nlaunch)
 {
@@ -422,9 +400,8 @@ cudaError_t launch_code_sweep(SweepArgs a, const SweepPlan& plan, int maxobs, fl
         n = 2;
     }
     if (e != cudaSuccess) return e;
-    count_active_kernel<<<a.g.K, 256, 0, s>>>(a.g, a.Zb, a.m);
-    if (nlaunch) *nlaunch = n + 1;
-    return cudaGetLastError();
+    if (nlaunch) *nlaunch = n;
+    return cudaSuccess;
 }
 
 }  // namespace sensai
