@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 && LANES == 1 ? 2
         const int wmax = __reduce_max_sync(0xffffffffu, nl);
         const long long org = valid ? patch_origin(a.g, i) : 0;
 
-        int offK[MAXOBS];
+        PixelOffsets<MAXOBS> offK;
         float r[MAXOBS];
         gather_patch<MAXOBS, LANES>(a, i, nl, org, ldK, offK, r, half);
 
@@ -118,9 +118,10 @@ int sweep_lanes(int maxobs) { return maxobs > 96 ? 2 : 1; }
 
 static void* select_kernel(int maxobs)
 {
-    if (maxobs > 96) {   // two lanes per patch: per-lane capacity 64 / 96 / 128
+    if (maxobs > 96) {   // two lanes per patch: per-lane capacity 64 / 96 / 112 / 128
         if (maxobs <= 128) return kernel_ptr<64, 2>();
         if (maxobs <= 192) return kernel_ptr<96, 2>();
+        if (maxobs <= 224) return kernel_ptr<112, 2>();
         if (maxobs <= 256) return kernel_ptr<128, 2>();
         return nullptr;
     }
@@ -140,7 +141,7 @@ static void* select_kernel(int maxobs)
 // variant would otherwise pay for it (a latency spike when serving).
 cudaError_t preload_sweep_variants()
 {
-    const int obs[] = {8, 16, 24, 32, 40, 48, 64, 72, 80, 96, 128, 192, 256};
+    const int obs[] = {8, 16, 24, 32, 40, 48, 64, 72, 80, 96, 128, 192, 224, 256};
     for (int m : obs) {
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, select_kernel(m));

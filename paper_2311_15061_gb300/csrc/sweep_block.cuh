@@ -40,6 +40,30 @@ struct PatchLanes {
     static constexpr int kPatchesPerWarp = 32 / LANES;
 };
 
+// Shared-memory offsets (in floats) of a lane's observed pixels.  At a
+// per-lane capacity above 96 two 16-bit offsets share a register, which keeps
+// the residual in registers up to 112; every offset is below 58,112 (a dictionary
+// buffer fits in 227 KB), so 16 bits hold it.
+template <int MAXOBS>
+struct PixelOffsets {
+    static constexpr bool kPacked = MAXOBS > 96;
+    uint32_t v[kPacked ? MAXOBS / 2 : MAXOBS];
+    __device__ __forceinline__ int operator[](int j) const
+    {
+        if (kPacked) return (int)((j & 1) ? (v[j >> 1] >> 16) : (v[j >> 1] & 0xffffu));
+        return (int)v[j];
+    }
+    __device__ __forceinline__ void set(int j, int off)
+    {
+        if (kPacked) {
+            if (j & 1) v[j >> 1] |= (uint32_t)off << 16;
+            else v[j >> 1] = (uint32_t)off;
+        } else {
+            v[j] = (uint32_t)off;
+        }
+    }
+};
+
 // The 16 even-lane bits of a ballot, in order (lane 2m -> bit m).
 __device__ __forceinline__ uint32_t even_lane_bits(uint32_t b)
 {
@@ -58,7 +82,7 @@ struct CodeTally {
 
 // r -= sum_k d_k w_k over the block's non-zero stored weights.
 template <int MAXOBS>
-__device__ __forceinline__ void rebuild_block(const float* Dcol, const int (&offK)[MAXOBS], float (&r)[MAXOBS],
+__device__ __forceinline__ void rebuild_block(const float* Dcol, const PixelOffsets<MAXOBS>& offK, float (&r)[MAXOBS],
                                               int wmax, const W8& wb)
 {
     const float* wv = wb.v;
@@ -85,7 +109,7 @@ __device__ __forceinline__ void rebuild_block(const float* Dcol, const int (&off
 // MAXOBS is per lane; unit is the warp's work unit (a 32-patch chunk, or with
 // two lanes per patch a 16-patch half chunk).
 template <int MAXOBS, int LANES = 1>
-__device__ __forceinline__ void code_block(const float* Dcol, const float* lpi_blk, const int (&offK)[MAXOBS],
+__device__ __forceinline__ void code_block(const float* Dcol, const float* lpi_blk, const PixelOffsets<MAXOBS>& offK,
                                            float (&r)[MAXOBS], int wmax, int nobs, long long i, bool valid,
                                            int kbase, int kend, const CodeConst& c, const PhiloxKeys& keys,
                                            uint32_t t, uint32_t* Zb, int NW, unsigned int unit, int lane,
@@ -203,7 +227,7 @@ __device__ __forceinline__ void finish_patch(const SweepArgs& a, const float (&r
 // nobs: this lane's count; its pixel jj is the patch's pixel jj * LANES + half.
 template <int MAXOBS, int LANES = 1>
 __device__ __forceinline__ void gather_patch(const SweepArgs& a, long long i, int nobs, long long org, int ld,
-                                             int (&offK)[MAXOBS], float (&r)[MAXOBS], int half)
+                                             PixelOffsets<MAXOBS>& offK, float (&r)[MAXOBS], int half)
 {
     const long long N = a.g.N;
     const int P = a.g.P;
@@ -215,7 +239,7 @@ __device__ __forceinline__ void gather_patch(const SweepArgs& a, long long i, in
             p = a.obs[(long long)(jj * LANES + half) * N + i];
             v = a.x[org + a.imgoff[p]];
         }
-        offK[jj] = p * ld;
+        offK.set(jj, p * ld);
         r[jj] = v;
     }
 }

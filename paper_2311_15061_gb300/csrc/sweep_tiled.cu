@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 && LANES == 1 ? 2
         const int wmax = __reduce_max_sync(0xffffffffu, nl);
         const long long org = valid ? patch_origin(a.g, i) : 0;
 
-        int offK[MAXOBS];
+        PixelOffsets<MAXOBS> offK;
         float r[MAXOBS];
         gather_patch<MAXOBS, LANES>(a, valid ? i : 0, nl, org, ldS, offK, r, half);
 
@@ -237,9 +237,10 @@ static void* tiled_ptr() { return (void*)sweep_tiled_kernel<MAXOBS, LANES>; }
 
 static void* select_tiled(int maxobs)
 {
-    if (maxobs > 96) {   // two lanes per patch: per-lane capacity 64 / 96 / 128
+    if (maxobs > 96) {   // two lanes per patch: per-lane capacity 64 / 96 / 112 / 128
         if (maxobs <= 128) return tiled_ptr<64, 2>();
         if (maxobs <= 192) return tiled_ptr<96, 2>();
+        if (maxobs <= 224) return tiled_ptr<112, 2>();
         if (maxobs <= 256) return tiled_ptr<128, 2>();
         return nullptr;
     }
@@ -257,7 +258,7 @@ static void* select_tiled(int maxobs)
 
 cudaError_t preload_tiled_variants()
 {
-    const int obs[] = {8, 16, 24, 32, 40, 48, 64, 72, 80, 96, 128, 192, 256};
+    const int obs[] = {8, 16, 24, 32, 40, 48, 64, 72, 80, 96, 128, 192, 224, 256};
     for (int m : obs) {
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, select_tiled(m));

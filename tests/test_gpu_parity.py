@@ -352,6 +352,8 @@ def test_flags_validation():
 @pytest.mark.parametrize("case", [
     dict(M=(40, 40), B=(12, 12), S=(1, 1), K=16, frac=1.0, full_mask=True),   # |Omega_i| = 144: 2 x 96
     dict(M=(30, 33), B=(11, 11), S=(1, 1), K=12, frac=1.0, full_mask=True),   # |Omega_i| = 121: 2 x 64
+    dict(M=(40, 40), B=(14, 14), S=(1, 1), K=16, frac=1.0, full_mask=True),   # |Omega_i| = 196: 2 x 112 (packed)
+    dict(M=(36, 36), B=(15, 15), S=(1, 1), K=8, frac=1.0, full_mask=True),    # |Omega_i| = 225: 2 x 128
     dict(M=(12, 12, 64), B=(4, 4, 32), S=(1, 1, 32), K=32, frac=0.3),        # spectrum-cube patches, P = 512
 ])
 def test_two_lanes_per_patch(case):
