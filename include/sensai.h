@@ -246,10 +246,12 @@ sensai_status sensai_serve_stop(sensai_ctx* ctx);
  *
  * The paper processes frames one after another; a batch runs the Gibbs
  * iterations (the BPFA section's sampler) of n independent contexts together
- * so that small problems share the GPU.  One iteration of every instance is
- * captured once into a CUDA graph, each instance on its own branch, and
- * replayed per iteration.  Each context ends exactly where sensai_learn(iters)
- * on it alone would: the same kernels, the same draws.
+ * so that small problems share the GPU.  One iteration of all instances is a
+ * few launches that each cover every instance (code sweeps per kernel
+ * variant, dictionary draws per storage mode, pi and gamma draws), captured
+ * once into a CUDA graph and replayed per iteration.  Each context ends
+ * exactly where sensai_learn(iters) on it alone would: the same per-instance
+ * arithmetic, the same draws.
  *
  * Contexts must have a frame set (sensai_set_frame or an earlier call with a
  * frame), share one device, be created with SENSAI_FLAG_CHAIN_DICTIONARY (the
@@ -265,10 +267,10 @@ sensai_status sensai_batch_create(sensai_ctx* const* ctxs, int32_t n, sensai_bat
  * waits for the batch). */
 sensai_status sensai_batch_learn(sensai_batch* b, int32_t iters, void* cuda_stream);
 
-/* Autotuner: times the batch with the code sweep of each instance limited to
- * 1/1, 1/2, 1/4, 1/8 and 1/16 of its full grid (narrower grids let more
- * instances run side by side), iters_per_trial iterations per candidate, and
- * keeps the fastest; *divisor (may be NULL) receives it.  The trials are real
+/* Autotuner: times the batch with the batched code sweeps' grids at 4 / d
+ * waves of the GPU for d = 1, 2, 4, 8, 16 (the CTAs are divided among the
+ * instances in proportion to their work), iters_per_trial iterations per
+ * candidate, and keeps the fastest; *divisor (may be NULL) receives d.  The trials are real
  * Gibbs iterations: each candidate runs one warm-up and iters_per_trial timed
  * iterations, so every instance advances by 5 * (1 + iters_per_trial)
  * iterations.  Results do not depend on the choice. */

@@ -5,6 +5,7 @@
 // every arithmetic step of the sampler runs in the kernels of sweep.cu,
 // dict.cu, hyper.cu and geometry.cu.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -86,7 +87,6 @@ struct sensai_ctx {
     DevScalars* sc = nullptr;
     int* pos = nullptr;         // [maxobs][N] residual position of each observed pixel of each patch
     bool t_on_device = false;   // kernels read the iteration index from sc->t_iter (graph capture)
-    int grid_cap = 0;           // > 0: at most this many CTAs for the code sweep (batches)
     DictSpacePlan ds{};         // space-organised dictionary sweep (cooperative launch), when it runs
     ServeEngine* serve = nullptr;   // live serving engine, when started
 };
@@ -226,11 +226,8 @@ sensai_status ensure_code_stats(sensai_ctx* ctx, cudaStream_t s)
     return SENSAI_OK;
 }
 
-sensai_status run_sweep(sensai_ctx* ctx, cudaStream_t s)
+SweepArgs sweep_args(const sensai_ctx* ctx)
 {
-    if (!ctx->frame_set) return fail(SENSAI_ESTATE, "no frame: call sensai_set_frame or pass a frame");
-    sensai_status st = ensure_gamma_eps(ctx, s);
-    if (st != SENSAI_OK) return st;
     SweepArgs a{};
     a.g = ctx->g;
     a.x = ctx->x;
@@ -252,8 +249,59 @@ sensai_status run_sweep(sensai_ctx* ctx, cudaStream_t s)
     a.keys = philox_round_keys(ctx->prm.seed);
     a.t = (uint32_t)ctx->t;
     a.t_dev = ctx->t_on_device;
-    SweepPlan plan = ctx->sweep_plan;
-    if (ctx->grid_cap > 0 && plan.grid > ctx->grid_cap) plan.grid = ctx->grid_cap;
+    return a;
+}
+
+DictArgs dict_args(const sensai_ctx* ctx)
+{
+    DictArgs a{};
+    a.g = ctx->g;
+    a.D = ctx->D;
+    a.W = ctx->W;
+    a.Ilist = ctx->Ilist;
+    a.Rbase = ctx->Rbase;
+    a.R = ctx->R;
+    a.sc = ctx->sc;
+    a.part_r2 = ctx->part_r2;
+    a.seed = ctx->prm.seed;
+    a.t = (uint32_t)ctx->t;
+    a.t_dev = ctx->t_on_device;
+    return a;
+}
+
+HyperArgs hyper_args(const sensai_ctx* ctx)
+{
+    HyperArgs a{};
+    a.g = ctx->g;
+    a.Zb = ctx->Zb;
+    a.m = ctx->m;
+    a.part_s2 = ctx->part_s2;
+    a.n_s2 = ctx->n_s2;
+    a.part_r2 = ctx->part_r2;
+    a.n_r2 = ctx->n_r2;
+    a.n_observed = ctx->n_observed;
+    a.a_over_K = ctx->a_over_K;
+    a.b_scaled = ctx->b_scaled;
+    a.c = ctx->prm.c;
+    a.d = ctx->prm.d;
+    a.e = ctx->prm.e;
+    a.f = ctx->prm.f;
+    a.pi = ctx->pi;
+    a.lpi = ctx->lpi;
+    a.sc = ctx->sc;
+    a.seed = ctx->prm.seed;
+    a.t = (uint32_t)ctx->t;
+    a.t_dev = ctx->t_on_device;
+    return a;
+}
+
+sensai_status run_sweep(sensai_ctx* ctx, cudaStream_t s)
+{
+    if (!ctx->frame_set) return fail(SENSAI_ESTATE, "no frame: call sensai_set_frame or pass a frame");
+    sensai_status st = ensure_gamma_eps(ctx, s);
+    if (st != SENSAI_OK) return st;
+    const SweepArgs a = sweep_args(ctx);
+    const SweepPlan plan = ctx->sweep_plan;
     PhaseTimer timer(ctx, kPhaseCodes, s);
     int nl = 0;
     SENSAI_CUDA(ctx, launch_code_sweep(a, plan, ctx->maxobs, ctx->Dsl, s, &nl));
@@ -297,18 +345,7 @@ sensai_status run_dictionary(sensai_ctx* ctx, cudaStream_t s)
         ctx->n_r2 = ctx->ds.grid;
         return SENSAI_OK;
     }
-    DictArgs a{};
-    a.g = ctx->g;
-    a.D = ctx->D;
-    a.W = ctx->W;
-    a.Ilist = ctx->Ilist;
-    a.Rbase = ctx->Rbase;
-    a.R = ctx->R;
-    a.sc = ctx->sc;
-    a.part_r2 = ctx->part_r2;
-    a.seed = ctx->prm.seed;
-    a.t = (uint32_t)ctx->t;
-    a.t_dev = ctx->t_on_device;
+    const DictArgs a = dict_args(ctx);
     PhaseTimer timer(ctx, kPhaseDict, s);
     SENSAI_CUDA(ctx, launch_dict(a, ctx->max_slots, s));
     timer.stop();
@@ -326,27 +363,7 @@ sensai_status run_hyper(sensai_ctx* ctx, cudaStream_t s)
     if (st != SENSAI_OK) return st;
     st = ensure_residual(ctx, s);
     if (st != SENSAI_OK) return st;
-    HyperArgs a{};
-    a.g = ctx->g;
-    a.Zb = ctx->Zb;
-    a.m = ctx->m;
-    a.part_s2 = ctx->part_s2;
-    a.n_s2 = ctx->n_s2;
-    a.part_r2 = ctx->part_r2;
-    a.n_r2 = ctx->n_r2;
-    a.n_observed = ctx->n_observed;
-    a.a_over_K = ctx->a_over_K;
-    a.b_scaled = ctx->b_scaled;
-    a.c = ctx->prm.c;
-    a.d = ctx->prm.d;
-    a.e = ctx->prm.e;
-    a.f = ctx->prm.f;
-    a.pi = ctx->pi;
-    a.lpi = ctx->lpi;
-    a.sc = ctx->sc;
-    a.seed = ctx->prm.seed;
-    a.t = (uint32_t)ctx->t;
-    a.t_dev = ctx->t_on_device;
+    const HyperArgs a = hyper_args(ctx);
     PhaseTimer timer(ctx, kPhaseHyper, s);
     SENSAI_CUDA(ctx, launch_hyper(a, s));
     timer.stop();
@@ -916,27 +933,70 @@ sensai_status sensai_profile_read(sensai_ctx* ctx, double* ms, int64_t* counts)
 
 // ------------------------------------------------------------------ batches --
 //
-// One Gibbs iteration of every instance (code sweep with its active counts,
-// dictionary draw, pi / gamma draws) is captured once into a CUDA graph, each
-// instance on its own forked stream so that independent instances run side by
-// side on the GPU.  The graph is replayed once per iteration.  Its kernels
-// read the iteration index from each context's device scalars, and the hyper
-// kernel advances it, so every replay draws with fresh counters.  The results
-// are exactly those of sensai_learn on each context alone.
+// A batch learns n independent contexts together.  One Gibbs iteration of all
+// instances is a handful of launches, each covering every instance:
+//  * the code sweeps: one launch per kernel variant, CTAs divided among the
+//    instances in proportion to their work, each instance's CTAs sharing its
+//    patches through the instance's own chunk counter;
+//  * the per-chain dictionary draws: one CTA per (instance, chain), one
+//    launch per storage mode;
+//  * the pi draws (one CTA per (instance, atom)) and the gamma draws (one CTA
+//    per instance).
+// The iteration is captured once into a CUDA graph and replayed per
+// iteration.  The kernels read the iteration index from each context's device
+// scalars and the gamma draws advance it, so every replay draws with fresh
+// counters, and every context ends exactly where sensai_learn on it alone
+// would.
+
+namespace {
+
+struct BatchClass {
+    int key = 0;                 // sweep: template capacity; dictionary: storage mode
+    bool streamed = false;       // sweep: dictionary streamed in slices
+    std::vector<int> members;    // instance indices, in argument-array order
+    size_t smem = 0;
+    int grid = 0;
+    int args_off = 0;            // first member in the class's argument array
+    int table_off = 0;           // its CTA prefix table in the batch's table array
+};
+
+}  // namespace
+
+constexpr int kBatchLanes = 8;   // side streams: launches of different classes overlap
 
 struct sensai_batch {
     std::vector<sensai_ctx*> ctx;
-    std::vector<cudaStream_t> streams;   // capture branches, one per instance
-    std::vector<cudaEvent_t> joins;
-    std::vector<long long> launches;     // kernels of one iteration, per instance
     cudaStream_t origin = nullptr;       // the stream graphs are captured on and replayed from
-    cudaEvent_t fork = nullptr, in = nullptr, out = nullptr;
+    cudaStream_t side[kBatchLanes] = {};
+    cudaEvent_t fork = nullptr, joins[kBatchLanes] = {};
+    cudaEvent_t in = nullptr, out = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int divisor = 1;                     // code-sweep CTAs per instance: full grid / divisor
+    int divisor = 1;                     // code-sweep grid: 4 waves / divisor
+    // device tables of the current graph
+    SweepArgs* d_sweep = nullptr;
+    DictArgs* d_dict = nullptr;
+    HyperArgs* d_hyper = nullptr;
+    unsigned int* d_counters = nullptr;  // per-instance chunk counters of the batched sweeps
+    int* d_tables = nullptr;             // CTA prefix tables
+    std::vector<BatchClass> sweeps, dicts;
+    int pi_table = 0, gamma_table = 0, pi_grid = 0;
+    long long launches_per_iter = 0;
 };
 
 namespace {
+
+void batch_free_tables(sensai_batch* b)
+{
+    void* ptrs[] = {b->d_sweep, b->d_dict, b->d_hyper, b->d_counters, b->d_tables};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    b->d_sweep = nullptr;
+    b->d_dict = nullptr;
+    b->d_hyper = nullptr;
+    b->d_counters = nullptr;
+    b->d_tables = nullptr;
+}
 
 void batch_drop_graph(sensai_batch* b)
 {
@@ -944,53 +1004,212 @@ void batch_drop_graph(sensai_batch* b)
     if (b->graph) cudaGraphDestroy(b->graph);
     b->exec = nullptr;
     b->graph = nullptr;
+    batch_free_tables(b);
+}
+
+// Per-instance arguments of the batched kernels, their classes and CTA
+// partitions, uploaded to device tables.
+sensai_status batch_build(sensai_batch* b)
+{
+    const int n = (int)b->ctx.size();
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->ctx[0]->device);
+    if (e != cudaSuccess) return cuda_failure(nullptr, e, "cudaDeviceGetAttribute", __LINE__);
+    if ((e = cudaMalloc((void**)&b->d_counters, sizeof(unsigned int) * n)) != cudaSuccess)
+        return cuda_failure(nullptr, e, "batch counters", __LINE__);
+    std::vector<SweepArgs> sa(n);
+    std::vector<DictArgs> da(n);
+    std::vector<HyperArgs> ha(n);
+    for (int i = 0; i < n; ++i) {
+        sensai_ctx* c = b->ctx[i];
+        c->t_on_device = true;
+        sa[i] = sweep_args(c);
+        da[i] = dict_args(c);
+        ha[i] = hyper_args(c);
+        c->t_on_device = false;
+        sa[i].chunk_counter = b->d_counters + i;
+        if (c->sweep_plan.slice_atoms > 0) {
+            sa[i].Dsl = c->Dsl;
+            sa[i].slice_atoms = c->sweep_plan.slice_atoms;
+            sa[i].slices = c->sweep_plan.slices;
+            sa[i].slice_stride = c->sweep_plan.slice_stride;
+        }
+        ha[i].n_s2 = c->g.NW * c->sweep_plan.lanes;   // the sweep's partials
+        ha[i].n_r2 = c->g.P;                          // the per-chain dictionary draws' partials
+    }
+    // classes
+    b->sweeps.clear();
+    b->dicts.clear();
+    for (int i = 0; i < n; ++i) {
+        sensai_ctx* c = b->ctx[i];
+        const bool streamed = c->sweep_plan.slice_atoms > 0;
+        const int key = sweep_variant(c->maxobs > 0 ? c->maxobs : 1);
+        BatchClass* cl = nullptr;
+        for (BatchClass& x : b->sweeps)
+            if (x.key == key && x.streamed == streamed) cl = &x;
+        if (!cl) {
+            b->sweeps.push_back(BatchClass{});
+            cl = &b->sweeps.back();
+            cl->key = key;
+            cl->streamed = streamed;
+        }
+        cl->members.push_back(i);
+        const size_t sm = streamed ? tiled_smem_bytes(c->g, c->sweep_plan.slice_atoms) : (size_t)sweep_smem_bytes(c->g);
+        cl->smem = std::max(cl->smem, sm);
+        size_t dsm = 0;
+        const int mode = dict_mode(c->max_slots, &dsm);
+        if (mode < 0) return fail(SENSAI_ECUDA, "no dictionary launch mode for instance %d", i);
+        BatchClass* dl = nullptr;
+        for (BatchClass& x : b->dicts)
+            if (x.key == mode) dl = &x;
+        if (!dl) {
+            b->dicts.push_back(BatchClass{});
+            dl = &b->dicts.back();
+            dl->key = mode;
+        }
+        dl->members.push_back(i);
+        dl->smem = std::max(dl->smem, dsm);
+    }
+    // CTA partitions and argument order
+    std::vector<int> tables;
+    std::vector<SweepArgs> sa_ord;
+    std::vector<DictArgs> da_ord;
+    for (BatchClass& cl : b->sweeps) {
+        const int per_sm = cl.streamed ? sweep_tiled_multi_ctas_per_sm(cl.key, cl.smem)
+                                       : sweep_multi_ctas_per_sm(cl.key, cl.smem);
+        if (per_sm < 1) return fail(SENSAI_ECUDA, "no batched code-sweep configuration (capacity %d)", cl.key);
+        const long long total = std::max<long long>((long long)cl.members.size(),
+                                                    4LL * per_sm * sms / std::max(1, b->divisor));
+        double work_sum = 0.0;
+        std::vector<double> work;
+        for (int i : cl.members) {
+            const sensai_ctx* c = b->ctx[i];
+            const double obs = (double)c->n_observed / std::max<long long>(1, c->g.N);
+            work.push_back((double)c->g.N * c->g.K * (75.0 + 3.0 * obs));
+            work_sum += work.back();
+        }
+        cl.args_off = (int)sa_ord.size();
+        cl.table_off = (int)tables.size();
+        int acc = 0;
+        for (size_t m = 0; m < cl.members.size(); ++m) {
+            const sensai_ctx* c = b->ctx[cl.members[m]];
+            const long long units = (long long)c->g.NW * c->sweep_plan.lanes;
+            const long long cap = (units + 7) / 8;     // 8 warps per CTA
+            long long ctas = (long long)std::floor((double)total * work[m] / work_sum);
+            ctas = std::max<long long>(1, std::min(ctas, cap));
+            tables.push_back(acc);
+            acc += (int)ctas;
+            sa_ord.push_back(sa[cl.members[m]]);
+        }
+        tables.push_back(acc);
+        cl.grid = acc;
+    }
+    for (BatchClass& cl : b->dicts) {
+        cl.args_off = (int)da_ord.size();
+        cl.table_off = (int)tables.size();
+        int acc = 0;
+        for (int i : cl.members) {
+            tables.push_back(acc);
+            acc += b->ctx[i]->g.P;
+            da_ord.push_back(da[i]);
+        }
+        tables.push_back(acc);
+        cl.grid = acc;
+    }
+    b->pi_table = (int)tables.size();
+    int acc = 0;
+    for (int i = 0; i < n; ++i) {
+        tables.push_back(acc);
+        acc += b->ctx[i]->g.K;
+    }
+    tables.push_back(acc);
+    b->pi_grid = acc;
+    b->gamma_table = (int)tables.size();
+    for (int i = 0; i <= n; ++i) tables.push_back(i);
+    // upload
+    e = cudaMalloc((void**)&b->d_sweep, sizeof(SweepArgs) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_dict, sizeof(DictArgs) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_hyper, sizeof(HyperArgs) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tables, sizeof(int) * tables.size());
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_sweep, sa_ord.data(), sizeof(SweepArgs) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_dict, da_ord.data(), sizeof(DictArgs) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_hyper, ha.data(), sizeof(HyperArgs) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_tables, tables.data(), sizeof(int) * tables.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_failure(nullptr, e, "batch tables", __LINE__);
+    return SENSAI_OK;
 }
 
 // Captures one iteration of every instance (the caller has run the eager
-// setup: frame, gamma_eps, residual).
+// setup: frame, gamma_eps, residual, iteration indices).
 sensai_status batch_capture(sensai_batch* b)
 {
     batch_drop_graph(b);
-    const size_t n = b->ctx.size();
-    for (size_t i = 0; i < n; ++i) {
-        sensai_ctx* c = b->ctx[i];
-        c->grid_cap = b->divisor > 1 ? std::max(1, c->sweep_plan.grid / b->divisor) : 0;
-    }
-    cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
-    if (e != cudaSuccess) return cuda_failure(nullptr, e, "cudaStreamBeginCapture", __LINE__);
-    sensai_status st = SENSAI_OK;
-    e = cudaEventRecord(b->fork, b->origin);
-    for (size_t i = 0; i < n && st == SENSAI_OK && e == cudaSuccess; ++i) {
-        sensai_ctx* c = b->ctx[i];
-        const bool prof = c->profiling;
-        const long long l0 = c->launches;
-        c->profiling = false;
-        c->t_on_device = true;
-        e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
-        if (e == cudaSuccess) st = run_sweep(c, b->streams[i]);
-        if (e == cudaSuccess && st == SENSAI_OK) st = run_dictionary(c, b->streams[i]);
-        if (e == cudaSuccess && st == SENSAI_OK) st = run_hyper(c, b->streams[i]);
-        c->t_on_device = false;
-        c->profiling = prof;
-        b->launches[i] = c->launches - l0;
-        c->launches = l0;
-        if (e == cudaSuccess && st == SENSAI_OK) e = cudaEventRecord(b->joins[i], b->streams[i]);
-        if (e == cudaSuccess && st == SENSAI_OK) e = cudaStreamWaitEvent(b->origin, b->joins[i], 0);
-    }
-    cudaGraph_t g = nullptr;
-    const cudaError_t e_end = cudaStreamEndCapture(b->origin, &g);
+    sensai_status st = batch_build(b);
     if (st != SENSAI_OK) {
-        if (g) cudaGraphDestroy(g);
+        batch_free_tables(b);
         return st;
     }
+    const int n = (int)b->ctx.size();
+    const cudaStream_t s = b->origin;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return cuda_failure(nullptr, e, "cudaStreamBeginCapture", __LINE__);
+    long long launches = 0;
+    e = cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned int) * n, s);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const sensai_ctx* c = b->ctx[i];
+        if (c->sweep_plan.slice_atoms > 0) {
+            e = launch_slice_dictionary(c->g, c->D, c->Dsl, c->sweep_plan.slice_atoms, s);
+            ++launches;
+        }
+    }
+    // the classes of one phase run side by side (fork / join), phases in order
+    auto fork = [&](size_t nclass) {
+        if (e == cudaSuccess) e = cudaEventRecord(b->fork, s);
+        for (size_t j = 0; j < std::min<size_t>(nclass, kBatchLanes) && e == cudaSuccess; ++j)
+            e = cudaStreamWaitEvent(b->side[j], b->fork, 0);
+    };
+    auto join = [&](size_t nclass) {
+        for (size_t j = 0; j < std::min<size_t>(nclass, kBatchLanes) && e == cudaSuccess; ++j) {
+            e = cudaEventRecord(b->joins[j], b->side[j]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->joins[j], 0);
+        }
+    };
+    fork(b->sweeps.size());
+    for (size_t j = 0; j < b->sweeps.size() && e == cudaSuccess; ++j) {
+        const BatchClass& cl = b->sweeps[j];
+        const SweepArgs* args = b->d_sweep + cl.args_off;
+        const int* table = b->d_tables + cl.table_off;
+        const int m = (int)cl.members.size();
+        const cudaStream_t ss = b->side[j % kBatchLanes];
+        e = cl.streamed ? launch_sweep_tiled_multi(args, table, m, cl.key, cl.grid, cl.smem, ss)
+                        : launch_sweep_multi(args, table, m, cl.key, cl.grid, cl.smem, ss);
+        ++launches;
+    }
+    join(b->sweeps.size());
+    fork(b->dicts.size());
+    for (size_t j = 0; j < b->dicts.size() && e == cudaSuccess; ++j) {
+        const BatchClass& cl = b->dicts[j];
+        e = launch_dict_multi(b->d_dict + cl.args_off, b->d_tables + cl.table_off, (int)cl.members.size(), cl.key,
+                              cl.smem, cl.grid, b->side[j % kBatchLanes]);
+        ++launches;
+    }
+    join(b->dicts.size());
+    if (e == cudaSuccess) {
+        e = launch_hyper_multi(b->d_hyper, b->d_tables + b->pi_table, b->d_tables + b->gamma_table, n, b->pi_grid, s);
+        launches += 2;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(s, &g);
     if (e == cudaSuccess) e = e_end;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
     if (e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         b->exec = nullptr;
+        batch_free_tables(b);
         return cuda_failure(nullptr, e, "batch graph capture", __LINE__);
     }
     b->graph = g;
+    b->launches_per_iter = launches;
     return SENSAI_OK;
 }
 
@@ -1004,7 +1223,6 @@ sensai_status batch_prepare(sensai_batch* b)
         if (!c->frame_set) return fail(SENSAI_ESTATE, "batch instance %zu has no frame", i);
         if ((st = ensure_gamma_eps(c, b->origin)) != SENSAI_OK) return st;
         if ((st = ensure_residual(c, b->origin)) != SENSAI_OK) return st;
-        if ((st = ensure_code_stats(c, b->origin)) != SENSAI_OK) return st;
         SENSAI_CUDA(c, launch_set_iteration(c->sc, (uint32_t)c->t, b->origin));
         c->launches += 1;
     }
@@ -1013,12 +1231,12 @@ sensai_status batch_prepare(sensai_batch* b)
 
 void batch_advance(sensai_batch* b, int iters)
 {
-    for (size_t i = 0; i < b->ctx.size(); ++i) {
-        sensai_ctx* c = b->ctx[i];
+    for (sensai_ctx* c : b->ctx) {
         c->t += iters;
-        c->launches += b->launches[i] * iters;
         c->codes_valid = true;
         c->resid_valid = true;
+        c->n_s2 = c->g.NW * c->sweep_plan.lanes;
+        c->n_r2 = c->g.P;
     }
 }
 
@@ -1049,15 +1267,14 @@ void sensai_batch_destroy(sensai_batch* b)
     if (!b) return;
     if (b->origin) cudaStreamSynchronize(b->origin);
     batch_drop_graph(b);
-    for (cudaStream_t s : b->streams)
-        if (s) cudaStreamDestroy(s);
-    for (cudaEvent_t ev : b->joins)
-        if (ev) cudaEventDestroy(ev);
-    cudaEvent_t evs[] = {b->fork, b->in, b->out};
+    cudaEvent_t evs[] = {b->in, b->out, b->fork};
     for (cudaEvent_t ev : evs)
         if (ev) cudaEventDestroy(ev);
+    for (int j = 0; j < kBatchLanes; ++j) {
+        if (b->joins[j]) cudaEventDestroy(b->joins[j]);
+        if (b->side[j]) cudaStreamDestroy(b->side[j]);
+    }
     if (b->origin) cudaStreamDestroy(b->origin);
-    for (sensai_ctx* c : b->ctx) c->grid_cap = 0;
     delete b;
 }
 
@@ -1080,17 +1297,14 @@ sensai_status sensai_batch_create(sensai_ctx* const* ctxs, int32_t n, sensai_bat
     sensai_batch* b = new (std::nothrow) sensai_batch();
     if (!b) return fail(SENSAI_ENOMEM, "host allocation failed");
     b->ctx.assign(ctxs, ctxs + n);
-    b->streams.assign(n, nullptr);
-    b->joins.assign(n, nullptr);
-    b->launches.assign(n, 0);
     cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {
-        e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming);
-    }
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int j = 0; j < kBatchLanes && e == cudaSuccess; ++j) {
+        e = cudaStreamCreateWithFlags(&b->side[j], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->joins[j], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         sensai_batch_destroy(b);
         return cuda_failure(nullptr, e, "batch resources", __LINE__);

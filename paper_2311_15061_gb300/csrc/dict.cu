@@ -31,14 +31,13 @@ constexpr int kRed = kAtomBlock + kGram;                    // 44 sums per block
 
 // RHO: residual slots in shared memory; LIST: slot -> patch list too.
 template <bool RHO, bool LIST>
-__global__ void __launch_bounds__(kDictThreads, 1) dict_kernel(const DictArgs a)
+__device__ __forceinline__ void dict_body(const DictArgs& a, const int p)
 {
     extern __shared__ float dsm[];
     __shared__ float red[kDictWarps][kRed];
     __shared__ double fin[kRed];
     __shared__ double xi[kDictMaxK];
     __shared__ float s_delta[kAtomBlock];
-    const int p = blockIdx.x;
     const int K = a.g.K, P = a.g.P, KB = a.g.KB;
     const long long Npad = a.g.Npad;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -171,6 +170,22 @@ __global__ void __launch_bounds__(kDictThreads, 1) dict_kernel(const DictArgs a)
 }
 
 template <bool RHO, bool LIST>
+__global__ void __launch_bounds__(kDictThreads, 1) dict_kernel(const DictArgs a)
+{
+    dict_body<RHO, LIST>(a, blockIdx.x);
+}
+
+// Batched instances: CTA b draws chain (b - cta_start[i]) of instance i.
+template <bool RHO, bool LIST>
+__global__ void __launch_bounds__(kDictThreads, 1)
+    dict_multi_kernel(const DictArgs* __restrict__ args, const int* __restrict__ cta_start, int n)
+{
+    int p = 0;
+    const DictArgs& a = *stage_instance_args(args, cta_start, n, &p);
+    dict_body<RHO, LIST>(a, p);
+}
+
+template <bool RHO, bool LIST>
 static cudaError_t launch_mode(const DictArgs& a, size_t smem, cudaStream_t s)
 {
     void* fn = (void*)dict_kernel<RHO, LIST>;
@@ -178,6 +193,35 @@ static cudaError_t launch_mode(const DictArgs& a, size_t smem, cudaStream_t s)
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&a};
     return cudaLaunchKernel(fn, dim3(a.g.P), dim3(kDictThreads), args, smem, s);
+}
+
+// The storage mode for a chain of at most max_slots slots: 2 = residual and
+// patch list in shared memory, 1 = residual only, 0 = global memory; and its
+// dynamic shared memory.
+int dict_mode(int max_slots, size_t* smem)
+{
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return -1;
+    const size_t fixed = sizeof(float) * kDictWarps * kRed + sizeof(double) * (kRed + kDictMaxK) +
+                         sizeof(float) * kAtomBlock + 256;
+    const size_t slots = (size_t)max_slots;
+    if (slots * 8 + fixed <= (size_t)optin) { *smem = slots * 8; return 2; }
+    if (slots * 4 + fixed <= (size_t)optin) { *smem = slots * 4; return 1; }
+    *smem = 0;
+    return 0;
+}
+
+cudaError_t launch_dict_multi(const DictArgs* args, const int* cta_start, int n, int mode, size_t smem, int grid,
+                              cudaStream_t s)
+{
+    void* fn = mode == 2 ? (void*)dict_multi_kernel<true, true>
+             : mode == 1 ? (void*)dict_multi_kernel<true, false> : (void*)dict_multi_kernel<false, false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void* kargs[] = {(void*)&args, (void*)&cta_start, (void*)&n};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kDictThreads), kargs, smem, s);
 }
 
 cudaError_t launch_dict(const DictArgs& a, int max_slots, cudaStream_t s)

@@ -30,11 +30,10 @@ __device__ double sum_partials(const double* v, int n, double* red)
 // popcount of atom k's activity words (fixed-order sum), and the Beta draw's
 // two Gamma draws run on two warps (the value is beta_draw's).  Spreading the
 // atoms over the SMs matters: FP64 throughput per SM is low on this part.
-__global__ void __launch_bounds__(256) pi_kernel(const HyperArgs a)
+__device__ __forceinline__ void pi_body(const HyperArgs& a, const int k)
 {
     __shared__ int red[8];
     __shared__ double g2_s;
-    const int k = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t t_it = launch_t(a.t, a.t_dev, a.sc);
     const uint32_t* z = a.Zb + (long long)k * a.g.NW;
@@ -59,10 +58,15 @@ __global__ void __launch_bounds__(256) pi_kernel(const HyperArgs a)
     }
 }
 
+__global__ void __launch_bounds__(256) pi_kernel(const HyperArgs a)
+{
+    pi_body(a, blockIdx.x);
+}
+
 // gamma_s and gamma_eps from fixed-order FP64 sums of the per-unit partials;
 // the two Gamma draws on two warps.  Last kernel of an iteration: advances the
 // replay iteration index.
-__global__ void __launch_bounds__(kHyperThreads) gamma_kernel(const HyperArgs a)
+__device__ __forceinline__ void gamma_body(const HyperArgs& a)
 {
     __shared__ double red[kHyperThreads / 32];
     __shared__ double ge_s;
@@ -93,6 +97,36 @@ __global__ void __launch_bounds__(kHyperThreads) gamma_kernel(const HyperArgs a)
         a.sc->n_active = (long long)bc[2];
         if (a.t_dev) a.sc->t_iter = t_it + 1u;   // the next replay's iteration
     }
+}
+
+__global__ void __launch_bounds__(kHyperThreads) gamma_kernel(const HyperArgs a)
+{
+    gamma_body(a);
+}
+
+// Batched instances: pi draws with one CTA per (instance, atom), then the
+// gamma draws with one CTA per instance.
+__global__ void __launch_bounds__(256) pi_multi_kernel(const HyperArgs* __restrict__ args,
+                                                       const int* __restrict__ cta_start, int n)
+{
+    int k = 0;
+    const HyperArgs& a = *stage_instance_args(args, cta_start, n, &k);
+    pi_body(a, k);
+}
+
+__global__ void __launch_bounds__(kHyperThreads) gamma_multi_kernel(const HyperArgs* __restrict__ args,
+                                                                    const int* __restrict__ cta_start, int n)
+{
+    const HyperArgs& a = *stage_instance_args(args, cta_start, n);
+    gamma_body(a);
+}
+
+cudaError_t launch_hyper_multi(const HyperArgs* args, const int* pi_start, const int* gamma_start, int n,
+                               int pi_grid, cudaStream_t s)
+{
+    pi_multi_kernel<<<pi_grid, 256, 0, s>>>(args, pi_start, n);
+    gamma_multi_kernel<<<n, kHyperThreads, 0, s>>>(args, gamma_start, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s)

@@ -445,6 +445,35 @@ uint64_t serve_frame_seed(uint64_t seed, int32_t stream_id, uint64_t frame_id);
 // Sets the calling thread's message returned by sensai_last_error().
 void record_error(const char* msg);
 
+// Batched launches: CTA b belongs to instance i with cta_start[i] <= b <
+// cta_start[i + 1].  Copies that instance's arguments into shared memory and
+// returns the copy (valid for the CTA's lifetime); *local (if not null)
+// receives b - cta_start[i].  CTA-uniform; all threads must call it.
+template <class Args>
+__device__ __forceinline__ const Args* stage_instance_args(const Args* args, const int* cta_start, int n,
+                                                           int* local = nullptr)
+{
+    __shared__ __align__(16) unsigned char buf[sizeof(Args)];
+    __shared__ int inst_s, local_s;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cta_start[mid] <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        inst_s = lo;
+        local_s = (int)blockIdx.x - cta_start[lo];
+    }
+    __syncthreads();
+    const int* src = reinterpret_cast<const int*>(args + inst_s);
+    int* dst = reinterpret_cast<int*>(buf);
+    for (int w = threadIdx.x; w < (int)(sizeof(Args) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+    if (local) *local = local_s;
+    __syncthreads();
+    return reinterpret_cast<const Args*>(buf);
+}
+
 // Launchers (defined in the .cu files).
 cudaError_t launch_sweep(const SweepArgs& a, int maxobs, int grid, cudaStream_t s);
 int sweep_block_size();
@@ -452,6 +481,14 @@ int sweep_smem_bytes(const Geom& g);
 int sweep_grid_size(const Geom& g, int maxobs, int device);
 cudaError_t preload_sweep_variants();   // load every code-sweep kernel variant now
 int sweep_lanes(int maxobs);            // lanes per patch for a largest |Omega_i|: 1, or 2 above 96
+int sweep_variant(int maxobs);          // the template capacity serving maxobs (equal: same kernel)
+// Batched code sweeps of instances sharing one variant (resident dictionary).
+cudaError_t launch_sweep_multi(const SweepArgs* args, const int* cta_start, int n, int maxobs, int grid,
+                               size_t smem, cudaStream_t s);
+int sweep_multi_ctas_per_sm(int maxobs, size_t smem);
+cudaError_t launch_sweep_tiled_multi(const SweepArgs* args, const int* cta_start, int n, int maxobs, int grid,
+                                     size_t smem, cudaStream_t s);
+int sweep_tiled_multi_ctas_per_sm(int maxobs, size_t smem);
 cudaError_t preload_tiled_variants();
 
 // How a code sweep runs: the whole dictionary resident in shared memory
@@ -480,6 +517,13 @@ cudaError_t launch_slice_dictionary(const Geom& g, const float* D, float* Dsl, i
 cudaError_t launch_sweep_tiled(const SweepArgs& a, int maxobs, int grid, cudaStream_t s);
 cudaError_t launch_dict(const DictArgs& a, int max_slots, cudaStream_t s);
 cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);   // two kernels: pi draws, then gammas
+// Batched: pi_start is the prefix of K_i (one CTA per atom), gamma_start = 0..n.
+cudaError_t launch_hyper_multi(const HyperArgs* args, const int* pi_start, const int* gamma_start, int n,
+                               int pi_grid, cudaStream_t s);
+// Per-chain dictionary kernels, batched: mode / smem from dict_mode(max slots).
+int dict_mode(int max_slots, size_t* smem);
+cudaError_t launch_dict_multi(const DictArgs* args, const int* cta_start, int n, int mode, size_t smem, int grid,
+                              cudaStream_t s);
 cudaError_t launch_set_iteration(DevScalars* sc, uint32_t t, cudaStream_t s);   // sc->t_iter = t
 // Self-tests of the bounded device waits (each gives up after ~1 s).
 cudaError_t launch_barrier_timeout_selftest(unsigned int* count, int* status, cudaStream_t s);

@@ -33,7 +33,7 @@ constexpr int kSweepThreads = 256;
 constexpr int kSweepWarps = kSweepThreads / 32;
 
 template <int MAXOBS, int LANES>
-__global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 && LANES == 1 ? 2 : 1)) sweep_kernel(const SweepArgs a)
+__device__ __forceinline__ void sweep_body(const SweepArgs& a)
 {
     extern __shared__ float smem[];
     const int K = a.g.K, P = a.g.P, KB = a.g.KB;
@@ -102,6 +102,24 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 && LANES == 1 ? 2
     flush_counts(a, lane, tl);
 }
 
+template <int MAXOBS, int LANES>
+__global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 && LANES == 1 ? 2 : 1)) sweep_kernel(const SweepArgs a)
+{
+    sweep_body<MAXOBS, LANES>(a);
+}
+
+// Batched instances in one launch: CTA b runs instance i with
+// cta_start[i] <= b < cta_start[i + 1] (each instance has its own chunk
+// counter, so its CTAs share its patches dynamically).  The instance's
+// arguments are staged in shared memory.
+template <int MAXOBS, int LANES>
+__global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 && LANES == 1 ? 2 : 1))
+    sweep_multi_kernel(const SweepArgs* __restrict__ args, const int* __restrict__ cta_start, int n)
+{
+    const SweepArgs& a = *stage_instance_args(args, cta_start, n);
+    sweep_body<MAXOBS, LANES>(a);
+}
+
 int sweep_block_size() { return kSweepThreads; }
 
 int sweep_smem_bytes(const Geom& g)
@@ -112,29 +130,59 @@ int sweep_smem_bytes(const Geom& g)
 }
 
 template <int MAXOBS, int LANES = 1>
-static void* kernel_ptr() { return (void*)sweep_kernel<MAXOBS, LANES>; }
+static void* kernel_ptr(bool multi) { return multi ? (void*)sweep_multi_kernel<MAXOBS, LANES> : (void*)sweep_kernel<MAXOBS, LANES>; }
 
 int sweep_lanes(int maxobs) { return maxobs > 96 ? 2 : 1; }
 
-static void* select_kernel(int maxobs)
+static void* select_kernel(int maxobs, bool multi = false)
 {
     if (maxobs > 96) {   // two lanes per patch: per-lane capacity 64 / 96 / 112 / 128
-        if (maxobs <= 128) return kernel_ptr<64, 2>();
-        if (maxobs <= 192) return kernel_ptr<96, 2>();
-        if (maxobs <= 224) return kernel_ptr<112, 2>();
-        if (maxobs <= 256) return kernel_ptr<128, 2>();
+        if (maxobs <= 128) return kernel_ptr<64, 2>(multi);
+        if (maxobs <= 192) return kernel_ptr<96, 2>(multi);
+        if (maxobs <= 224) return kernel_ptr<112, 2>(multi);
+        if (maxobs <= 256) return kernel_ptr<128, 2>(multi);
         return nullptr;
     }
-    if (maxobs <= 8) return kernel_ptr<8>();
-    if (maxobs <= 16) return kernel_ptr<16>();
-    if (maxobs <= 24) return kernel_ptr<24>();
-    if (maxobs <= 32) return kernel_ptr<32>();
-    if (maxobs <= 40) return kernel_ptr<40>();
-    if (maxobs <= 48) return kernel_ptr<48>();
-    if (maxobs <= 64) return kernel_ptr<64>();
-    if (maxobs <= 72) return kernel_ptr<72>();
-    if (maxobs <= 80) return kernel_ptr<80>();
-    return kernel_ptr<96>();
+    if (maxobs <= 8) return kernel_ptr<8>(multi);
+    if (maxobs <= 16) return kernel_ptr<16>(multi);
+    if (maxobs <= 24) return kernel_ptr<24>(multi);
+    if (maxobs <= 32) return kernel_ptr<32>(multi);
+    if (maxobs <= 40) return kernel_ptr<40>(multi);
+    if (maxobs <= 48) return kernel_ptr<48>(multi);
+    if (maxobs <= 64) return kernel_ptr<64>(multi);
+    if (maxobs <= 72) return kernel_ptr<72>(multi);
+    if (maxobs <= 80) return kernel_ptr<80>(multi);
+    return kernel_ptr<96>(multi);
+}
+
+// Variant key: equal keys run the same kernel template.
+int sweep_variant(int maxobs)
+{
+    const int caps[] = {8, 16, 24, 32, 40, 48, 64, 72, 80, 96, 128, 192, 224, 256};
+    for (int c : caps)
+        if (maxobs <= c) return c;
+    return 0;
+}
+
+cudaError_t launch_sweep_multi(const SweepArgs* args, const int* cta_start, int n, int maxobs, int grid,
+                               size_t smem, cudaStream_t s)
+{
+    void* fn = select_kernel(maxobs, true);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void* kargs[] = {(void*)&args, (void*)&cta_start, (void*)&n};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kSweepThreads), kargs, smem, s);
+}
+
+int sweep_multi_ctas_per_sm(int maxobs, size_t smem)
+{
+    void* fn = select_kernel(maxobs, true);
+    int per_sm = 0;
+    if (!fn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSweepThreads, smem) != cudaSuccess)
+        return 0;
+    return per_sm;
 }
 
 // Loads every variant now: with lazy module loading the first launch of a

@@ -109,7 +109,7 @@ __global__ void slice_dictionary_kernel(Geom g, const float* D, float* Dsl, int 
 }
 
 template <int MAXOBS, int LANES>
-__global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 && LANES == 1 ? 2 : 1)) sweep_tiled_kernel(const SweepArgs a)
+__device__ __forceinline__ void tiled_body(const SweepArgs& a)
 {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -232,28 +232,47 @@ __global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 && LANES == 1 ? 2
     flush_counts(a, lane, tl);
 }
 
-template <int MAXOBS, int LANES = 1>
-static void* tiled_ptr() { return (void*)sweep_tiled_kernel<MAXOBS, LANES>; }
+template <int MAXOBS, int LANES>
+__global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 && LANES == 1 ? 2 : 1)) sweep_tiled_kernel(const SweepArgs a)
+{
+    tiled_body<MAXOBS, LANES>(a);
+}
 
-static void* select_tiled(int maxobs)
+// Batched instances in one launch (see sweep_multi_kernel); each instance
+// streams its own dictionary slices.
+template <int MAXOBS, int LANES>
+__global__ void __launch_bounds__(kTiledThreads, (MAXOBS <= 48 && LANES == 1 ? 2 : 1))
+    sweep_tiled_multi_kernel(const SweepArgs* __restrict__ args, const int* __restrict__ cta_start, int n)
+{
+    const SweepArgs& a = *stage_instance_args(args, cta_start, n);
+    tiled_body<MAXOBS, LANES>(a);
+}
+
+template <int MAXOBS, int LANES = 1>
+static void* tiled_ptr(bool multi)
+{
+    return multi ? (void*)sweep_tiled_multi_kernel<MAXOBS, LANES> : (void*)sweep_tiled_kernel<MAXOBS, LANES>;
+}
+
+static void* select_tiled(int maxobs, bool multi = false)
 {
     if (maxobs > 96) {   // two lanes per patch: per-lane capacity 64 / 96 / 112 / 128
-        if (maxobs <= 128) return tiled_ptr<64, 2>();
-        if (maxobs <= 192) return tiled_ptr<96, 2>();
-        if (maxobs <= 224) return tiled_ptr<112, 2>();
-        if (maxobs <= 256) return tiled_ptr<128, 2>();
+        if (maxobs <= 128) return tiled_ptr<64, 2>(multi);
+        if (maxobs <= 192) return tiled_ptr<96, 2>(multi);
+        if (maxobs <= 224) return tiled_ptr<112, 2>(multi);
+        if (maxobs <= 256) return tiled_ptr<128, 2>(multi);
         return nullptr;
     }
-    if (maxobs <= 8) return tiled_ptr<8>();
-    if (maxobs <= 16) return tiled_ptr<16>();
-    if (maxobs <= 24) return tiled_ptr<24>();
-    if (maxobs <= 32) return tiled_ptr<32>();
-    if (maxobs <= 40) return tiled_ptr<40>();
-    if (maxobs <= 48) return tiled_ptr<48>();
-    if (maxobs <= 64) return tiled_ptr<64>();
-    if (maxobs <= 72) return tiled_ptr<72>();
-    if (maxobs <= 80) return tiled_ptr<80>();
-    return tiled_ptr<96>();
+    if (maxobs <= 8) return tiled_ptr<8>(multi);
+    if (maxobs <= 16) return tiled_ptr<16>(multi);
+    if (maxobs <= 24) return tiled_ptr<24>(multi);
+    if (maxobs <= 32) return tiled_ptr<32>(multi);
+    if (maxobs <= 40) return tiled_ptr<40>(multi);
+    if (maxobs <= 48) return tiled_ptr<48>(multi);
+    if (maxobs <= 64) return tiled_ptr<64>(multi);
+    if (maxobs <= 72) return tiled_ptr<72>(multi);
+    if (maxobs <= 80) return tiled_ptr<80>(multi);
+    return tiled_ptr<96>(multi);
 }
 
 cudaError_t preload_tiled_variants()
@@ -325,6 +344,27 @@ int tiled_grid_size(const Geom& g, int maxobs, int KS, int device)
     const long long items = ((long long)g.NW * sweep_lanes(maxobs) + kTiledWarps - 1) / kTiledWarps;
     const long long grid = (long long)per_sm * sms;
     return (int)(grid < items ? grid : items);
+}
+
+cudaError_t launch_sweep_tiled_multi(const SweepArgs* args, const int* cta_start, int n, int maxobs, int grid,
+                                     size_t smem, cudaStream_t s)
+{
+    void* fn = select_tiled(maxobs, true);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void* kargs[] = {(void*)&args, (void*)&cta_start, (void*)&n};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kTiledThreads), kargs, smem, s);
+}
+
+int sweep_tiled_multi_ctas_per_sm(int maxobs, size_t smem)
+{
+    void* fn = select_tiled(maxobs, true);
+    int per_sm = 0;
+    if (!fn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTiledThreads, smem) != cudaSuccess)
+        return 0;
+    return per_sm;
 }
 
 cudaError_t launch_sweep_tiled(const SweepArgs& a, int maxobs, int grid, cudaStream_t s)
