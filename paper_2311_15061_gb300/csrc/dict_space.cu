@@ -45,21 +45,24 @@ constexpr long long kBarrierSpins = 1LL << 24;               // x ~64 ns sleep: 
 
 // Grid barrier on a monotonic arrival counter (zeroed by the host before
 // every launch): barrier number n of the launch waits until the counter reaches
-// (n + 1) * nblocks.  One atomic per CTA and a poll; no reset round trips.
-// Returns false (and sets *status) if it does not complete within the spin
-// limit.
+// (n + 1) * nblocks.  Thread 0 arrives with a release reduction (no round
+// trip) after the block barrier, so the CTA's earlier writes are published
+// (release is cumulative over what the block barrier ordered before it), and
+// polls with acquire loads.  Returns false (and sets *status) if it does not
+// complete within the spin and time limits.
 __device__ bool grid_barrier(unsigned int* count, unsigned int target, int* status)
 {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
-        atomicAdd(count, 1u);
-        volatile unsigned int* vc = count;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
         const unsigned long long t0 = global_ns();
         long long spins = 0;
-        while (*vc < target) {
+        for (;;) {
+            unsigned int v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            if (v >= target) break;
             if (++spins > kBarrierSpins || ((spins & 255) == 0 && global_ns() - t0 > kWaitLimitNs)) {
                 atomicExch(status, (int)SENSAI_ETIMEOUT);
                 ok = 0;
@@ -67,7 +70,6 @@ __device__ bool grid_barrier(unsigned int* count, unsigned int target, int* stat
             }
             __nanosleep(32);
         }
-        __threadfence();
         ok_s = ok;
     }
     __syncthreads();
@@ -182,6 +184,7 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
 {
     extern __shared__ float dyn[];
     __shared__ float dold8[kAtomBlock];
+    __shared__ float gain8[kAtomBlock], noise8[kAtomBlock];
     __shared__ double fin[kDSRed];
     __shared__ double tmp[kDSRed][11];
     __shared__ float r2_s[kDSThreads / 32];
@@ -285,7 +288,6 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
 #pragma unroll
             for (int v = 0; v < kDSRed; ++v) a.part[((size_t)q * ncta + c) * kDSRed + v] = acc[v];
         }
-        __threadfence();
         if (!grid_barrier(a.bar, (unsigned int)(2 * kb + 1) * ncta, &a.sc->status)) return;
 
         // chains c, c + grid, ...: fixed-order FP64 sums of the CTA partials,
@@ -316,9 +318,18 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
                 fin[t] = sum;
             }
             __syncthreads();
+            const float* xo = xis + (size_t)((ch - c) / ncta) * K;
+            if (t < kAtomBlock) {
+                // per atom, in parallel: gamma_eps / Lambda and the noise term Lambda^-1/2 xi
+                const int k = kb * kAtomBlock + t;
+                const float ckk = (float)fin[kAtomBlock + t * (t + 1) / 2 + t];
+                const float prec = (float)P + gef * ckk;
+                gain8[t] = gef / prec;
+                noise8[t] = k < K ? xo[k] * rsqrtf(prec) : 0.0f;
+            }
+            __syncthreads();
             if (t == 0) {
                 // the 8 sequential draws in FP32 on the FP64-reduced sums
-                const float* xo = xis + (size_t)((ch - c) / ncta) * K;
                 float dl[kAtomBlock];
                 for (int kk = 0; kk < kAtomBlock; ++kk) {
                     const int k = kb * kAtomBlock + kk;
@@ -328,8 +339,7 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
                     const float ckk = (float)fin[kAtomBlock + kk * (kk + 1) / 2 + kk];
                     float num = (float)fin[kk] + d_old * ckk;             // sum w_k r^{-k}
                     for (int l = 0; l < kk; ++l) num = fmaf(-dl[l], (float)fin[kAtomBlock + kk * (kk + 1) / 2 + l], num);
-                    const float prec = (float)P + gef * ckk;
-                    const float dnew = gef * num / prec + xo[k] * rsqrtf(prec);
+                    const float dnew = fmaf(gain8[kk], num, noise8[kk]);
                     a.D[(long long)k * P + ch] = dnew;
                     dl[kk] = dnew - d_old;
                 }
@@ -337,7 +347,6 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
             }
             __syncthreads();
         }
-        __threadfence();
         if (!grid_barrier(a.bar, (unsigned int)(2 * kb + 2) * ncta, &a.sc->status)) return;
         if (active) {
 #pragma unroll
