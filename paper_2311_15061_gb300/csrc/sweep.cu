@@ -11,20 +11,23 @@
 //   r_i -= d_k (w_new - w_old) on Omega_i
 // (z with s integrated out, then s | z = 1; inactive weights are not stored).
 //
-// GB300 mapping: one thread owns one patch; a warp owns 32 consecutive,
-// 32-aligned patches so the atom's activity bits of the warp form one 32-bit
-// word (ballot).  Warps pull 32-patch chunks from a global counter, so the
-// tail of the grid is a single chunk per warp.  Weights are read and written
-// in 8-atom blocks (one 256-bit access per lane, 1 KB per warp), the next
-// block prefetched behind the current one, so no global load sits on the
-// per-atom path; per-warp counters replace any block-wide barrier.  The dictionary sits in shared
-// memory as [p][k] with an odd row pitch plus one zero row (p = P) that padded
-// observation slots point at, so the inner loops need no predicates.  The
-// residual of the patch lives in registers (MAXOBS slots, chosen per problem
-// from the largest |Omega_i|).  Patch extraction is fused: the observed
-// pixels are gathered from the frame and the residual rebuilt from the stored
-// weights at the start of each sweep.  At the end the residual is scattered
-// to the per-pixel slot layout the dictionary kernel consumes.
+// GB300 mapping: one thread owns one patch (above 96 observed pixels a lane
+// pair, see sweep_block.cuh); a warp owns 32 consecutive, 32-aligned patches
+// so the atom's activity bits of the warp form one 32-bit word (ballot).
+// Warps pull 32-patch chunks from a global counter, so the tail of the grid is
+// a single chunk per warp.  Weights are read and written in 8-atom blocks (one
+// 256-bit access per lane, 1 KB per warp), the next block prefetched behind
+// the current one, so no global load sits on the per-atom path.  The
+// dictionary sits in shared memory as [p][k] with an odd row pitch plus one
+// zero row (p = P) that padded observation slots point at, so the inner loops
+// need no predicates.  The residual of the patch lives in registers (MAXOBS
+// slots, chosen per problem from the largest |Omega_i|).  Patch extraction is
+// fused: the observed pixels are gathered from the frame and the residual
+// rebuilt from the stored weights at the start of each sweep.  At the end the
+// residual is written, through the position table, into the layout the
+// dictionary kernel consumes.  The per-block code is in sweep_block.cuh,
+// shared with the streamed-dictionary kernel (sweep_tiled.cu); the batched
+// kernel runs the same body on per-instance arguments.
 #include "sweep_block.cuh"
 
 namespace sensai {

@@ -1,8 +1,9 @@
 """GPU tests of batches (sensai_batch_*): many independent contexts learned
 together under one captured CUDA graph.
 
-* A batch of heterogeneous instances (2-D and 3-D, different K, P, masks,
-  strides, one streamed dictionary) ends bit for bit where sensai_learn on
+* A batch of heterogeneous instances (1-D, 2-D and 3-D, different K, P,
+  masks, strides, one streamed dictionary, one with two lanes per patch)
+  ends bit for bit where sensai_learn on
   each instance alone ends: codes, dictionary, pi, gammas and reconstruction.
 * Repeated replays advance the iteration index (3 + 2 batch iterations equal
   5 single ones), and tuning, whose trials are real iterations with narrower
@@ -24,6 +25,7 @@ CASES = [
     dict(M=(48, 48), B=(16, 16), S=(1, 1), K=256, frac=0.1, seed=3),   # streamed dictionary
     dict(M=(128, 96), B=(8, 8), S=(1, 1), K=64, frac=0.05, seed=4),
     dict(M=(333,), B=(9,), S=(2,), K=8, frac=0.4, seed=5),
+    dict(M=(40, 40), B=(12, 12), S=(1, 1), K=16, frac=1.0, seed=6),   # |Omega_i| = 144: two lanes per patch
 ]
 
 

@@ -10,6 +10,9 @@
 * Memory-based admission: a budget that fits one large frame at a time still
   completes every frame with the same results; a frame larger than the engine
   accepts is rejected with EINVAL.
+* A dictionary too large for shared memory (K = 256 atoms of 16x16 pixels)
+  is streamed in slices when serving too, with the same results as
+  sensai_inpaint.
 """
 import threading
 
@@ -139,3 +142,26 @@ def test_memory_admission_and_rejection(learned):
     ctx.sensai_serve_stop()
     for key in free:
         np.testing.assert_array_equal(free[key], tight[key])
+
+
+def test_serving_with_streamed_dictionary():
+    from paper_2311_15061_gb300 import sensai, synth
+    M, B, K = (48, 48), (16, 16), 256
+    x, clean = synth.stem_frame(M, 3)
+    mask = synth.random_mask(M, 0.15, 3)
+    ctx = sensai.Context(sensai.make_params(M, B, (1, 1), K, seed=5), mask)
+    ctx.sensai_learn(x, 2)
+    assert ctx.sensai_get_stats().slices >= 2
+    st = ctx.sensai_get_state()
+    ctx.sensai_serve_start(slots=2, max_pixels=64 * 64, max_observed=96)
+    frames = [(synth.stem_frame((56, 52), 10 + j)[0], synth.random_mask((56, 52), 0.12, 10 + j)) for j in range(3)]
+    served = _serve(ctx, [(2, j, fx, fm) for j, (fx, fm) in enumerate(frames)])
+    ctx.sensai_serve_stop()
+    for j, (fx, fm) in enumerate(frames):
+        p = sensai.make_params((56, 52), B, (1, 1), K, seed=_frame_seed(5, 2, j))
+        c2 = sensai.Context(p, fm)
+        c2.sensai_set_state(D=st["D"], pi=st["pi"], gamma_s=st["gamma_s"], gamma_eps=st["gamma_eps"], iter=st["iter"])
+        ref = np.empty((56, 52), np.float32)
+        c2.sensai_inpaint(fx, 3, ref)
+        c2.close()
+        np.testing.assert_array_equal(served[(2, j)], ref)
