@@ -241,7 +241,6 @@ SweepArgs sweep_args(const sensai_ctx* ctx)
     a.sc = ctx->sc;
     a.pos = ctx->pos;
     a.R = ctx->R;
-    a.m = ctx->m;
     a.part_s2 = ctx->part_s2;
     a.part_r2 = ctx->part_r2;
     a.chunk_counter = ctx->chunk_counter;

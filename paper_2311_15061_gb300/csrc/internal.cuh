@@ -330,7 +330,6 @@ struct SweepArgs {
     const int* pos;            // [maxobs][N] residual position of observed pixel j of patch i
     float* R;                  // residual in the dictionary step's layout, R[pos[j][i]]
                                // (null: inpainting only, the residual is not kept)
-    int* m;                    // [K] active count per atom (written by the pi draws)
     double* part_s2;           // [NW] per 32-patch chunk
     double* part_r2;           // [NW] per 32-patch chunk
     unsigned int* chunk_counter;  // work counter, zeroed before each launch

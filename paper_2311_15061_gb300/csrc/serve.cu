@@ -286,7 +286,6 @@ static sensai_status process_frame(ServeEngine* e, ServeSlot* sl, const ServeReq
         a.lpi = sl->lpi;
         a.sc = sl->sc;
         a.R = nullptr;   // inpainting keeps no per-pixel residual
-        a.m = sl->m;
         a.part_s2 = sl->part_s2;
         a.part_r2 = sl->part_r2;
         a.chunk_counter = sl->counter;
