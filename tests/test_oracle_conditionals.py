@@ -179,3 +179,35 @@ def test_pi_and_precision_conditionals():
     ge_law = stats.gamma(prm.e + 0.5 * Om.sum(), scale=1 / (prm.f + 0.5 * np.sum(R ** 2)))
     assert stats.kstest(gss, gs_law.cdf).pvalue > 1e-3
     assert stats.kstest(ges, ge_law.cdf).pvalue > 1e-3
+
+
+def test_consecutive_code_draws_are_independent():
+    """With two atoms orthogonal on the observed pixels and both (almost)
+    always active, s_0 and s_1 are independent with the single-atom
+    posteriors N(ge d_k.x / lam_k, 1 / lam_k), lam_k = gs + ge |d_k|^2: their
+    correlation must vanish (random words shared between the two draws would
+    correlate them) and each must have its posterior moments."""
+    M, B, S, K = (3, 3), (3, 3), (1, 1), 2
+    prm = O.params(M, B, S, K, seed=21)
+    rng = np.random.default_rng(21)
+    x = rng.standard_normal(M).astype(np.float32)
+    mask = np.ones(M, np.uint8)
+    D = np.zeros((K, 9))
+    D[0, :3] = 1.0 / np.sqrt(3.0)
+    D[1, 3], D[1, 4] = 1.0 / np.sqrt(2.0), -1.0 / np.sqrt(2.0)
+    gs, ge = 2.0, 3.0
+    st = O.State(prm, D=D, pi=[0.999999, 0.999999], gamma_s=gs, gamma_eps=ge)
+    T = 30000
+    s = np.zeros((T, K))
+    for t in range(T):
+        st.t = t
+        O.zs_sweep(st, x, mask)
+        s[t] = st.S[0]
+    assert np.all(st.Z[0] == 1)
+    xo = x.reshape(-1).astype(np.float64)
+    for k in range(K):
+        lam = gs + ge * np.dot(D[k], D[k])
+        mean, var = ge * np.dot(D[k], xo) / lam, 1.0 / lam
+        assert abs(s[:, k].mean() - mean) < 5 * np.sqrt(var / T)
+        assert abs(s[:, k].var() / var - 1) < 5 * np.sqrt(2.0 / T)
+    assert abs(np.corrcoef(s[:, 0], s[:, 1])[0, 1]) < 5 / np.sqrt(T)
