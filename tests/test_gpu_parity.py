@@ -9,7 +9,8 @@ with the tolerances stated in parity_helpers:
 * the 128x128, K=64 workload in full, several tiles and a ragged tail;
 * the 512x512, K=128 benchmark workload: the code sweep on sampled patches
   (the oracle sweeps those patches with their own Philox counters), the
-  dictionary and hyper-parameter draws in full;
+  dictionary and hyper-parameter draws in full; the 3-D video workload at
+  full size (streamed dictionary): the code sweep on sampled patches;
 * edge cases: ragged patch counts, 1-D and 3-D frames with strides, K = 1,
   full masks, an empty mask, determinism;
 * the streamed code sweep (dictionary in atom slices through shared memory):
@@ -362,3 +363,29 @@ def test_two_lanes_per_patch(case):
 
 def test_two_lanes_streamed():
     _phase_parity(M=(12, 12, 64), B=(4, 4, 32), S=(1, 1, 32), K=32, frac=0.3, warm=1, flags=_stream(16), slices=2)
+
+
+def test_full_size_streamed_sweep_sampled_video():
+    """The 3-D video workload at full size (32x256x256, 4x8x8 patches at
+    stride (2, 1, 1): N = 930,015, P = 256, K = 256), in the launch
+    configuration the bench times (dictionary streamed in slices): one code
+    sweep from the prior on the GPU, the oracle on 400 sampled patches."""
+    M, B, S, K = (32, 256, 256), (4, 8, 8), (2, 1, 1), 256
+    prm, x, clean, mask = problem(M, B, S, K, 0.15, seed=0)
+    st = O.State(prm)                       # prior dictionary, all codes 0
+    st.D = st.D.astype(np.float32).astype(np.float64)
+    st.gamma_eps = O.init_gamma_eps(prm, x, mask)
+    ctx = gpu_context(prm, mask)
+    ctx.sensai_set_frame(np.ascontiguousarray(x, np.float32))
+    ctx.sensai_set_state(D=st.D.astype(np.float32), pi=st.pi, gamma_s=st.gamma_s, gamma_eps=st.gamma_eps, iter=0)
+    assert ctx.sensai_get_stats().slices >= 2
+    ctx.sensai_sweep_codes()
+    g = ctx.sensai_get_state()
+    ctx.close()
+    rng = np.random.default_rng(1)
+    N = st.Z.shape[0]
+    sample = np.unique(np.concatenate([rng.choice(N, 400, replace=False), [0, N - 1]]))
+    _, L = O.zs_sweep_subset(st, x, mask, patches=sample, want_logodds=True)   # st keeps prm and t
+    nflip, serr = compare_codes(st, g, st, L, patches=sample)
+    assert nflip <= 3
+    assert serr <= S_TOL
