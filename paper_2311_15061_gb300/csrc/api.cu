@@ -83,6 +83,7 @@ struct sensai_ctx {
     int* m = nullptr;
     double* part_s2 = nullptr;
     double* part_r2 = nullptr;
+    double* ge_part = nullptr;  // scratch of the initial gamma_eps
     unsigned int* chunk_counter = nullptr;
     DevScalars* sc = nullptr;
     int* pos = nullptr;         // [maxobs][N] residual position of each observed pixel of each patch
@@ -128,7 +129,7 @@ void free_all(sensai_ctx* c)
 {
     void* ptrs[] = {c->mask_bits, c->imgoff, c->nobs, c->obs, c->Ibits, c->Ipre, c->Icnt, c->Rbase, c->Ilist,
                     c->misc, c->x, c->D, c->W, c->Zb, c->R, c->Y, c->out, c->pi, c->lpi, c->m,
-                    c->part_s2, c->part_r2, c->chunk_counter, c->sc, c->pos, c->Dsl};
+                    c->part_s2, c->part_r2, c->chunk_counter, c->sc, c->pos, c->Dsl, c->ge_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ds_free(&c->ds);
@@ -199,8 +200,8 @@ sensai_status copy_frame(sensai_ctx* ctx, const float* frame, cudaStream_t s)
 sensai_status ensure_gamma_eps(sensai_ctx* ctx, cudaStream_t s)
 {
     if (ctx->ge_set) return SENSAI_OK;
-    SENSAI_CUDA(ctx, launch_init_gamma_eps(ctx->g, ctx->x, ctx->mask_bits, ctx->sc, s));
-    ctx->launches += 1;
+    SENSAI_CUDA(ctx, launch_init_gamma_eps(ctx->g, ctx->x, ctx->mask_bits, ctx->sc, ctx->ge_part, s));
+    ctx->launches += 2;
     ctx->ge_set = true;
     return SENSAI_OK;
 }
@@ -541,6 +542,7 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
         CREATE_CUDA(dalloc(&ctx->part_r2, n));
     }
     CREATE_CUDA(dalloc(&ctx->chunk_counter, 1));
+    CREATE_CUDA(dalloc(&ctx->ge_part, (size_t)kInitGammaEpsScratch));
     CREATE_CUDA(dalloc(&ctx->sc, 1));
     {
         const bool stream = (p.flags & SENSAI_FLAG_STREAM_DICTIONARY) != 0;

@@ -176,35 +176,77 @@ __global__ void init_scalars_kernel(int K, double* pi, float* lpi, DevScalars* s
 }
 
 // gamma_eps = 1 / max(var(frame over sampled pixels), 1e-12), two passes.
-__global__ void __launch_bounds__(kHyperThreads) init_gamma_eps_kernel(long long nframe, const float* x,
-                                                                       const uint32_t* mbits, DevScalars* sc)
+// Initial noise precision 1 / var(observed pixels), in two kernels: per CTA
+// (a range of mask words, visiting only the observed bits) the count, the sum
+// and the sum of squared deviations from the CTA's own mean, in FP64; then
+// one thread merges the partials in a fixed order with the parallel variance
+// formula M2 = sum_c (M2_c + n_c (mean_c - mean)^2).
+constexpr int kGeParts = kInitGammaEpsScratch / 3;
+
+__global__ void __launch_bounds__(256) gamma_eps_parts_kernel(long long nframe, const float* x,
+                                                              const uint32_t* mbits, double* part)
 {
-    __shared__ double red[kHyperThreads / 32];
+    __shared__ double red[8];
     __shared__ double s_mean;
+    const long long nmw = (nframe + 31) / 32;
+    const long long w0 = nmw * blockIdx.x / gridDim.x, w1 = nmw * (blockIdx.x + 1) / gridDim.x;
+    const uint32_t tail = (nframe & 31) ? (1u << (nframe & 31)) - 1u : 0xffffffffu;
     double sum = 0.0, cnt = 0.0;
-    for (long long u = threadIdx.x; u < nframe; u += blockDim.x)
-        if ((mbits[u >> 5] >> (u & 31)) & 1u) {
-            sum += x[u];
-            cnt += 1.0;
+    for (long long w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
+        uint32_t bits = mbits[w] & (w == nmw - 1 ? tail : 0xffffffffu);
+        cnt += (double)__popc(bits);
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            sum += (double)x[w * 32 + b];
+            bits &= bits - 1u;
         }
+    }
     sum = block_sum(sum, red);
     cnt = block_sum(cnt, red);
     if (threadIdx.x == 0) s_mean = cnt > 0.0 ? sum / cnt : 0.0;
     __syncthreads();
     const double mean = s_mean;
     double ss = 0.0;
-    for (long long u = threadIdx.x; u < nframe; u += blockDim.x)
-        if ((mbits[u >> 5] >> (u & 31)) & 1u) {
-            const double dv = (double)x[u] - mean;
+    for (long long w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
+        uint32_t bits = mbits[w] & (w == nmw - 1 ? tail : 0xffffffffu);
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            const double dv = (double)x[w * 32 + b] - mean;
             ss += dv * dv;
+            bits &= bits - 1u;
         }
+    }
     ss = block_sum(ss, red);
     if (threadIdx.x == 0) {
-        double var = cnt > 0.0 ? ss / cnt : 1.0;
-        if (var < 1e-12) var = 1e-12;
-        sc->gamma_eps = 1.0 / var;
-        sc->ge_set = 1;
+        part[3 * blockIdx.x + 0] = cnt;
+        part[3 * blockIdx.x + 1] = sum;
+        part[3 * blockIdx.x + 2] = ss;
     }
+}
+
+__global__ void gamma_eps_merge_kernel(const double* part, int nparts, DevScalars* sc)
+{
+    if (threadIdx.x != 0) return;
+    double n = 0.0, total = 0.0;
+    for (int c = 0; c < nparts; ++c) {
+        n += part[3 * c];
+        total += part[3 * c + 1];
+    }
+    double var = 1.0;
+    if (n > 0.0) {
+        const double mean = total / n;
+        double m2 = 0.0;
+        for (int c = 0; c < nparts; ++c) {
+            const double nc = part[3 * c];
+            if (nc <= 0.0) continue;
+            const double dm = part[3 * c + 1] / nc - mean;
+            m2 += part[3 * c + 2] + nc * dm * dm;
+        }
+        var = m2 / n;
+    }
+    if (var < 1e-12) var = 1e-12;
+    sc->gamma_eps = 1.0 / var;
+    sc->ge_set = 1;
 }
 
 // Statistics of an arbitrary state (after set_state / set_dictionary): active
@@ -275,9 +317,10 @@ cudaError_t launch_init_state(const Geom& g, float* D, double* pi, float* lpi, D
 }
 
 cudaError_t launch_init_gamma_eps(const Geom& g, const float* x, const uint32_t* mbits, DevScalars* sc,
-                                  cudaStream_t s)
+                                  double* scratch, cudaStream_t s)
 {
-    init_gamma_eps_kernel<<<1, kHyperThreads, 0, s>>>(g.nframe, x, mbits, sc);
+    gamma_eps_parts_kernel<<<kGeParts, 256, 0, s>>>(g.nframe, x, mbits, scratch);
+    gamma_eps_merge_kernel<<<1, 32, 0, s>>>(scratch, kGeParts, sc);
     return cudaGetLastError();
 }
 

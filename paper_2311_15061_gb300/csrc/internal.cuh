@@ -548,8 +548,10 @@ cudaError_t launch_reconstruct(const Geom& g, const float* D, const float* W, co
                                float* out, cudaStream_t s);
 cudaError_t launch_init_state(const Geom& g, float* D, double* pi, float* lpi, DevScalars* sc,
                               unsigned long long seed, cudaStream_t s);
+// scratch: kInitGammaEpsScratch doubles.
+constexpr int kInitGammaEpsScratch = 3 * 256;
 cudaError_t launch_init_gamma_eps(const Geom& g, const float* x, const uint32_t* mbits, DevScalars* sc,
-                                  cudaStream_t s);
+                                  double* scratch, cudaStream_t s);
 cudaError_t launch_code_stats(const Geom& g, const float* W, const uint32_t* Zb, int* m, double* part_s2,
                               cudaStream_t s);
 cudaError_t launch_residual(const Geom& g, const float* x, const uint16_t* obs, const uint16_t* nobs,
