@@ -161,6 +161,20 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(x, world):
+    """The largest value of x over all ranks (the whole-job time is the slowest
+    rank's); x itself when there is one rank.  Works with nccl (CUDA tensor)
+    and gloo (CPU tensor)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_gpu(args):
     import torch
     world, rank, local = _dist()
@@ -226,11 +240,7 @@ def run_gpu(args):
     prof = ctx.sensai_profile_read()
     ctx.sensai_profile(0)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world)
     updates = float(N) * K * iters * args.steps * world
     value = updates / (total_ms / 1e3)
 
