@@ -77,6 +77,7 @@ struct sensai_ctx {
     uint32_t* Zb = nullptr;
     float* R = nullptr;
     float* Y = nullptr;         // per-patch reconstructions, P x N
+    float* Dc = nullptr;        // dictionary operands of the tensor-core reconstruction
     float* out = nullptr;       // frame-sized staging buffer
     double* pi = nullptr;
     float* lpi = nullptr;
@@ -129,7 +130,7 @@ void free_all(sensai_ctx* c)
 {
     void* ptrs[] = {c->mask_bits, c->imgoff, c->nobs, c->obs, c->Ibits, c->Ipre, c->Icnt, c->Rbase, c->Ilist,
                     c->misc, c->x, c->D, c->W, c->Zb, c->R, c->Y, c->out, c->pi, c->lpi, c->m,
-                    c->part_s2, c->part_r2, c->chunk_counter, c->sc, c->pos, c->Dsl, c->ge_part};
+                    c->part_s2, c->part_r2, c->chunk_counter, c->sc, c->pos, c->Dsl, c->ge_part, c->Dc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ds_free(&c->ds);
@@ -530,6 +531,7 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     CREATE_CUDA(dalloc(&ctx->W, (size_t)g.KB * kAtomBlock * g.Npad));
     CREATE_CUDA(dalloc(&ctx->Zb, (size_t)g.K * g.NW));
     CREATE_CUDA(dalloc(&ctx->Y, (size_t)P * N));
+    if (recon_tc_available(ctx->g)) CREATE_CUDA(dalloc(&ctx->Dc, recon_tc_operand_floats(ctx->g)));
     CREATE_CUDA(dalloc(&ctx->pi, (size_t)g.K));
     CREATE_CUDA(dalloc(&ctx->lpi, (size_t)g.K));
     CREATE_CUDA(dalloc(&ctx->m, (size_t)g.K));
@@ -654,9 +656,9 @@ sensai_status sensai_inpaint(sensai_ctx* ctx, const float* frame, int32_t sweeps
     float* dst = dev ? out : ctx->out;
     {
         PhaseTimer timer(ctx, kPhaseRecon, s);
-        SENSAI_CUDA(ctx, launch_reconstruct(ctx->g, ctx->D, ctx->W, ctx->Zb, ctx->Y, dst, s));
+        SENSAI_CUDA(ctx, launch_reconstruct(ctx->g, ctx->D, ctx->Dc, ctx->W, ctx->Y, dst, &ctx->sc->status, s));
         timer.stop();
-        ctx->launches += 2;
+        ctx->launches += reconstruct_launches(ctx->g);
     }
     if (!dev) return write_out(ctx, ctx->out, out, sizeof(float) * (size_t)ctx->g.nframe, s);
     return SENSAI_OK;
@@ -673,9 +675,9 @@ sensai_status sensai_reconstruct(sensai_ctx* ctx, float* out, void* stream)
     float* dst = dev ? out : ctx->out;
     {
         PhaseTimer timer(ctx, kPhaseRecon, s);
-        SENSAI_CUDA(ctx, launch_reconstruct(ctx->g, ctx->D, ctx->W, ctx->Zb, ctx->Y, dst, s));
+        SENSAI_CUDA(ctx, launch_reconstruct(ctx->g, ctx->D, ctx->Dc, ctx->W, ctx->Y, dst, &ctx->sc->status, s));
         timer.stop();
-        ctx->launches += 2;
+        ctx->launches += reconstruct_launches(ctx->g);
     }
     if (!dev) return write_out(ctx, ctx->out, out, sizeof(float) * (size_t)ctx->g.nframe, s);
     return SENSAI_OK;

@@ -173,42 +173,71 @@ __global__ void overlap_counts_kernel(Geom g, int* counts)
 
 // Overlap-add, gather form: pixel q averages Y[p][i] over the patches i that
 // cover it, with p = q - origin(i).  Y holds every patch's reconstruction.
+// The covering patches are visited in row-major order, eight addresses at a
+// time, so that eight independent loads are in flight per thread; the sum
+// takes them in that order.  NDIM is the frame's dimension count, so that
+// the per-dimension state stays in registers.
+constexpr int kGatherBatch = 8;
+
+template <int NDIM>
 __global__ void ola_gather_kernel(Geom g, const float* Y, float* out)
 {
     const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= g.nframe) return;
-    long long y[kMaxDim], f[kMaxDim], l[kMaxDim], cur[kMaxDim];
+    long long y[NDIM], f[NDIM], l[NDIM], cur[NDIM];
     long long rem = u;
-    for (int d = g.ndim - 1; d >= 0; --d) {
+    bool empty = false;
+#pragma unroll
+    for (int d = NDIM - 1; d >= 0; --d) {
         y[d] = rem % g.M[d];
         rem /= g.M[d];
         cover_range(g, d, y[d], &f[d], &l[d]);
-        if (l[d] < f[d]) {
-            out[u] = 0.0f;
-            return;
-        }
+        empty = empty || l[d] < f[d];
         cur[d] = f[d];
+    }
+    if (empty) {
+        out[u] = 0.0f;
+        return;
     }
     float acc = 0.0f;
     int count = 0;
-    for (;;) {
-        long long i = 0;
-        int p = 0;
-        for (int d = 0; d < g.ndim; ++d) {
-            i = i * g.G[d] + cur[d];
-            p = p * g.B[d] + (int)(y[d] - cur[d] * g.S[d]);
+    bool more = true;
+    while (more) {
+        long long at[kGatherBatch];
+#pragma unroll
+        for (int j = 0; j < kGatherBatch; ++j) {
+            at[j] = -1;
+            if (!more) continue;
+            long long i = 0;
+            int p = 0;
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) {
+                i = i * g.G[d] + cur[d];
+                p = p * g.B[d] + (int)(y[d] - cur[d] * g.S[d]);
+            }
+            at[j] = (long long)p * g.N + i;
+            ++count;
+            bool carry = true;   // odometer step, last dimension fastest
+#pragma unroll
+            for (int d = NDIM - 1; d >= 0; --d) {
+                if (carry) {
+                    if (++cur[d] > l[d]) cur[d] = f[d];
+                    else carry = false;
+                }
+            }
+            more = !carry;
         }
-        acc += Y[(long long)p * g.N + i];
-        ++count;
-        int d = g.ndim - 1;
-        while (d >= 0 && ++cur[d] > l[d]) {
-            cur[d] = f[d];
-            --d;
-        }
-        if (d < 0) break;
+        float v[kGatherBatch];
+#pragma unroll
+        for (int j = 0; j < kGatherBatch; ++j) v[j] = at[j] >= 0 ? __ldg(Y + at[j]) : 0.0f;
+#pragma unroll
+        for (int j = 0; j < kGatherBatch; ++j)
+            if (at[j] >= 0) acc += v[j];
     }
     out[u] = acc / (float)count;
 }
+
+static cudaError_t launch_ola_gather(const Geom& g, const float* Y, float* out, cudaStream_t s);
 
 // Residual position of observed pixel j of patch i in the per-pixel slot
 // layout: slot Rbase[p] + rank of i among the patches observing p.
@@ -242,7 +271,8 @@ __global__ void ilist_kernel(Geom g, const uint32_t* Ibits, const uint32_t* Ipre
     }
 }
 
-// Per-patch reconstruction Y[p][i] = sum_k z_ik w_ik d_kp.  One thread per
+// Per-patch reconstruction Y[p][i] = sum_k z_ik w_ik d_kp on the FP32 ALUs, for
+// patches of more than 256 pixels (the tensor-core form covers the rest).  One thread per
 // patch, 32 pixels at a time; the dictionary chunk is read with warp-uniform
 // (broadcast) shared-memory loads.
 __global__ void __launch_bounds__(256) patch_recon_kernel(Geom g, const float* D, const float* W, float* Y)
@@ -339,15 +369,36 @@ cudaError_t launch_overlap_counts(const Geom& g, int* counts, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_reconstruct(const Geom& g, const float* D, const float* W, const uint32_t* Zb, float* Y,
-                               float* out, cudaStream_t s)
+cudaError_t launch_recon_alu(const Geom& g, const float* D, const float* W, float* Y, cudaStream_t s)
 {
-    (void)Zb;
     const int smem = (int)(sizeof(float) * (size_t)g.KB * kAtomBlock * 32);
     cudaError_t e = cudaFuncSetAttribute((void*)patch_recon_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     patch_recon_kernel<<<blocks_for(g.NW, 8), 256, smem, s>>>(g, D, W, Y);
-    ola_gather_kernel<<<blocks_for(g.nframe, 256), 256, 0, s>>>(g, Y, out);
+    return cudaGetLastError();
+}
+
+int reconstruct_launches(const Geom& g) { return recon_tc_available(g) ? 3 : 2; }
+
+cudaError_t launch_reconstruct(const Geom& g, const float* D, float* Dc, const float* W, float* Y, float* out,
+                               int* status, cudaStream_t s)
+{
+    cudaError_t e = recon_tc_available(g) ? launch_recon_tc(g, D, Dc, W, Y, status, s)
+                                          : launch_recon_alu(g, D, W, Y, s);
+    if (e != cudaSuccess) return e;
+    return launch_ola_gather(g, Y, out, s);
+}
+
+static cudaError_t launch_ola_gather(const Geom& g, const float* Y, float* out, cudaStream_t s)
+{
+    const unsigned int blocks = blocks_for(g.nframe, 256);
+    switch (g.ndim) {
+    case 1: ola_gather_kernel<1><<<blocks, 256, 0, s>>>(g, Y, out); break;
+    case 2: ola_gather_kernel<2><<<blocks, 256, 0, s>>>(g, Y, out); break;
+    case 3: ola_gather_kernel<3><<<blocks, 256, 0, s>>>(g, Y, out); break;
+    case 4: ola_gather_kernel<4><<<blocks, 256, 0, s>>>(g, Y, out); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -544,8 +544,19 @@ cudaError_t launch_slots(const Geom& g, const uint32_t* mask_bits, const int* im
 cudaError_t launch_ilist(const Geom& g, const uint32_t* Ibits, const uint32_t* Ipre, const int* Rbase, int* Ilist,
                          cudaStream_t s);
 cudaError_t launch_overlap_counts(const Geom& g, int* counts, cudaStream_t s);
-cudaError_t launch_reconstruct(const Geom& g, const float* D, const float* W, const uint32_t* Zb, float* Y,
-                               float* out, cudaStream_t s);
+// Per-patch reconstructions Y = W D (tensor cores for P <= 256, with Dc the
+// recon_tc_operand_floats(g) scratch for their dictionary operands; else the
+// FP32 ALU kernel) and the overlap-add gather into out; a device-side wait
+// that gives up sets SENSAI_ETIMEOUT in *status.  reconstruct_launches(g)
+// kernels.
+cudaError_t launch_reconstruct(const Geom& g, const float* D, float* Dc, const float* W, float* Y, float* out,
+                               int* status, cudaStream_t s);
+int reconstruct_launches(const Geom& g);
+bool recon_tc_available(const Geom& g);
+size_t recon_tc_operand_floats(const Geom& g);   // 0 if the tensor-core form does not apply
+cudaError_t launch_recon_tc(const Geom& g, const float* D, float* Dc, const float* W, float* Y, int* status,
+                            cudaStream_t s);
+cudaError_t launch_recon_alu(const Geom& g, const float* D, const float* W, float* Y, cudaStream_t s);
 cudaError_t launch_init_state(const Geom& g, float* D, double* pi, float* lpi, DevScalars* sc,
                               unsigned long long seed, cudaStream_t s);
 // scratch: kInitGammaEpsScratch doubles.

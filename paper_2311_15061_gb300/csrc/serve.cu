@@ -78,6 +78,7 @@ struct ServeSlot {
     double* pi = nullptr;
     float* lpi = nullptr;
     float* Y = nullptr;
+    float* Dc = nullptr;                 // dictionary operands of the tensor-core reconstruction
     float* out = nullptr;
     float* Dsl = nullptr;                // dictionary slices (streamed code sweep)
     int* h_misc = nullptr;               // pinned readback
@@ -158,7 +159,7 @@ namespace sensai {
 static void free_slot(ServeSlot* s)
 {
     void* dev[] = {s->x, s->mask_bytes, s->mask_bits, s->imgoff, s->nobs, s->obs, s->misc, s->total, s->W, s->Zb,
-                   s->m, s->part_s2, s->part_r2, s->counter, s->sc, s->pi, s->lpi, s->Y, s->out, s->Dsl};
+                   s->m, s->part_s2, s->part_r2, s->counter, s->sc, s->pi, s->lpi, s->Y, s->out, s->Dsl, s->Dc};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (s->h_misc) cudaFreeHost(s->h_misc);
@@ -205,6 +206,7 @@ static cudaError_t alloc_slot(ServeEngine* e, ServeSlot* s)
     SLOT_TRY(slot_alloc(&s->pi, (size_t)b.K));
     SLOT_TRY(slot_alloc(&s->lpi, (size_t)b.K));
     SLOT_TRY(slot_alloc(&s->Y, (size_t)b.P * px));
+    if (recon_tc_available(b)) SLOT_TRY(slot_alloc(&s->Dc, recon_tc_operand_floats(b)));
     SLOT_TRY(slot_alloc(&s->Dsl, (size_t)slice_capacity_floats(b)));
     SLOT_TRY(cudaMallocHost((void**)&s->h_misc, 2 * sizeof(int)));
     SLOT_TRY(cudaMallocHost((void**)&s->h_total, sizeof(unsigned long long)));
@@ -315,10 +317,15 @@ static sensai_status process_frame(ServeEngine* e, ServeSlot* sl, const ServeReq
         h.t = e->t0 + (uint32_t)sw;
         FRAME_TRY(launch_hyper(h, s));
     }
-    FRAME_TRY(launch_reconstruct(g, e->D, sl->W, sl->Zb, sl->Y, sl->out, s));
+    FRAME_TRY(launch_reconstruct(g, e->D, sl->Dc, sl->W, sl->Y, sl->out, &sl->sc->status, s));
     FRAME_TRY(cudaMemcpyAsync(q.out, sl->out, sizeof(float) * (size_t)g.nframe, cudaMemcpyDeviceToHost, s));
+    FRAME_TRY(cudaMemcpyAsync(sl->h_misc + 1, &sl->sc->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     FRAME_TRY(cudaStreamSynchronize(s));
 #undef FRAME_TRY
+    if (sl->h_misc[1] != 0) {
+        note_error(e, SENSAI_ETIMEOUT, "a device-side wait timed out", "frame kernels");
+        return SENSAI_ETIMEOUT;
+    }
     return SENSAI_OK;
 }
 
