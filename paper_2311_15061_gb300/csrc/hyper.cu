@@ -179,8 +179,10 @@ __global__ void init_scalars_kernel(int K, double* pi, float* lpi, DevScalars* s
 // Initial noise precision 1 / var(observed pixels), in two kernels: per CTA
 // (a range of mask words, visiting only the observed bits) the count, the sum
 // and the sum of squared deviations from the CTA's own mean, in FP64; then
-// one thread merges the partials in a fixed order with the parallel variance
-// formula M2 = sum_c (M2_c + n_c (mean_c - mean)^2).
+// one CTA merges the partials pairwise in a fixed binary tree with the
+// parallel variance update (n, mean, M2) + (n', mean', M2') -> (n + n',
+// mean + d n' / (n + n'), M2 + M2' + d^2 n n' / (n + n')), d = mean' - mean,
+// so the result does not depend on scheduling.
 constexpr int kGeParts = kInitGammaEpsScratch / 3;
 
 __global__ void __launch_bounds__(256) gamma_eps_parts_kernel(long long nframe, const float* x,
@@ -224,29 +226,46 @@ __global__ void __launch_bounds__(256) gamma_eps_parts_kernel(long long nframe, 
     }
 }
 
-__global__ void gamma_eps_merge_kernel(const double* part, int nparts, DevScalars* sc)
+__global__ void __launch_bounds__(kGeParts) gamma_eps_merge_kernel(const double* part, int nparts, DevScalars* sc)
 {
-    if (threadIdx.x != 0) return;
-    double n = 0.0, total = 0.0;
-    for (int c = 0; c < nparts; ++c) {
-        n += part[3 * c];
-        total += part[3 * c + 1];
-    }
-    double var = 1.0;
-    if (n > 0.0) {
-        const double mean = total / n;
-        double m2 = 0.0;
-        for (int c = 0; c < nparts; ++c) {
-            const double nc = part[3 * c];
-            if (nc <= 0.0) continue;
-            const double dm = part[3 * c + 1] / nc - mean;
-            m2 += part[3 * c + 2] + nc * dm * dm;
+    __shared__ double sn[kGeParts], smu[kGeParts], sm2[kGeParts];
+    const int t = threadIdx.x;
+    double n = 0.0, mu = 0.0, m2 = 0.0;
+    if (t < nparts) {
+        n = part[3 * t];
+        if (n > 0.0) {
+            mu = part[3 * t + 1] / n;
+            m2 = part[3 * t + 2];
         }
-        var = m2 / n;
     }
-    if (var < 1e-12) var = 1e-12;
-    sc->gamma_eps = 1.0 / var;
-    sc->ge_set = 1;
+    sn[t] = n;
+    smu[t] = mu;
+    sm2[t] = m2;
+    __syncthreads();
+    for (int h = 1; h < kGeParts; h <<= 1) {
+        if ((t & (2 * h - 1)) == 0) {
+            const double na = sn[t], nb = sn[t + h];
+            if (nb > 0.0) {
+                if (na > 0.0) {
+                    const double nn = na + nb, d = smu[t + h] - smu[t];
+                    smu[t] += d * (nb / nn);
+                    sm2[t] += sm2[t + h] + d * d * (na * nb / nn);
+                    sn[t] = nn;
+                } else {
+                    sn[t] = nb;
+                    smu[t] = smu[t + h];
+                    sm2[t] = sm2[t + h];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        double var = sn[0] > 0.0 ? sm2[0] / sn[0] : 1.0;
+        if (var < 1e-12) var = 1e-12;
+        sc->gamma_eps = 1.0 / var;
+        sc->ge_set = 1;
+    }
 }
 
 // Statistics of an arbitrary state (after set_state / set_dictionary): active
@@ -320,7 +339,7 @@ cudaError_t launch_init_gamma_eps(const Geom& g, const float* x, const uint32_t*
                                   double* scratch, cudaStream_t s)
 {
     gamma_eps_parts_kernel<<<kGeParts, 256, 0, s>>>(g.nframe, x, mbits, scratch);
-    gamma_eps_merge_kernel<<<1, 32, 0, s>>>(scratch, kGeParts, sc);
+    gamma_eps_merge_kernel<<<1, kGeParts, 0, s>>>(scratch, kGeParts, sc);
     return cudaGetLastError();
 }
 
