@@ -276,6 +276,7 @@ HyperArgs hyper_args(const sensai_ctx* ctx)
     a.g = ctx->g;
     a.Zb = ctx->Zb;
     a.m = ctx->m;
+    a.arrive = reinterpret_cast<unsigned int*>(ctx->m + ctx->g.K);
     a.part_s2 = ctx->part_s2;
     a.n_s2 = ctx->n_s2;
     a.part_r2 = ctx->part_r2;
@@ -368,7 +369,7 @@ sensai_status run_hyper(sensai_ctx* ctx, cudaStream_t s)
     PhaseTimer timer(ctx, kPhaseHyper, s);
     SENSAI_CUDA(ctx, launch_hyper(a, s));
     timer.stop();
-    ctx->launches += 2;
+    ctx->launches += 1;
     return SENSAI_OK;
 }
 
@@ -534,7 +535,8 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     if (recon_tc_available(ctx->g)) CREATE_CUDA(dalloc(&ctx->Dc, recon_tc_operand_floats(ctx->g)));
     CREATE_CUDA(dalloc(&ctx->pi, (size_t)g.K));
     CREATE_CUDA(dalloc(&ctx->lpi, (size_t)g.K));
-    CREATE_CUDA(dalloc(&ctx->m, (size_t)g.K));
+    CREATE_CUDA(dalloc(&ctx->m, (size_t)g.K + 1));   // [K] counts, then the draw kernel's arrival counter
+    CREATE_CUDA(cudaMemset(ctx->m, 0, sizeof(int) * ((size_t)g.K + 1)));
     CREATE_CUDA(dalloc(&ctx->part_s2, (size_t)2 * g.NW));   // per 16- or 32-patch work unit
     int sms = 0;
     CREATE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));

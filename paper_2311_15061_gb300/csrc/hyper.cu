@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(256) pi_kernel(const HyperArgs a)
 }
 
 // gamma_s and gamma_eps from fixed-order FP64 sums of the per-unit partials;
-// the two Gamma draws on two warps.  Last kernel of an iteration: advances the
-// replay iteration index.
+// the two Gamma draws on two warps.  Last kernel of a batched iteration:
+// advances the replay iteration index.
 __device__ __forceinline__ void gamma_body(const HyperArgs& a)
 {
     __shared__ double red[kHyperThreads / 32];
@@ -129,10 +129,84 @@ cudaError_t launch_hyper_multi(const HyperArgs* args, const int* pi_start, const
     return cudaGetLastError();
 }
 
+// All of an iteration's draws in one launch of K + 1 CTAs.  CTA k < K
+// counts m_k and draws pi_k (as pi_body); CTA K sums the s^2 and r^2
+// partials and draws gamma_eps (as gamma_body).  gamma_s needs sum_k m_k and
+// the s^2 sum, so the last CTA to publish its part (arrival counter, no
+// waiting) sums the counts in index order and draws it on a warp of its own,
+// then resets the counter.  Same sums in the same order and the same draw
+// counters as pi_kernel + gamma_kernel, so the values are identical; the
+// Gamma chains of the K + 2 draws run concurrently instead of in two rounds.
+__global__ void __launch_bounds__(kHyperThreads) hyper_kernel(const HyperArgs a)
+{
+    __shared__ int redi[kHyperThreads / 32];
+    __shared__ double red[kHyperThreads / 32];
+    __shared__ double g2_s, r2_s;
+    __shared__ int last_s;
+    const int K = a.g.K, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool is_pi = (int)blockIdx.x < K;
+    const uint32_t t_it = launch_t(a.t, a.t_dev, a.sc);
+    int mk = 0;
+    if (is_pi) {
+        const int k = blockIdx.x;
+        const uint32_t* z = a.Zb + (long long)k * a.g.NW;
+        int c = 0;
+        for (int w = threadIdx.x; w < a.g.NW; w += blockDim.x) c += __popc(z[w]);
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0) redi[warp] = c;
+        __syncthreads();
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mk += redi[w];
+        if (threadIdx.x == 0) a.m[k] = mk;
+    } else {
+        const double s2 = sum_partials(a.part_s2, a.n_s2, red);   // valid in thread 0
+        const double r2 = sum_partials(a.part_r2, a.n_r2, red);
+        if (threadIdx.x == 0) {
+            a.sc->sum_s2 = s2;
+            a.sc->sum_r2 = r2;
+            r2_s = r2;
+        }
+    }
+    // publish this CTA's part; the last to arrive sees every part
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last_s = atomicAdd(a.arrive, 1u) == (unsigned int)K;
+    }
+    __syncthreads();
+    double g1 = 0.0;
+    if (is_pi) {
+        const int k = blockIdx.x;
+        const double alpha = a.a_over_K + (double)mk;
+        const double beta = a.b_scaled + (double)a.g.N - (double)mk;
+        if (threadIdx.x == 32) g2_s = gamma_draw(beta, a.seed, (uint32_t)k, 0, t_it, kTagPiB);
+        if (threadIdx.x == 0) g1 = gamma_draw(alpha, a.seed, (uint32_t)k, 0, t_it, kTagPiA);
+    } else if (threadIdx.x == 32) {
+        a.sc->gamma_eps =
+            gamma_draw(a.e + 0.5 * (double)a.n_observed, a.seed, 0, 0, t_it, kTagGe) / (a.f + 0.5 * r2_s);
+    }
+    if (last_s && threadIdx.x == 64) {
+        __threadfence();
+        double mtot = 0.0;
+        for (int k = 0; k < K; ++k) mtot += (double)__ldcg(a.m + k);
+        const double s2 = __ldcg(&a.sc->sum_s2);
+        a.sc->gamma_s = gamma_draw(a.c + 0.5 * mtot, a.seed, 0, 0, t_it, kTagGs) / (a.d + 0.5 * s2);
+        a.sc->n_active = (long long)mtot;
+        atomicExch(a.arrive, 0u);
+        if (a.t_dev) a.sc->t_iter = t_it + 1u;   // every CTA has read this replay's index
+    }
+    __syncthreads();
+    if (is_pi && threadIdx.x == 0) {
+        const int k = blockIdx.x;
+        const double pi = g1 / (g1 + g2_s);
+        a.pi[k] = pi;
+        a.lpi[k] = (float)(log(pi) - log1p(-pi));
+    }
+}
+
 cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s)
 {
-    pi_kernel<<<a.g.K, 256, 0, s>>>(a);
-    gamma_kernel<<<1, kHyperThreads, 0, s>>>(a);
+    if (!a.arrive) return cudaErrorInvalidValue;
+    hyper_kernel<<<a.g.K + 1, kHyperThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -400,6 +400,7 @@ struct HyperArgs {
     Geom g;
     const uint32_t* Zb;        // [K][NW] activity words (the counts m_k come from them)
     int* m;                    // [K] active counts, written by the pi draws
+    unsigned int* arrive = nullptr;   // arrival counter of the fused draw kernel (0 between launches)
     const double* part_s2;
     int n_s2;
     const double* part_r2;
@@ -515,7 +516,7 @@ int tiled_grid_size(const Geom& g, int maxobs, int KS, int device);
 cudaError_t launch_slice_dictionary(const Geom& g, const float* D, float* Dsl, int KS, cudaStream_t s);
 cudaError_t launch_sweep_tiled(const SweepArgs& a, int maxobs, int grid, cudaStream_t s);
 cudaError_t launch_dict(const DictArgs& a, int max_slots, cudaStream_t s);
-cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);   // two kernels: pi draws, then gammas
+cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);   // one kernel: K pi draws + gamma_s, gamma_eps
 // Batched: pi_start is the prefix of K_i (one CTA per atom), gamma_start = 0..n.
 cudaError_t launch_hyper_multi(const HyperArgs* args, const int* pi_start, const int* gamma_start, int n,
                                int pi_grid, cudaStream_t s);

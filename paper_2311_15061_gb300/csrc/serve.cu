@@ -198,7 +198,8 @@ static cudaError_t alloc_slot(ServeEngine* e, ServeSlot* s)
     SLOT_TRY(slot_alloc(&s->total, 1));
     SLOT_TRY(slot_alloc(&s->W, (size_t)b.KB * kAtomBlock * npad));
     SLOT_TRY(slot_alloc(&s->Zb, (size_t)b.K * nw));
-    SLOT_TRY(slot_alloc(&s->m, (size_t)b.K));
+    SLOT_TRY(slot_alloc(&s->m, (size_t)b.K + 1));   // [K] counts, then the draw kernel's arrival counter
+    SLOT_TRY(cudaMemset(s->m, 0, sizeof(int) * ((size_t)b.K + 1)));
     SLOT_TRY(slot_alloc(&s->part_s2, 2 * nw));   // per 16- or 32-patch work unit
     SLOT_TRY(slot_alloc(&s->part_r2, 2 * nw));
     SLOT_TRY(slot_alloc(&s->counter, 1));
@@ -299,6 +300,7 @@ static sensai_status process_frame(ServeEngine* e, ServeSlot* sl, const ServeReq
         h.g = g;
         h.Zb = sl->Zb;
         h.m = sl->m;
+        h.arrive = reinterpret_cast<unsigned int*>(sl->m + g.K);
         h.part_s2 = sl->part_s2;
         h.n_s2 = g.NW * plan.lanes;
         h.part_r2 = sl->part_r2;
