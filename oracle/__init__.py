@@ -54,10 +54,14 @@ class Params(ctypes.Structure):
         ("c", ctypes.c_double), ("d", ctypes.c_double),
         ("e", ctypes.c_double), ("f", ctypes.c_double),
         ("seed", ctypes.c_uint64),
+        ("flags", ctypes.c_int32),
     ]
 
 
-def params(M, B, S, K, *, a=None, b=None, c=1e-6, d=1e-6, e=1e-6, f=1e-6, seed=0):
+FLAG_GAMMA_S_FULL = 4   # reading A of the gamma_s update (prior draws for inactive s)
+
+
+def params(M, B, S, K, *, a=None, b=None, c=1e-6, d=1e-6, e=1e-6, f=1e-6, seed=0, flags=0):
     """Model parameters; defaults a = K, b = N/8 (N = number of patches)."""
     prm = Params()
     prm.ndim = len(M)
@@ -71,6 +75,7 @@ def params(M, B, S, K, *, a=None, b=None, c=1e-6, d=1e-6, e=1e-6, f=1e-6, seed=0
     prm.b = float(n / 8.0 if b is None else b)
     prm.c, prm.d, prm.e, prm.f = float(c), float(d), float(e), float(f)
     prm.seed = int(seed)
+    prm.flags = int(flags)
     return prm
 
 

@@ -337,17 +337,22 @@ const int64_t nvisit = patches ? npatches : N;
                 uint32_t blk[4];
                 block_at(prm->seed, (uint32_t)i, (uint32_t)k, (uint32_t)t, ORC_TAG_ZS, blk);
                 int z = (uint64_t)blk[0] < thr;
-                double w_new = 0.0;
+                double w_new = 0.0, s_new = 0.0;
                 if (z) {
                     w_new = gamma_eps * g / lam + box_muller(blk[1], blk[2]) / sqrt(lam);
+                    s_new = w_new;
                     zc += 1.0;
                     s2 += w_new * w_new;
+                } else if (prm->flags & ORC_FLAG_GAMMA_S_FULL) {
+                    /* inactive: s from its prior; the weight z s stays 0 */
+                    s_new = box_muller(blk[1], blk[2]) / sqrt(gamma_s);
+                    s2 += s_new * s_new;
                 }
                 double dw = w_new - w_old;
                 if (dw != 0.0)
                     for (int64_t j = 0; j < nobs; ++j) r[j] -= dk[plist[j]] * dw;
                 Z[i * K + k] = (uint8_t)z;
-                S[i * K + k] = w_new;
+                S[i * K + k] = s_new;
             }
             double r2 = 0.0;
             for (int64_t j = 0; j < nobs; ++j) r2 += r[j] * r[j];
@@ -450,14 +455,14 @@ void orc_hyper(const orc_params* prm, const float* x, const uint8_t* mask,
     orc_patch_origins(prm, origin);
     orc_pixel_offsets(prm, offset);
 
+    const int full_s = (prm->flags & ORC_FLAG_GAMMA_S_FULL) != 0;
     double z_total = 0.0, s2_total = 0.0;
     for (int k = 0; k < K; ++k) {
         double m = 0.0;
-        for (int64_t i = 0; i < N; ++i)
-            if (Z[i * K + k]) {
-                m += 1.0;
-                s2_total += S[i * K + k] * S[i * K + k];
-            }
+        for (int64_t i = 0; i < N; ++i) {
+            if (Z[i * K + k]) m += 1.0;
+            if (Z[i * K + k] || full_s) s2_total += S[i * K + k] * S[i * K + k];
+        }
         z_total += m;
         double alpha = prm->a / K + m;
         double beta = prm->b * (K - 1) / K + (double)N - m;
@@ -476,7 +481,8 @@ void orc_hyper(const orc_params* prm, const float* x, const uint8_t* mask,
             obs_total += 1.0;
         }
 
-    *gamma_s = orc_gamma(prm->c + 0.5 * z_total, prm->seed, 0, 0, (uint32_t)t, ORC_TAG_GS)
+    const double s_count = full_s ? (double)N * K : z_total;   /* entries whose s enters the sum */
+    *gamma_s = orc_gamma(prm->c + 0.5 * s_count, prm->seed, 0, 0, (uint32_t)t, ORC_TAG_GS)
              / (prm->d + 0.5 * s2_total);
     *gamma_eps = orc_gamma(prm->e + 0.5 * obs_total, prm->seed, 0, 0, (uint32_t)t, ORC_TAG_GE)
                / (prm->f + 0.5 * r2_total);

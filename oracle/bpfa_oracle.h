@@ -60,7 +60,17 @@ typedef struct {
     double c, d;       /* gamma_s ~ Gamma(c, d), shape / rate */
     double e, f;       /* gamma_eps ~ Gamma(e, f), shape / rate */
     uint64_t seed;     /* Philox key */
+    int32_t flags;     /* ORC_FLAG_* */
 } orc_params;
+
+/* Reading of the gamma_s update.  Default: the weights of inactive atoms are
+ * integrated out, and gamma_s ~ Ga(c + sum z / 2, d + sum_{z=1} s^2 / 2).
+ * ORC_FLAG_GAMMA_S_FULL: the sweep also draws s_ik ~ N(0, 1/gamma_s) for
+ * every inactive entry (from the same Philox words a z = 1 entry uses for its
+ * normal) and stores it in S; then gamma_s ~ Ga(c + N K / 2,
+ * d + sum_all s^2 / 2).  Both are valid samplers of the same posterior; z
+ * and the active s are the same under both for the same counters. */
+enum { ORC_FLAG_GAMMA_S_FULL = 4 };
 
 enum {
     ORC_TAG_INIT = 1,  /* dictionary initialisation, counter (p, k, 0) */
@@ -101,8 +111,9 @@ void orc_init_dictionary(const orc_params* prm, double* D);
 double orc_init_gamma_eps(const orc_params* prm, const float* x, const uint8_t* mask);
 
 /* Sparse-code sweep at iteration t.  Updates Z and S in place.  stats (may be
- * NULL) receives {sum z, sum of s^2 over active entries, sum over patches of
- * the squared residual on observed pixels after the sweep}. */
+ * NULL) receives {sum z, sum of s^2 over active entries (over all entries
+ * with ORC_FLAG_GAMMA_S_FULL), sum over patches of the squared residual on
+ * observed pixels after the sweep}. */
 void orc_zs_sweep(const orc_params* prm, const float* x, const uint8_t* mask,
                   const double* D, uint8_t* Z, double* S, const double* pi,
                   double gamma_s, double gamma_eps, int64_t t, double* stats);
@@ -122,7 +133,8 @@ void orc_d_sweep(const orc_params* prm, const float* x, const uint8_t* mask,
                  double* D, const uint8_t* Z, const double* S, double gamma_eps, int64_t t);
 
 /* pi, gamma_s and gamma_eps draws at iteration t from the current state.
- * stats (may be NULL) receives {sum z, sum s^2, sum r^2, sum |Omega_i|}. */
+ * stats (may be NULL) receives {sum z, sum s^2 (active entries; all entries
+ * with ORC_FLAG_GAMMA_S_FULL), sum r^2, sum |Omega_i|}. */
 void orc_hyper(const orc_params* prm, const float* x, const uint8_t* mask,
                const double* D, const uint8_t* Z, const double* S,
                double* pi, double* gamma_s, double* gamma_eps, int64_t t, double* stats);
