@@ -253,7 +253,7 @@ def run_gpu(args):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SMS * LANES_PER_SM * sm_mhz * 1e6 / 1e12   # T lane-ops/s
     achieved = ops / sweep_n / (sweep_ms / sweep_n / 1e3) / 1e12
-    traffic = _traffic_record(("sweep.cu", "internal.cuh"))
+    traffic = _traffic_record(("sweep.cu", "sweep_block.cuh", "internal.cuh"))
 
     # end to end through the C ABI with pinned host buffers
     xh = torch.from_numpy(x).pin_memory()

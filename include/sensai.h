@@ -68,7 +68,8 @@ typedef enum {
  * in any patch (above 96 a patch's pixels are split over a lane pair).  a <= 0 selects a = K and
  * b <= 0 selects b = N / 8 (N = number of patches).  c..f > 0.  flags:
  * SENSAI_FLAG_CHAIN_DICTIONARY, SENSAI_FLAG_STREAM_DICTIONARY, and with the
- * latter SENSAI_SLICE_ATOMS(n); other bits are EINVAL.
+ * latter SENSAI_SLICE_ATOMS(n), SENSAI_FLAG_GAMMA_S_FULL; other bits are
+ * EINVAL.
  *
  * The code sweep keeps the whole dictionary in shared memory when
  * (P + 1) * (K rounded up to 8, odd) floats fit (K = 128, P = 100: 52 KB);
@@ -82,6 +83,19 @@ typedef enum {
  * GPU with others (required for sensai_batch_create).  Results are the same
  * draws up to FP32 summation order. */
 #define SENSAI_FLAG_CHAIN_DICTIONARY 0x2
+/* Reading of the gamma_s update (BPFA section: the weights' precision has a
+ * Gamma prior).  Default: the weights of inactive atoms are integrated out;
+ * gamma_s ~ Ga(c + sum z / 2, d + sum_{z=1} s^2 / 2).  With this flag every
+ * code sweep is followed by a draw of s_ik ~ N(0, 1/gamma_s) for each entry
+ * it left inactive (from the Philox words an active entry uses for its
+ * normal; the weight z s stays 0 and the draw is not stored), whose square
+ * is added to the s^2 sum; then
+ * gamma_s ~ Ga(c + N K / 2, d + sum_all s^2 / 2).  z and the active weights
+ * are the same draws under both readings.  The inactive draws exist only
+ * within the sweep that made them: a gamma_s draw from a state set by
+ * sensai_set_state with no sweep since sums the stored (active) weights.
+ * One extra kernel per code sweep; not accepted by sensai_batch_create. */
+#define SENSAI_FLAG_GAMMA_S_FULL 0x4
 #define SENSAI_SLICE_ATOMS(n) ((((n) / 8) & 0xff) << 8)
 typedef struct {
     int32_t ndim;

@@ -294,6 +294,7 @@ HyperArgs hyper_args(const sensai_ctx* ctx)
     a.seed = ctx->prm.seed;
     a.t = (uint32_t)ctx->t;
     a.t_dev = ctx->t_on_device;
+    a.full_s = (ctx->prm.flags & SENSAI_FLAG_GAMMA_S_FULL) != 0;
     return a;
 }
 
@@ -307,6 +308,11 @@ sensai_status run_sweep(sensai_ctx* ctx, cudaStream_t s)
     PhaseTimer timer(ctx, kPhaseCodes, s);
     int nl = 0;
     SENSAI_CUDA(ctx, launch_code_sweep(a, plan, ctx->maxobs, ctx->Dsl, s, &nl));
+    if (ctx->prm.flags & SENSAI_FLAG_GAMMA_S_FULL) {
+        SENSAI_CUDA(ctx, launch_prior_s2(ctx->g, ctx->Zb, ctx->sc, a.t, a.t_dev, ctx->prm.seed, plan.lanes,
+                                         ctx->part_s2, s));
+        ++nl;
+    }
     timer.stop();
     ctx->launches += nl;
     ctx->codes_valid = true;
@@ -415,7 +421,8 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     const sensai_params& p = *prm;
     if (p.ndim < 1 || p.ndim > kMaxDim) return fail(SENSAI_EINVAL, "ndim must be 1..4 (got %d)", p.ndim);
     if (p.K < 1 || p.K > 1024) return fail(SENSAI_EINVAL, "K must be 1..1024 (got %d)", p.K);
-    const int known_flags = SENSAI_FLAG_STREAM_DICTIONARY | SENSAI_FLAG_CHAIN_DICTIONARY | SENSAI_SLICE_ATOMS(2040);
+    const int known_flags = SENSAI_FLAG_STREAM_DICTIONARY | SENSAI_FLAG_CHAIN_DICTIONARY | SENSAI_FLAG_GAMMA_S_FULL |
+                            SENSAI_SLICE_ATOMS(2040);
     if ((p.flags & ~known_flags) != 0) return fail(SENSAI_EINVAL, "unknown flags 0x%x", p.flags);
     if ((p.flags & SENSAI_SLICE_ATOMS(2040)) != 0 && !(p.flags & SENSAI_FLAG_STREAM_DICTIONARY))
         return fail(SENSAI_EINVAL, "SENSAI_SLICE_ATOMS needs SENSAI_FLAG_STREAM_DICTIONARY");
@@ -865,6 +872,7 @@ sensai_status sensai_serve_start(sensai_ctx* ctx, const sensai_serve_params* sp)
     in.max_observed = sp->max_observed;
     in.stream_dictionary = (ctx->prm.flags & SENSAI_FLAG_STREAM_DICTIONARY) != 0;
     in.slice_atoms = ((ctx->prm.flags >> 8) & 0xff) * kAtomBlock;
+    in.full_s = (ctx->prm.flags & SENSAI_FLAG_GAMMA_S_FULL) != 0;
     ctx->serve = serve_create(in, &st);
     if (!ctx->serve) return fail(st, "could not allocate the serving slots");
     return SENSAI_OK;
@@ -1293,6 +1301,8 @@ sensai_status sensai_batch_create(sensai_ctx* const* ctxs, int32_t n, sensai_bat
             return fail(SENSAI_EINVAL, "context %d uses the cooperative dictionary kernel; create it with "
                         "SENSAI_FLAG_CHAIN_DICTIONARY", i);
         if (ctxs[i]->device != ctxs[0]->device) return fail(SENSAI_EINVAL, "contexts on different devices");
+        if (ctxs[i]->prm.flags & SENSAI_FLAG_GAMMA_S_FULL)
+            return fail(SENSAI_EINVAL, "context %d uses SENSAI_FLAG_GAMMA_S_FULL, which batches do not support", i);
         if (ctxs[i]->serve) return fail(SENSAI_EBUSY, "context %d is serving", i);
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return fail(SENSAI_EINVAL, "context %d appears twice", i);

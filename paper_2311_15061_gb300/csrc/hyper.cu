@@ -5,6 +5,8 @@
 // conjugacy), given the current codes, weights and residual:
 //   pi_k      ~ Beta(a/K + m_k, b(K-1)/K + N - m_k),    m_k = sum_i z_ik
 //   gamma_s   ~ Gamma(c + 1/2 sum_ik z_ik, d + 1/2 sum_{z_ik=1} s_ik^2)
+//               (with SENSAI_FLAG_GAMMA_S_FULL: Gamma(c + N K / 2, d + 1/2 sum_ik s_ik^2),
+//               the inactive s_ik being the sweep's prior draws)
 //   gamma_eps ~ Gamma(e + 1/2 sum_i |Omega_i|, f + 1/2 sum_i ||r_i||^2)
 // (shape, rate).  The global sums are FP64 and reduced in a fixed order from
 // per-chunk (or per-pixel) partials, so the draws are deterministic.
@@ -87,7 +89,8 @@ __device__ __forceinline__ void gamma_body(const HyperArgs& a)
     if (threadIdx.x == 32)
         ge_s = gamma_draw(a.e + 0.5 * (double)a.n_observed, a.seed, 0, 0, t_it, kTagGe) / (a.f + 0.5 * bc[1]);
     double gs = 0.0;
-    if (threadIdx.x == 0) gs = gamma_draw(a.c + 0.5 * bc[2], a.seed, 0, 0, t_it, kTagGs) / (a.d + 0.5 * bc[0]);
+    const double s_count = a.full_s ? (double)a.g.N * K : bc[2];   // entries whose s enters the s^2 sum
+    if (threadIdx.x == 0) gs = gamma_draw(a.c + 0.5 * s_count, a.seed, 0, 0, t_it, kTagGs) / (a.d + 0.5 * bc[0]);
     __syncthreads();
     if (threadIdx.x == 0) {
         a.sc->gamma_s = gs;
@@ -126,6 +129,45 @@ cudaError_t launch_hyper_multi(const HyperArgs* args, const int* pi_start, const
 {
     pi_multi_kernel<<<pi_grid, 256, 0, s>>>(args, pi_start, n);
     gamma_multi_kernel<<<n, kHyperThreads, 0, s>>>(args, gamma_start, n);
+    return cudaGetLastError();
+}
+
+// Reading A of the gamma_s update: every entry the last code sweep left
+// inactive (z_ik = 0, patch i < N) has its weight drawn from the prior,
+// s_ik ~ N(0, 1/gamma_s), from the Philox words an active entry uses for its
+// normal (counter (i, k, t, codes), words 1 and 2, the same Box-Muller
+// normal); the weight z s stays 0, so only s_ik^2 is kept, added to the
+// sweep's s^2 partial of the patch's work unit.  One warp per 32-patch
+// activity word over all atoms; lane 0 is the one writer of its unit.
+__global__ void __launch_bounds__(256) prior_s2_kernel(Geom g, const uint32_t* Zb, const DevScalars* sc, uint32_t t,
+                                                       bool t_dev, unsigned long long seed, int lanes,
+                                                       double* part_s2)
+{
+    const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= g.NW) return;
+    const uint32_t t_it = launch_t(t, t_dev, sc);
+    const float sd = rsqrtf((float)sc->gamma_s);
+    const uint2 key = seed_key(seed);
+    const long long i = w * 32 + lane;
+    float s2 = 0.0f;
+    if (i < g.N) {
+        for (int k = 0; k < g.K; ++k) {
+            if ((Zb[(long long)k * g.NW + w] >> lane) & 1u) continue;
+            const uint4 blk = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)k, t_it, kTagCodes), key);
+            const float sp = normal32(blk.y, blk.z) * sd;
+            s2 = fmaf(sp, sp, s2);
+        }
+    }
+    const double sum = warp_sum((double)s2);
+    if (lane == 0) part_s2[lanes == 2 ? 2 * w : w] += sum;
+}
+
+cudaError_t launch_prior_s2(const Geom& g, const uint32_t* Zb, const DevScalars* sc, uint32_t t, bool t_dev,
+                            unsigned long long seed, int lanes, double* part_s2, cudaStream_t s)
+{
+    if (lanes != 1 && lanes != 2) return cudaErrorInvalidValue;
+    prior_s2_kernel<<<(unsigned int)((g.NW + 7) / 8), 256, 0, s>>>(g, Zb, sc, t, t_dev, seed, lanes, part_s2);
     return cudaGetLastError();
 }
 
@@ -189,7 +231,8 @@ __global__ void __launch_bounds__(kHyperThreads) hyper_kernel(const HyperArgs a)
         double mtot = 0.0;
         for (int k = 0; k < K; ++k) mtot += (double)__ldcg(a.m + k);
         const double s2 = __ldcg(&a.sc->sum_s2);
-        a.sc->gamma_s = gamma_draw(a.c + 0.5 * mtot, a.seed, 0, 0, t_it, kTagGs) / (a.d + 0.5 * s2);
+        const double s_count = a.full_s ? (double)a.g.N * K : mtot;   // entries whose s enters the s^2 sum
+        a.sc->gamma_s = gamma_draw(a.c + 0.5 * s_count, a.seed, 0, 0, t_it, kTagGs) / (a.d + 0.5 * s2);
         a.sc->n_active = (long long)mtot;
         atomicExch(a.arrive, 0u);
         if (a.t_dev) a.sc->t_iter = t_it + 1u;   // every CTA has read this replay's index

@@ -413,6 +413,7 @@ struct HyperArgs {
     unsigned long long seed;
     uint32_t t;
     bool t_dev = false;        // take t from sc->t_iter (graph replay)
+    bool full_s = false;       // SENSAI_FLAG_GAMMA_S_FULL: gamma_s shape c + N K / 2
 };
 
 // Live serving engine (serve.cu).
@@ -433,6 +434,7 @@ struct ServeInit {
     int max_observed;
     bool stream_dictionary;    // the context's SENSAI_FLAG_STREAM_DICTIONARY
     int slice_atoms;           // the context's SENSAI_SLICE_ATOMS (0: largest that fits)
+    bool full_s = false;       // the context's SENSAI_FLAG_GAMMA_S_FULL
 };
 ServeEngine* serve_create(const ServeInit& in, sensai_status* status);
 sensai_status serve_submit(ServeEngine* e, int32_t stream_id, uint64_t frame_id, const float* frame,
@@ -516,6 +518,12 @@ int tiled_grid_size(const Geom& g, int maxobs, int KS, int device);
 cudaError_t launch_slice_dictionary(const Geom& g, const float* D, float* Dsl, int KS, cudaStream_t s);
 cudaError_t launch_sweep_tiled(const SweepArgs& a, int maxobs, int grid, cudaStream_t s);
 cudaError_t launch_dict(const DictArgs& a, int max_slots, cudaStream_t s);
+// Reading A of the gamma_s update (SENSAI_FLAG_GAMMA_S_FULL): after a code
+// sweep with the same (t, t_dev, seed), adds to part_s2 the squares of the
+// prior draws of the entries that sweep left inactive.  lanes: the sweep's
+// lanes per patch (its partials are per 32 / lanes patches).
+cudaError_t launch_prior_s2(const Geom& g, const uint32_t* Zb, const DevScalars* sc, uint32_t t, bool t_dev,
+                            unsigned long long seed, int lanes, double* part_s2, cudaStream_t s);
 cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);   // one kernel: K pi draws + gamma_s, gamma_eps
 // Batched: pi_start is the prefix of K_i (one CTA per atom), gamma_start = 0..n.
 cudaError_t launch_hyper_multi(const HyperArgs* args, const int* pi_start, const int* gamma_start, int n,

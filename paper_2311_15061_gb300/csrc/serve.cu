@@ -92,6 +92,7 @@ struct ServeEngine {
     Geom base{};                 // ndim, B, S, K, P of the context
     int32_t max_observed = 0;
     bool stream_dictionary = false;
+    bool full_s = false;                 // SENSAI_FLAG_GAMMA_S_FULL of the context
     int slice_atoms = 0;
     long long max_pixels = 0;
     long long budget = 0;
@@ -296,6 +297,7 @@ static sensai_status process_frame(ServeEngine* e, ServeSlot* sl, const ServeReq
         a.keys = philox_round_keys(fseed);
         a.t = e->t0 + (uint32_t)sw;
         FRAME_TRY(launch_code_sweep(a, plan, maxobs, sl->Dsl, s, nullptr));
+        if (e->full_s) FRAME_TRY(launch_prior_s2(g, sl->Zb, sl->sc, a.t, false, fseed, plan.lanes, sl->part_s2, s));
         HyperArgs h{};
         h.g = g;
         h.Zb = sl->Zb;
@@ -317,6 +319,7 @@ static sensai_status process_frame(ServeEngine* e, ServeSlot* sl, const ServeReq
         h.sc = sl->sc;
         h.seed = fseed;
         h.t = e->t0 + (uint32_t)sw;
+        h.full_s = e->full_s;
         FRAME_TRY(launch_hyper(h, s));
     }
     FRAME_TRY(launch_reconstruct(g, e->D, sl->Dc, sl->W, sl->Y, sl->out, &sl->sc->status, s));
@@ -374,6 +377,7 @@ ServeEngine* serve_create(const ServeInit& in, sensai_status* status)
     e->max_observed = in.max_observed;
     e->stream_dictionary = in.stream_dictionary;
     e->slice_atoms = in.slice_atoms;
+    e->full_s = in.full_s;
     e->max_pixels = in.max_pixels;
     e->a_over_K = in.a_over_K;
     e->b_param = in.b_param;

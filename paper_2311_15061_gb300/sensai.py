@@ -176,6 +176,7 @@ def _buf(a, dtype, count=None, name="buffer"):
 
 SENSAI_FLAG_STREAM_DICTIONARY = 0x1
 SENSAI_FLAG_CHAIN_DICTIONARY = 0x2
+SENSAI_FLAG_GAMMA_S_FULL = 0x4   # reading A of the gamma_s update: prior draws for inactive weights
 
 
 def SENSAI_SLICE_ATOMS(n):

@@ -67,7 +67,7 @@ def test_invalid_hyperparameters_rejected(lib):
     mask = np.ones((16, 16), np.uint8)
     h = ctypes.c_void_p()
     assert lib._lib.sensai_create(ctypes.byref(prm), mask.ctypes.data, ctypes.byref(h)) == lib.SENSAI_EINVAL
-    for flags in (0x4, lib.SENSAI_SLICE_ATOMS(8)):   # an unknown bit; a slice size without streaming
+    for flags in (0x8, lib.SENSAI_SLICE_ATOMS(8)):   # an unknown bit; a slice size without streaming
         prm = lib.make_params((16, 16), (4, 4), (1, 1), 8, flags=flags)
         assert lib._lib.sensai_create(ctypes.byref(prm), mask.ctypes.data, ctypes.byref(h)) == lib.SENSAI_EINVAL
 

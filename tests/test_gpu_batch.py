@@ -89,11 +89,13 @@ def test_tuning_keeps_results(lib):
         _assert_same(_state(cb), _state(ca))
 
 
-def test_batch_rejects_cooperative_and_duplicate_contexts(lib):
+def test_batch_rejects_cooperative_duplicate_and_full_reading_contexts(lib):
     prm, x, clean, mask = problem((64, 64), (8, 8), (1, 1), 16, 0.25)
     coop = lib.Context(lib.make_params((64, 64), (8, 8), (1, 1), 16), mask)
     chain = lib.Context(lib.make_params((64, 64), (8, 8), (1, 1), 16, flags=lib.SENSAI_FLAG_CHAIN_DICTIONARY), mask)
-    for members in ([coop], [chain, chain]):
+    full = lib.Context(lib.make_params((64, 64), (8, 8), (1, 1), 16, flags=lib.SENSAI_FLAG_CHAIN_DICTIONARY
+                                       | lib.SENSAI_FLAG_GAMMA_S_FULL), mask)
+    for members in ([coop], [chain, chain], [chain, full]):
         with pytest.raises(lib.SensaiError) as err:
             lib.Batch(members)
         assert err.value.status == lib.SENSAI_EINVAL

@@ -340,7 +340,7 @@ def test_streamed_learning_is_bit_identical_to_resident():
 def test_flags_validation():
     from paper_2311_15061_gb300 import sensai
     prm, x, clean, mask = problem((40, 40), (8, 8), (1, 1), 16, 0.25)
-    for bad in (0x4, sensai.SENSAI_SLICE_ATOMS(8)):   # unknown bit; slice without streaming
+    for bad in (0x8, sensai.SENSAI_SLICE_ATOMS(8)):   # unknown bit; slice without streaming
         with pytest.raises(sensai.SensaiError) as err:
             gpu_context(prm, mask, bad)
         assert err.value.status == sensai.SENSAI_EINVAL
@@ -389,3 +389,53 @@ def test_full_size_streamed_sweep_sampled_video():
     nflip, serr = compare_codes(st, g, st, L, patches=sample)
     assert nflip <= 3
     assert serr <= S_TOL
+
+
+# --- reading A of the gamma_s update (SENSAI_FLAG_GAMMA_S_FULL) ---
+
+def test_gamma_s_full_reading():
+    """Under reading A the code sweep gives the same z and active weights as
+    the oracle's reading A sweep (and as the default reading's sweep on the
+    GPU, bit for bit).  The s^2 sum behind the next gamma_s draw also holds
+    the prior draws of the inactive weights: FP32 normals against the
+    oracle's FP64 ones, within 1e-5 relative.  gamma_s then has shape
+    c + N K / 2 (1e-5 relative: it inherits the FP32 s^2 sum)."""
+    from paper_2311_15061_gb300 import sensai
+    prm, x, clean, mask = problem(C1["M"], C1["B"], C1["S"], C1["K"], C1["frac"], 3)
+    prm.flags = O.FLAG_GAMMA_S_FULL
+    st = oracle_state(prm, x, mask, 2)
+    N = st.Z.shape[0]
+
+    ctx = gpu_context(prm, mask, sensai.SENSAI_FLAG_GAMMA_S_FULL)
+    push_state(ctx, st, x)
+    ctx.sensai_sweep_codes()
+    g = ctx.sensai_get_state()
+    ctx.sensai_draw_hyper()
+    gh = ctx.sensai_get_state()
+    gstats = ctx.sensai_get_stats()
+
+    ost = st.copy()
+    _, L = O.zs_sweep_subset(ost, x, mask, want_logodds=True)
+    active = ost.copy()
+    active.S = active.S * active.Z   # the GPU stores only the active weights
+    nflip, serr = compare_codes(st, g, active, L)
+    assert nflip <= max(3, 1e-4 * N), nflip
+    assert serr <= S_TOL, serr
+    assert np.count_nonzero(ost.S[ost.Z == 0]) > 0.99 * np.count_nonzero(ost.Z == 0)
+    ostats = O.hyper(ost, x, mask)
+    assert abs(gstats.sum_s2 / ostats[1] - 1) <= 1e-5, (gstats.sum_s2, ostats[1])
+    assert abs(gh["gamma_s"] / ost.gamma_s - 1) <= 1e-5, (gh["gamma_s"], ost.gamma_s)
+    np.testing.assert_allclose(gh["pi"], ost.pi, rtol=1e-9)
+    ctx.close()
+
+    # the default reading on the GPU: the same z and weights, a smaller s^2 sum
+    ctx = gpu_context(prm, mask, 0)
+    push_state(ctx, st, x)
+    ctx.sensai_sweep_codes()
+    gb = ctx.sensai_get_state()
+    ctx.sensai_draw_hyper()
+    bstats = ctx.sensai_get_stats()
+    ctx.close()
+    np.testing.assert_array_equal(gb["Z"], g["Z"])
+    np.testing.assert_array_equal(gb["S"], g["S"])
+    assert bstats.sum_s2 < gstats.sum_s2
