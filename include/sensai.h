@@ -302,6 +302,21 @@ void sensai_batch_destroy(sensai_batch* b);
  * did not give up, SENSAI_EINVAL for another `which`.  Takes ~1 s. */
 sensai_status sensai_selftest_wait(int32_t which);
 
+/* Per-iteration metrics trace, the paper's live statistics and image-quality
+ * monitoring as text.  path: a file opened for appending; NULL stops
+ * tracing (and closes the file).  clean: NULL, or the ground-truth frame
+ * (prod(M) floats, host or device; copied).  After every Gibbs iteration of
+ * sensai_learn and sensai_inpaint the context appends one JSON line:
+ * {"t": the iteration's counter, "mode": "learn" | "inpaint", "gamma_s",
+ * "gamma_eps": the iteration's draws, "active": sum z, "active_per_patch",
+ * "sum_s2", "sum_r2": the sums behind the gamma draws, "psnr_db": 10 log10(1 /
+ * MSE) of the current overlap-add reconstruction against clean over all
+ * pixels (null without clean), "wall_ms": host time since the previous
+ * line}.  Each line synchronises the stream; with clean it adds one
+ * reconstruction and a frame-sized device-to-host copy.  The sampler's
+ * results do not depend on tracing.  EINVAL if the file cannot be opened. */
+sensai_status sensai_trace(sensai_ctx* ctx, const char* path, const float* clean);
+
 /* Per-phase device timing.  enable = 1 clears the record and starts timing:
  * every later phase records a CUDA event pair on its launching stream;
  * enable = 0 stops.  sensai_profile_read synchronises and returns, for the

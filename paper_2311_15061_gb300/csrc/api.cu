@@ -5,6 +5,7 @@
 // every arithmetic step of the sampler runs in the kernels of sweep.cu,
 // dict.cu, hyper.cu and geometry.cu.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -56,6 +57,10 @@ struct sensai_ctx {
     int n_r2 = 0;               // valid entries of part_r2
     int n_s2 = 0;               // valid entries of part_s2
     bool broken = false;
+    FILE* trace = nullptr;               // per-iteration metrics lines (sensai_trace)
+    std::vector<float> trace_clean;      // ground truth of the trace's PSNR (empty: none)
+    std::vector<float> trace_rec;        // host copy of the reconstruction
+    std::chrono::steady_clock::time_point trace_last{};
     cudaStream_t last_stream = nullptr;
     long long launches = 0;     // kernels launched by this context
     bool profiling = false;
@@ -409,6 +414,47 @@ sensai_status write_out(sensai_ctx* ctx, const void* src, void* dst, size_t byte
 
 }  // namespace
 
+// One metrics line per Gibbs iteration (sensai_trace): the draws of the
+// iteration just finished, its active count and sums, the host time since
+// the previous line, and the PSNR of the current reconstruction against the
+// ground truth when one was given.  Synchronises the stream.
+sensai_status trace_iteration(sensai_ctx* ctx, cudaStream_t s, const char* mode)
+{
+    if (!ctx->trace) return SENSAI_OK;
+    DevScalars h{};
+    SENSAI_CUDA(ctx, cudaMemcpyAsync(&h, ctx->sc, sizeof h, cudaMemcpyDeviceToHost, s));
+    const bool have_clean = !ctx->trace_clean.empty();
+    if (have_clean) {
+        SENSAI_CUDA(ctx, launch_reconstruct(ctx->g, ctx->D, ctx->Dc, ctx->W, ctx->Y, ctx->out, &ctx->sc->status, s));
+        ctx->launches += reconstruct_launches(ctx->g);
+        SENSAI_CUDA(ctx, cudaMemcpyAsync(ctx->trace_rec.data(), ctx->out, sizeof(float) * ctx->trace_rec.size(),
+                                         cudaMemcpyDeviceToHost, s));
+    }
+    SENSAI_CUDA(ctx, cudaStreamSynchronize(s));
+    if (h.status != 0) return fail(SENSAI_ETIMEOUT, "a device-side wait timed out (status %d)", h.status);
+    char psnr[40] = "null";
+    if (have_clean) {
+        double se = 0.0;
+        for (size_t q = 0; q < ctx->trace_rec.size(); ++q) {
+            const double d = (double)ctx->trace_rec[q] - (double)ctx->trace_clean[q];
+            se += d * d;
+        }
+        const double mse = se / (double)ctx->trace_rec.size();
+        if (mse > 0.0) snprintf(psnr, sizeof psnr, "%.17g", 10.0 * std::log10(1.0 / mse));
+    }
+    const auto now = std::chrono::steady_clock::now();
+    const double wall_ms = std::chrono::duration<double, std::milli>(now - ctx->trace_last).count();
+    ctx->trace_last = now;
+    fprintf(ctx->trace,
+            "{\"t\": %lld, \"mode\": \"%s\", \"gamma_s\": %.17g, \"gamma_eps\": %.17g, \"active\": %lld, "
+            "\"active_per_patch\": %.17g, \"sum_s2\": %.17g, \"sum_r2\": %.17g, \"psnr_db\": %s, "
+            "\"wall_ms\": %.3f}\n",
+            (long long)(ctx->t - 1), mode, h.gamma_s, h.gamma_eps, (long long)h.n_active,
+            (double)h.n_active / (double)ctx->g.N, h.sum_s2, h.sum_r2, psnr, wall_ms);
+    fflush(ctx->trace);
+    return SENSAI_OK;
+}
+
 extern "C" {
 
 const char* sensai_last_error(void) { return g_last_error.c_str(); }
@@ -579,6 +625,7 @@ void sensai_destroy(sensai_ctx* ctx)
     if (ctx->serve) serve_destroy(ctx->serve);
     cudaDeviceSynchronize();
     clear_timers(ctx);
+    if (ctx->trace) fclose(ctx->trace);
     free_all(ctx);
     delete ctx;
 }
@@ -641,6 +688,7 @@ sensai_status sensai_learn(sensai_ctx* ctx, const float* frame, int32_t iters, v
         if ((st = run_dictionary(ctx, s)) != SENSAI_OK) return st;
         if ((st = run_hyper(ctx, s)) != SENSAI_OK) return st;
         ctx->t += 1;
+        if ((st = trace_iteration(ctx, s, "learn")) != SENSAI_OK) return st;
     }
     return SENSAI_OK;
 }
@@ -659,6 +707,7 @@ sensai_status sensai_inpaint(sensai_ctx* ctx, const float* frame, int32_t sweeps
         if ((st = run_sweep(ctx, s)) != SENSAI_OK) return st;
         if ((st = run_hyper(ctx, s)) != SENSAI_OK) return st;
         ctx->t += 1;
+        if ((st = trace_iteration(ctx, s, "inpaint")) != SENSAI_OK) return st;
     }
     if (!out) return SENSAI_OK;
     const bool dev = is_device_pointer(out);
@@ -906,6 +955,32 @@ sensai_status sensai_serve_stop(sensai_ctx* ctx)
     if (!ctx->serve) return fail(SENSAI_ESTATE, "serving engine not started");
     serve_destroy(ctx->serve);
     ctx->serve = nullptr;
+    return SENSAI_OK;
+}
+
+sensai_status sensai_trace(sensai_ctx* ctx, const char* path, const float* clean)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    if (ctx->trace) fclose(ctx->trace);
+    ctx->trace = nullptr;
+    ctx->trace_clean.clear();
+    ctx->trace_rec.clear();
+    if (!path) return SENSAI_OK;
+    const size_t n = (size_t)ctx->g.nframe;
+    if (clean) {
+        ctx->trace_clean.resize(n);
+        ctx->trace_rec.resize(n);
+        SENSAI_CUDA(ctx, cudaMemcpy(ctx->trace_clean.data(), clean, sizeof(float) * n, cudaMemcpyDefault));
+    }
+    FILE* f = fopen(path, "a");
+    if (!f) {
+        ctx->trace_clean.clear();
+        ctx->trace_rec.clear();
+        return fail(SENSAI_EINVAL, "cannot open the trace file %s", path);
+    }
+    ctx->trace = f;
+    ctx->trace_last = std::chrono::steady_clock::now();
     return SENSAI_OK;
 }
 

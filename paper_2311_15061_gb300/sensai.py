@@ -26,7 +26,8 @@ EXPORTED = [
     "sensai_create", "sensai_destroy", "sensai_set_frame", "sensai_reset", "sensai_learn",
     "sensai_inpaint", "sensai_sweep_codes", "sensai_draw_dictionary", "sensai_draw_hyper",
     "sensai_reconstruct", "sensai_overlap_counts", "sensai_get_dictionary", "sensai_set_dictionary",
-    "sensai_get_state", "sensai_set_state", "sensai_get_stats", "sensai_profile", "sensai_profile_read",
+    "sensai_get_state", "sensai_set_state", "sensai_get_stats", "sensai_trace", "sensai_profile",
+    "sensai_profile_read",
     "sensai_reconstruct_static", "sensai_serve_start", "sensai_submit_frame", "sensai_serve_drain",
     "sensai_serve_stop", "sensai_batch_create", "sensai_batch_learn", "sensai_batch_tune",
     "sensai_batch_destroy", "sensai_selftest_wait", "sensai_last_error",
@@ -117,6 +118,7 @@ _SIG = {
     "sensai_get_state": (_st, [_vp, ctypes.POINTER(sensai_state)]),
     "sensai_set_state": (_st, [_vp, ctypes.POINTER(sensai_state)]),
     "sensai_get_stats": (_st, [_vp, ctypes.POINTER(sensai_stats)]),
+    "sensai_trace": (_st, [_vp, ctypes.c_char_p, _vp]),
     "sensai_profile": (_st, [_vp, _i32]),
     "sensai_profile_read": (_st, [_vp, _vp, _vp]),
     "sensai_reconstruct_static": (_st, [ctypes.POINTER(sensai_params), _vp, _vp, _vp, _vp]),
@@ -346,6 +348,14 @@ class Context:
 
     def sensai_serve_stop(self):
         _check(_lib.sensai_serve_stop(self._h))
+
+    def sensai_trace(self, path, clean=None):
+        """Append one JSON line of metrics per Gibbs iteration to ``path``
+        (None stops); ``clean`` (a float32 frame, host or device) adds the
+        PSNR of the current reconstruction."""
+        arr = np.ascontiguousarray(clean, np.float32) if isinstance(clean, np.ndarray) else clean
+        c = None if arr is None else _buf(arr, np.float32, self.nframe, "clean")
+        _check(_lib.sensai_trace(self._h, None if path is None else str(path).encode(), c))
 
     def sensai_profile(self, enable):
         _check(_lib.sensai_profile(self._h, int(enable)))
