@@ -165,3 +165,35 @@ def test_serving_with_streamed_dictionary():
         c2.sensai_inpaint(fx, 3, ref)
         c2.close()
         np.testing.assert_array_equal(served[(2, j)], ref)
+
+
+def test_serving_with_full_gamma_s_reading():
+    """SENSAI_FLAG_GAMMA_S_FULL carries into serving: each served frame runs
+    the prior-draw pass after its code sweeps and equals sensai_inpaint on a
+    context with the same flag and the frame's seed."""
+    from paper_2311_15061_gb300 import sensai, synth
+    M, B, K = (48, 48), (8, 8), 32
+    flags = sensai.SENSAI_FLAG_GAMMA_S_FULL
+    x, clean = synth.stem_frame(M, 4)
+    mask = synth.random_mask(M, 0.2, 4)
+    ctx = sensai.Context(sensai.make_params(M, B, (1, 1), K, seed=6, flags=flags), mask)
+    ctx.sensai_learn(x, 2)
+    st = ctx.sensai_get_state()
+    ctx.sensai_serve_start(slots=2, max_pixels=64 * 64, max_observed=64)
+    frames = [(synth.stem_frame((52, 56), 20 + j)[0], synth.random_mask((52, 56), 0.15, 20 + j)) for j in range(3)]
+    served = _serve(ctx, [(3, j, fx, fm) for j, (fx, fm) in enumerate(frames)])
+    ctx.sensai_serve_stop()
+    ctx.close()
+    for j, (fx, fm) in enumerate(frames):
+        for f, same in ((flags, True), (0, False)):
+            p = sensai.make_params((52, 56), B, (1, 1), K, seed=_frame_seed(6, 3, j), flags=f)
+            c2 = sensai.Context(p, fm)
+            c2.sensai_set_state(D=st["D"], pi=st["pi"], gamma_s=st["gamma_s"], gamma_eps=st["gamma_eps"],
+                                iter=st["iter"])
+            ref = np.empty((52, 56), np.float32)
+            c2.sensai_inpaint(fx, 3, ref)
+            c2.close()
+            if same:
+                np.testing.assert_array_equal(served[(3, j)], ref)
+            else:   # the default reading draws other gamma_s values, so other codes
+                assert not np.array_equal(served[(3, j)], ref)
