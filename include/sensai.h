@@ -152,7 +152,10 @@ typedef struct {
  * 1 / max(var(observed pixels), 1e-12).  Device memory is allocated here
  * and released by sensai_destroy.  Sec. "N-Dimensional Inpainting" (patch
  * shape B in any dimension), Sec. "SenseAI: Feature Summary" (modular
- * library, programmatic signal selection = the caller's mask). */
+ * library, programmatic signal selection = the caller's mask).  Any failure
+ * frees everything allocated so far; out of device memory is ENOMEM.  For
+ * tests of that path the environment variable SENSAI_FAULT=alloc:N makes the
+ * N-th device allocation of the call (1-based) fail as out of memory. */
 sensai_status sensai_create(const sensai_params* params, const uint8_t* mask, sensai_ctx** out);
 void sensai_destroy(sensai_ctx* ctx);
 

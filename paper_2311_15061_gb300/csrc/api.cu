@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -113,10 +114,27 @@ sensai_status cuda_failure(sensai_ctx* ctx, cudaError_t e, const char* what, int
     return fail(st, "CUDA error %d (%s) at api.cu:%d in %s", (int)e, cudaGetErrorString(e), line, what);
 }
 
+// Host-side fault injection, for tests of the clean-up paths (no GPU fault):
+// with SENSAI_FAULT=alloc:N in the environment, the N-th device allocation
+// (1-based) of each sensai_create reports cudaErrorMemoryAllocation without
+// allocating.  Armed per call and per thread.
+thread_local int g_alloc_fault = 0;   // allocations left until the injected failure (0: none)
+
+struct FaultScope {
+    FaultScope()
+    {
+        g_alloc_fault = 0;
+        const char* f = getenv("SENSAI_FAULT");
+        if (f && strncmp(f, "alloc:", 6) == 0) g_alloc_fault = atoi(f + 6);
+    }
+    ~FaultScope() { g_alloc_fault = 0; }
+};
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t count)
 {
     *p = nullptr;
+    if (g_alloc_fault > 0 && --g_alloc_fault == 0) return cudaErrorMemoryAllocation;
     if (count == 0) count = 1;
     return cudaMalloc((void**)p, sizeof(T) * count);
 }
@@ -462,6 +480,7 @@ const char* sensai_last_error(void) { return g_last_error.c_str(); }
 sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensai_ctx** out)
 {
     g_last_error.clear();
+    const FaultScope faults;
     if (!prm || !mask || !out) return fail(SENSAI_EINVAL, "null argument");
     *out = nullptr;
     const sensai_params& p = *prm;

@@ -8,6 +8,10 @@
 * Checkpoint / resume: learning 3 iterations, exporting the state, importing
   it into a new context and learning 2 more gives bit for bit the state of 5
   uninterrupted iterations (the random numbers are counter-based).
+* Allocation failures, injected on the host (SENSAI_FAULT=alloc:N fails the
+  N-th device allocation of sensai_create as out of memory): every N gives
+  ENOMEM until N exceeds the allocations made, nothing leaks, and a context
+  created afterwards learns as a fresh one does.
 """
 import time
 
@@ -61,3 +65,38 @@ def test_checkpoint_resume_is_exact(lib):
     for key in ("D", "Z", "S", "pi"):
         np.testing.assert_array_equal(got[key], ref[key], err_msg=key)
     assert got["gamma_s"] == ref["gamma_s"] and got["gamma_eps"] == ref["gamma_eps"] and got["iter"] == ref["iter"]
+
+
+def test_injected_allocation_failures_free_everything(lib, monkeypatch):
+    import torch
+    prm, x, clean, mask = problem((64, 64), (8, 8), (1, 1), 16, 0.25, seed=2)
+    ref = gpu_context(prm, mask)          # warm-up: the CUDA context and module loads
+    ref.sensai_learn(x, 2)
+    want = ref.sensai_get_state()
+    ref.close()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    failed = 0
+    for n in range(1, 200):
+        monkeypatch.setenv("SENSAI_FAULT", f"alloc:{n}")
+        try:
+            ctx = gpu_context(prm, mask)
+        except lib.SensaiError as err:
+            assert err.status == lib.SENSAI_ENOMEM, (n, str(err))
+            failed += 1
+            continue
+        ctx.close()                       # n is past the last allocation
+        break
+    else:
+        raise AssertionError("creation never succeeded")
+    assert failed >= 10, failed
+    monkeypatch.delenv("SENSAI_FAULT")
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert abs(free1 - free0) < 64 << 20, (free0, free1)
+    ctx = gpu_context(prm, mask)
+    ctx.sensai_learn(x, 2)
+    got = ctx.sensai_get_state()
+    ctx.close()
+    for key in ("D", "Z", "S"):
+        np.testing.assert_array_equal(got[key], want[key], err_msg=key)
