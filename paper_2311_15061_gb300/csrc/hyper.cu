@@ -60,11 +60,6 @@ __device__ __forceinline__ void pi_body(const HyperArgs& a, const int k)
     }
 }
 
-__global__ void __launch_bounds__(256) pi_kernel(const HyperArgs a)
-{
-    pi_body(a, blockIdx.x);
-}
-
 // gamma_s and gamma_eps from fixed-order FP64 sums of the per-unit partials;
 // the two Gamma draws on two warps.  Last kernel of a batched iteration:
 // advances the replay iteration index.
@@ -100,11 +95,6 @@ __device__ __forceinline__ void gamma_body(const HyperArgs& a)
         a.sc->n_active = (long long)bc[2];
         if (a.t_dev) a.sc->t_iter = t_it + 1u;   // the next replay's iteration
     }
-}
-
-__global__ void __launch_bounds__(kHyperThreads) gamma_kernel(const HyperArgs a)
-{
-    gamma_body(a);
 }
 
 // Batched instances: pi draws with one CTA per (instance, atom), then the
@@ -177,8 +167,9 @@ cudaError_t launch_prior_s2(const Geom& g, const uint32_t* Zb, const DevScalars*
 // the s^2 sum, so the last CTA to publish its part (arrival counter, no
 // waiting) sums the counts in index order and draws it on a warp of its own,
 // then resets the counter.  Same sums in the same order and the same draw
-// counters as pi_kernel + gamma_kernel, so the values are identical; the
-// Gamma chains of the K + 2 draws run concurrently instead of in two rounds.
+// counters as the batched pi_multi_kernel + gamma_multi_kernel, so the values
+// are identical; the Gamma chains of the K + 2 draws run concurrently instead
+// of in two rounds.
 __global__ void __launch_bounds__(kHyperThreads) hyper_kernel(const HyperArgs a)
 {
     __shared__ int redi[kHyperThreads / 32];
