@@ -10,7 +10,9 @@ j > k) is then
 with xi the normal at counter (p, k, t, D).  The oracle computes the same
 draw from the running residual r + d_k w_k; the two must agree to rounding.
 The statistics here are built with dense numpy products over the
-patch-by-pixel matrices, independently of the oracle's loops.
+patch-by-pixel matrices, independently of the oracle's loops.  The same
+statistics give the residual energy behind the gamma_eps draw exactly:
+sum_i ||r_i||^2 = sum_p (X2_p - 2 d_p . Y_p + d_p^T C_p d_p).
 """
 import numpy as np
 
@@ -72,3 +74,29 @@ def _dense_form_unordered(prm, x, mask, D, Z, S, gamma_eps, t):
             lam = P + gamma_eps * C[p, k, k]
             Dn[k, p] = gamma_eps * A / lam + O.normal(prm.seed, [p, k, t, O.TAG_D]) / np.sqrt(lam)
     return Dn
+
+
+def test_residual_energy_from_the_statistics():
+    """sum_i ||r_i||^2 over observed pixels (the gamma_eps rate's sum, as the
+    oracle's hyper step computes it from the residuals) equals
+    sum_p (X2_p - 2 d_p . Y_p + d_p^T C_p d_p), X2_p = sum_{i in I_p} x_ip^2."""
+    rng = np.random.default_rng(45)
+    M, B, S, K = (10, 12), (3, 3), (1, 1), 6
+    prm = O.params(M, B, S, K, seed=45)
+    N, P = O.num_patches(prm), O.patch_size(prm)
+    mask = (rng.random(M) < 0.5).astype(np.uint8)
+    x = rng.standard_normal(M).astype(np.float32)
+    D = rng.standard_normal((K, P)) / np.sqrt(P)
+    Z = (rng.random((N, K)) < 0.4).astype(np.uint8)
+    Sv = rng.standard_normal((N, K)) * Z
+    st = O.State(prm, D=D, Z=Z, S=Sv, gamma_eps=1.0, t=0)
+    r2_oracle = O.hyper(st, x, mask)[2]
+    idx = O.patch_origins(prm)[:, None] + O.pixel_offsets(prm)[None, :]
+    X = x.reshape(-1)[idx].astype(np.float64)
+    Om = mask.reshape(-1)[idx].astype(np.float64)
+    W = Z * Sv
+    Y = np.einsum("ik,ip,ip->kp", W, Om, X)
+    C = np.einsum("ik,ij,ip->pkj", W, W, Om)
+    X2 = np.einsum("ip,ip->p", Om, X * X)
+    r2 = sum(X2[p] - 2 * D[:, p] @ Y[:, p] + D[:, p] @ C[p] @ D[:, p] for p in range(P))
+    assert abs(r2 - r2_oracle) <= 1e-10 * r2_oracle, (r2, r2_oracle)
