@@ -305,8 +305,10 @@ void sensai_batch_destroy(sensai_batch* b);
  * did not give up, SENSAI_EINVAL for another `which`.  Takes ~1 s. */
 sensai_status sensai_selftest_wait(int32_t which);
 
-/* Per-iteration metrics trace, the paper's live statistics and image-quality
- * monitoring as text.  path: a file opened for appending; NULL stops
+/* Per-iteration metrics trace: the live statistics, parameters and
+ * image-quality metrics that the paper's display window plots (abstract;
+ * Sec. "SenseAI: Feature Summary"), as text lines instead of plots.  path: a
+ * file opened for appending; NULL stops
  * tracing (and closes the file).  clean: NULL, or the ground-truth frame
  * (prod(M) floats, host or device; copied).  After every Gibbs iteration of
  * sensai_learn and sensai_inpaint the context appends one JSON line:
