@@ -338,10 +338,14 @@ sensai_status sensai_profile_read(sensai_ctx* ctx, double* ms, int64_t* counts);
  * device) is not allowed.  The paper has no counterpart; it computes the same
  * frame as sensai_reconstruct without a context.
  *  - params: frame / patch / stride geometry and K (the other fields are
- *    ignored); the same validity rules as sensai_create.
+ *    ignored); the same validity rules as sensai_create (P <= 1024, N and
+ *    prod(M) below 2^31), checked before anything touches the device.
  *  - D: K*P floats, S: N*K floats patch-major (S[i*K + k], 0 where atom k
- *    is inactive in patch i), out: prod(M) floats -- all device pointers on
- *    the current device, owned by the caller.
+ *    is inactive in patch i), out: prod(M) floats -- all device (or
+ *    managed) pointers on the current device, owned by the caller; host
+ *    memory and another GPU's memory are refused with SENSAI_EINVAL.  The
+ *    element counts cannot be checked from bare pointers: the caller
+ *    guarantees them.
  *  - Scratch is a fixed 16 MiB static device array (4,194,304 floats) that
  *    every GPU loading the library holds until exit; P * N above that is
  *    rejected with SENSAI_EINVAL.  No cudaMalloc / cudaFree is called.

@@ -121,14 +121,17 @@ sensai_status static_fail(sensai_status st, const char* msg)
     return st;
 }
 
-bool device_resident(const void* p)
+// Device memory of the current device dev, or managed memory.  Device memory
+// of another GPU is refused: without peer access a kernel touching it faults.
+bool device_resident(const void* p, int dev)
 {
     cudaPointerAttributes attr;
     if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    if (attr.type == cudaMemoryTypeManaged) return true;
+    return attr.type == cudaMemoryTypeDevice && attr.device == dev;
 }
 
 }  // namespace
@@ -148,11 +151,17 @@ extern "C" sensai_status sensai_reconstruct_static(const sensai_params* prm, con
     Geom g{};
     g.ndim = p.ndim;
     g.K = p.K;
+    // The same limits as sensai_create (N and the frame below 2^31, P at most
+    // 1024), checked as the products grow so that none of them can overflow
+    // and the grid sizes below fit in 32 bits.
+    const long long kLimit = 1LL << 31;
     long long P = 1, N = 1, nframe = 1;
     for (int d = 0; d < p.ndim; ++d) {
         if (p.M[d] < 1 || p.B[d] < 1 || p.B[d] > p.M[d] || p.stride[d] < 1 ||
             (p.M[d] - p.B[d]) % p.stride[d] != 0)
             return static_fail(SENSAI_EINVAL, "invalid frame / patch / stride geometry");
+        if (p.M[d] >= kLimit || nframe * p.M[d] >= kLimit)
+            return static_fail(SENSAI_EINVAL, "frame too large (2^31 pixels or more)");
         g.M[d] = p.M[d];
         g.B[d] = p.B[d];
         g.S[d] = p.stride[d];
@@ -160,8 +169,9 @@ extern "C" sensai_status sensai_reconstruct_static(const sensai_params* prm, con
         P *= p.B[d];
         N *= g.G[d];
         nframe *= p.M[d];
+        if (P > 1024) return static_fail(SENSAI_EINVAL, "patch size P exceeds 1024");
     }
-    if (P > 1024) return static_fail(SENSAI_EINVAL, "patch size P exceeds 1024");
+    if (N >= kLimit) return static_fail(SENSAI_EINVAL, "too many patches (2^31 or more)");
     if (P * N > kStaticScratchFloats)
         return static_fail(SENSAI_EINVAL,
                            "P x N exceeds the 4194304-float static scratch of sensai_reconstruct_static");
@@ -174,12 +184,11 @@ extern "C" sensai_status sensai_reconstruct_static(const sensai_params* prm, con
     g.N = N;
     g.NW = (int)((N + 31) / 32);
     g.nframe = nframe;
-    if (!device_resident(D) || !device_resident(S) || !device_resident(out))
-        return static_fail(SENSAI_EINVAL, "D, S and out must be device pointers");
-
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices)
         return static_fail(SENSAI_ECUDA, "no usable current CUDA device");
+    if (!device_resident(D, dev) || !device_resident(S, dev) || !device_resident(out, dev))
+        return static_fail(SENSAI_EINVAL, "D, S and out must be device pointers on the current device");
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return static_fail(SENSAI_ECUDA, "cudaDeviceGetAttribute failed");
     const int ldP = (g.P + 31) & ~31;

@@ -374,14 +374,38 @@ class Context:
         return st
 
 
+def _static_sizes(params):
+    """(P, N, frame pixels) of a sensai_params, as the C side computes them."""
+    P = N = nframe = 1
+    for d in range(params.ndim):
+        M, B, S = int(params.M[d]), int(params.B[d]), int(params.stride[d])
+        if M < 1 or B < 1 or B > M or S < 1 or (M - B) % S:
+            raise ValueError(f"dimension {d}: invalid frame / patch / stride geometry")
+        P *= B
+        N *= (M - B) // S + 1
+        nframe *= M
+    return P, N, nframe
+
+
 def sensai_reconstruct_static(params, D, S, out, stream=None):
     """Overlap-add reconstruction without any device allocation (device
-    tensors D: K x P, S: N x K patch-major, out: frame shape)."""
-    for name, t in (("D", D), ("S", S), ("out", out)):
-        if not (hasattr(t, "is_cuda") and t.is_cuda):
+    tensors on the current device: D K x P, S N x K patch-major, out the
+    frame shape).  The element counts are checked here, since the C side
+    receives bare pointers."""
+    P, N, nframe = _static_sizes(params)
+    K = int(params.K)
+    counts = (("D", D, K * P), ("S", S, N * K), ("out", out, nframe))
+    for name, t, n in counts:
+        if not hasattr(t, "numel"):
             raise TypeError(f"{name}: need a CUDA float32 tensor")
-    _check(_lib.sensai_reconstruct_static(ctypes.byref(params), _buf(D, np.float32, name="D"),
-                                          _buf(S, np.float32, name="S"), _buf(out, np.float32, name="out"),
+        if t.numel() != n:
+            raise ValueError(f"{name}: need {n} elements, got {t.numel()}")
+    import torch
+    for name, t, _ in counts:
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise TypeError(f"{name}: need a CUDA float32 tensor on the current device")
+    _check(_lib.sensai_reconstruct_static(ctypes.byref(params), _buf(D, np.float32, K * P, "D"),
+                                          _buf(S, np.float32, N * K, "S"), _buf(out, np.float32, nframe, "out"),
                                           _stream(stream)))
 
 

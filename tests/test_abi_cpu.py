@@ -75,3 +75,40 @@ def test_invalid_hyperparameters_rejected(lib):
 def test_null_context_is_an_error_not_a_crash(lib):
     assert lib._lib.sensai_learn(None, None, 1, None) == lib.SENSAI_EINVAL
     lib._lib.sensai_destroy(None)
+
+
+# --- sensai_reconstruct_static: the checks made before anything touches the device ---
+
+def _fake_ptr():
+    # never dereferenced: every case below is rejected during argument checks
+    return ctypes.c_void_p(256)
+
+
+@pytest.mark.parametrize("M,B,S,K,what", [
+    ((70000, 70000), (1, 1), (1, 1), 4, "frame too large"),       # 4.9e9 pixels >= 2^31
+    ((2100, 2100), (1, 1), (1, 1), 4, "static scratch"),          # P * N = 4.41 M floats > 4.19 M
+    ((40, 40), (33, 33), (1, 1), 4, "exceeds 1024"),              # P = 1089
+    ((10,), (4,), (4,), 8, "geometry"),                           # stride does not divide M - B
+])
+def test_static_reconstruction_rejects_before_device(lib, M, B, S, K, what):
+    prm = lib.make_params(M, B, S, K)
+    st = lib._lib.sensai_reconstruct_static(ctypes.byref(prm), _fake_ptr(), _fake_ptr(), _fake_ptr(), None)
+    assert st == lib.SENSAI_EINVAL
+    assert what in lib.sensai_last_error()
+
+
+def test_static_reconstruction_binding_checks_counts(lib):
+    """The C side gets bare pointers, so the binding checks every element count
+    (an undersized tensor would be read or written past its end)."""
+    import torch
+    M, B, S, K = (20, 18), (4, 3), (1, 1), 6
+    prm = lib.make_params(M, B, S, K)
+    P, N = 12, 17 * 16
+    good = dict(D=torch.zeros(K * P), S=torch.zeros(N * K), out=torch.zeros(M))
+    for name in good:
+        args = dict(good)
+        args[name] = torch.zeros(good[name].numel() - 1)
+        with pytest.raises(ValueError, match=name):
+            lib.sensai_reconstruct_static(prm, args["D"], args["S"], args["out"])
+    with pytest.raises(TypeError, match="CUDA"):   # right sizes, host memory
+        lib.sensai_reconstruct_static(prm, good["D"], good["S"], good["out"])

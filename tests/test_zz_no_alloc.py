@@ -32,10 +32,15 @@ def sensai():
     return s
 
 
-def test_static_reconstruction_matches_context_path(sensai):
+@pytest.mark.parametrize("M,B,S,K", [
+    ((96, 80), (8, 6), (1, 2), 24),          # 2-D, stride 2 on the last axis
+    ((6, 20, 21), (2, 4, 3), (2, 2, 3), 7),  # 3-D, strides on every axis
+    ((48, 40), (6, 5), (3, 5), 9),           # stride 5 on the last axis
+    ((263, 263), (8, 8), (1, 1), 12),        # P * N = 4,194,304: the whole static scratch
+])
+def test_static_reconstruction_matches_context_path(sensai, M, B, S, K):
     import torch
     from paper_2311_15061_gb300 import synth
-    M, B, S, K = (96, 80), (8, 6), (1, 2), 24
     mask = synth.random_mask(M, 0.3, 0)
     prm = sensai.make_params(M, B, S, K)
     ctx = sensai.Context(prm, mask)
@@ -62,7 +67,26 @@ def test_static_reconstruction_rejects_oversized_problems(sensai):
     import torch
     prm = sensai.make_params((2100, 2100), (1, 1), (1, 1), 4)   # P * N = 4.41 M floats > 4.19 M
     small = torch.zeros(16, dtype=torch.float32, device="cuda")
-    with pytest.raises(sensai.SensaiError) as err:
+    with pytest.raises(ValueError):   # the binding checks the element counts first
         sensai.sensai_reconstruct_static(prm, small, small, small)
-    assert err.value.status == sensai.SENSAI_EINVAL
+    import ctypes                     # the C side rejects the size before any launch
+    p = small.data_ptr()
+    st = sensai._lib.sensai_reconstruct_static(ctypes.byref(prm), p, p, p, None)
+    assert st == sensai.SENSAI_EINVAL
     assert "static scratch" in sensai.sensai_last_error()
+
+
+def test_static_reconstruction_rejects_host_memory(sensai):
+    """Host pointers reach the C side only through the raw ABI (the binding
+    refuses them earlier); the entry point rejects them without a launch."""
+    import ctypes
+    import torch
+    M, B, S, K = (20, 18), (4, 3), (1, 1), 6
+    prm = sensai.make_params(M, B, S, K)
+    D = torch.zeros(K * 12, device="cuda")
+    Sv = torch.zeros(17 * 16 * K, device="cuda")
+    host_out = np.zeros(M, np.float32)
+    st = sensai._lib.sensai_reconstruct_static(ctypes.byref(prm), D.data_ptr(), Sv.data_ptr(),
+                                               host_out.ctypes.data, None)
+    assert st == sensai.SENSAI_EINVAL
+    assert "current device" in sensai.sensai_last_error()
