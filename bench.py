@@ -46,7 +46,7 @@ UNIT = "patch·atom updates/s"
 #   60, log-odds / sigmoid / threshold: 15), 14 more when z = 1 (Box-Muller +
 #   weight), |Omega_i| FMAs when the weight changes (rank-1 residual update).
 OPS_FIXED, OPS_GAUSS = 75, 14
-SMS, LANES_PER_SM = 152, 128
+LANES_PER_SM = 128   # FP32 / INT32 lanes per SM (4 sub-partitions x 32)
 
 
 def _frame():
@@ -251,7 +251,8 @@ def run_gpu(args):
            + OPS_GAUSS * float(stats.active_draws))
     peaks, peak_src = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SMS * LANES_PER_SM * sm_mhz * 1e6 / 1e12   # T lane-ops/s
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = sms * LANES_PER_SM * sm_mhz * 1e6 / 1e12   # T lane-ops/s
     achieved = ops / sweep_n / (sweep_ms / sweep_n / 1e3) / 1e12
     traffic = _traffic_record(("sweep.cu", "sweep_block.cuh", "internal.cuh"))
 
@@ -285,7 +286,7 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "kernel": "sweep_kernel (code sweep)", "achieved": achieved,
                      "peak": peak, "unit": "T lane-ops/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz ({peak_src} max SM clock)",
+                     "peak_source": f"{sms} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz ({peak_src} max SM clock)",
                      "ms_per_launch": sweep_ms / sweep_n, "launches": sweep_n},
         "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "wall_s": wall,

@@ -77,6 +77,43 @@ def test_batch_equals_individual_learning(lib):
     assert batched[3].sensai_get_stats().slices >= 2   # the streamed instance really streamed
 
 
+@pytest.mark.parametrize("which", [0, 2])
+def test_batch_member_matches_oracle(lib, which):
+    """One batched Gibbs iteration of one member, from an oracle state,
+    against the oracle: the codes by the flip rule and 1e-5 on s; the
+    dictionary and then pi / gammas conditioned on the GPU's codes (and
+    dictionary), so that a near-threshold flip does not change the path."""
+    import oracle as O
+    from parity_helpers import (D_TOL, S_TOL, compare_codes, dict_errors, oracle_state, push_state,
+                                round_state)
+    c = CASES[which]
+    prm, x, clean, mask = problem(c["M"], c["B"], c["S"], c["K"], c["frac"], seed=c["seed"])
+    st = oracle_state(prm, x, mask, 2)
+    members = _contexts(lib)
+    ctx = members[which]
+    push_state(ctx, st, x)
+    b = lib.Batch(members)
+    b.sensai_batch_learn(1)
+    b.close()
+    g = ctx.sensai_get_state()
+    assert g["iter"] == st.t + 1
+    ost = st.copy()
+    _, L = O.zs_sweep_subset(ost, x, mask, want_logodds=True)
+    nflip, serr = compare_codes(st, g, ost, L)
+    assert nflip <= max(3, 1e-4 * ost.Z.shape[0]), nflip
+    assert serr <= S_TOL, serr
+    od = round_state(O.State(prm, D=st.D, Z=g["Z"], S=g["S"].astype(np.float64), pi=st.pi,
+                             gamma_s=st.gamma_s, gamma_eps=st.gamma_eps, t=st.t))
+    O.d_sweep(od, x, mask)
+    assert dict_errors(g["D"], od.D).max() <= D_TOL
+    oh = round_state(O.State(prm, D=g["D"].astype(np.float64), Z=g["Z"], S=g["S"].astype(np.float64),
+                             pi=st.pi, gamma_s=st.gamma_s, gamma_eps=st.gamma_eps, t=st.t))
+    O.hyper(oh, x, mask)
+    np.testing.assert_allclose(g["pi"], oh.pi, rtol=1e-9)
+    assert abs(g["gamma_s"] / oh.gamma_s - 1) <= 1e-9
+    assert abs(g["gamma_eps"] / oh.gamma_eps - 1) <= 1e-5
+
+
 def test_tuning_keeps_results(lib):
     batched, alone = _contexts(lib), _contexts(lib)
     b = lib.Batch(batched)

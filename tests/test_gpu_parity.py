@@ -128,7 +128,13 @@ def test_empty_mask_samples_the_prior():
     _, L = O.zs_sweep_subset(ost, x, mask, want_logodds=True)
     nflip, serr = compare_codes(st, g, ost, L)
     assert serr <= S_TOL
+    # every atom is drawn from its prior N(0, I/P) with the same normals
+    post = round_state(ost.copy())
+    push_state(ctx, post, x)
     ctx.sensai_draw_dictionary()
+    Dg = ctx.sensai_get_dictionary()
+    O.d_sweep(post, x, mask)
+    assert dict_errors(Dg, post.D).max() <= D_TOL
     ctx.close()
 
 
@@ -252,6 +258,19 @@ def test_full_size_dictionary_and_hyper(c2_state):
     ctx.close()
 
 
+def test_full_size_chain_dictionary(c2_state):
+    """The per-chain dictionary kernel at the full 512x512, K = 128 size."""
+    prm, x, mask, st = c2_state
+    ctx = gpu_context(prm, mask, _chain())
+    push_state(ctx, st, x)
+    ctx.sensai_draw_dictionary()
+    Dg = ctx.sensai_get_dictionary()
+    ctx.close()
+    od = st.copy()
+    O.d_sweep(od, x, mask)
+    assert dict_errors(Dg, od.D).max() <= D_TOL
+
+
 def test_full_size_reconstruct_and_counts(c2_state):
     prm, x, mask, st = c2_state
     ctx = gpu_context(prm, mask)
@@ -285,6 +304,35 @@ def test_device_buffers_and_streams():
             outs.append(ctx.sensai_reconstruct())
         ctx.close()
     np.testing.assert_array_equal(outs[0], outs[1])
+
+
+# --- the per-chain dictionary kernel (batches, P > 512, empty masks) ---
+
+def _chain():
+    from paper_2311_15061_gb300 import sensai
+    return sensai.SENSAI_FLAG_CHAIN_DICTIONARY
+
+
+def test_chain_dictionary_128x128_k64():
+    _phase_parity(**C1, flags=_chain())
+
+
+@pytest.mark.parametrize("case", [
+    dict(M=(37, 45), B=(5, 4), S=(1, 1), K=12, frac=0.3),
+    dict(M=(333,), B=(9,), S=(2,), K=5, frac=0.4),
+    dict(M=(6, 20, 21), B=(2, 4, 3), S=(2, 2, 3), K=7, frac=0.35),
+    dict(M=(20, 20), B=(4, 4), S=(1, 1), K=1, frac=0.5),
+    dict(M=(24, 24), B=(8, 8), S=(1, 1), K=16, frac=1.0, full_mask=True),
+    dict(M=(48, 40), B=(6, 5), S=(3, 5), K=9, frac=0.2),
+])
+def test_chain_dictionary_edge_geometries(case):
+    _phase_parity(**case, flags=_chain())
+
+
+def test_chain_dictionary_patch_above_512_pixels():
+    """P = 576 (24 x 24 patches): the space-organised kernel does not apply,
+    so the per-chain kernel runs without any flag."""
+    _phase_parity(M=(40, 36), B=(24, 24), S=(1, 1), K=12, frac=0.3, warm=1)
 
 
 # --- streamed dictionary: the code sweep with the dictionary in atom slices ---
