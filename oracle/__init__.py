@@ -112,6 +112,7 @@ def lib():
         "orc_d_sweep": (None, [pp, P(f32), P(u8), P(dbl), P(u8), P(dbl), dbl, i64]),
         "orc_hyper": (None, [pp, P(f32), P(u8), P(dbl), P(u8), P(dbl), P(dbl), P(dbl), P(dbl), i64, P(dbl)]),
         "orc_reconstruct": (None, [pp, P(dbl), P(u8), P(dbl), P(dbl)]),
+        "orc_reconstruct_mean": (None, [pp, ctypes.c_int, P(dbl), P(u8), P(dbl), P(dbl)]),
         "orc_num_threads": (ctypes.c_int, []),
     }
     for name, (res, args) in sig.items():
@@ -280,6 +281,20 @@ def reconstruct(st):
     out = np.zeros(shape, dtype=np.float64)
     lib().orc_reconstruct(ctypes.byref(st.prm), _p(st.D, ctypes.c_double), _p(st.Z, ctypes.c_uint8),
                           _p(st.S, ctypes.c_double), _p(out, ctypes.c_double))
+    return out
+
+
+def reconstruct_mean(states):
+    """Posterior-mean reconstruction: the mean of the overlap-add
+    reconstructions of the given samples (states of one chain)."""
+    prm = states[0].prm
+    shape = tuple(prm.M[i] for i in range(prm.ndim))
+    D = np.ascontiguousarray(np.stack([st.D for st in states]), np.float64)
+    Z = np.ascontiguousarray(np.stack([st.Z for st in states]), np.uint8)
+    S = np.ascontiguousarray(np.stack([st.S for st in states]), np.float64)
+    out = np.zeros(shape, dtype=np.float64)
+    lib().orc_reconstruct_mean(ctypes.byref(prm), len(states), _p(D, ctypes.c_double), _p(Z, ctypes.c_uint8),
+                               _p(S, ctypes.c_double), _p(out, ctypes.c_double))
     return out
 
 

@@ -522,6 +522,25 @@ void orc_reconstruct(const orc_params* prm, const double* D, const uint8_t* Z,
     free(counts);
 }
 
+/* Posterior-mean reconstruction over T samples of the chain: the mean of the
+ * T overlap-add reconstructions, sample t given by D + t K P, Z + t N K and
+ * S + t N K. */
+void orc_reconstruct_mean(const orc_params* prm, int T, const double* D, const uint8_t* Z, const double* S,
+                          double* out)
+{
+    const int64_t N = orc_num_patches(prm), P = orc_patch_size(prm);
+    const int64_t nf = orc_frame_size(prm);
+    const int64_t K = prm->K;
+    double* one = malloc(sizeof(double) * nf);
+    for (int64_t u = 0; u < nf; ++u) out[u] = 0.0;
+    for (int t = 0; t < T; ++t) {
+        orc_reconstruct(prm, D + (int64_t)t * K * P, Z + (int64_t)t * N * K, S + (int64_t)t * N * K, one);
+        for (int64_t u = 0; u < nf; ++u) out[u] += one[u];
+    }
+    for (int64_t u = 0; u < nf; ++u) out[u] = T > 0 ? out[u] / T : 0.0;
+    free(one);
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

@@ -143,6 +143,12 @@ void orc_hyper(const orc_params* prm, const float* x, const uint8_t* mask,
 void orc_reconstruct(const orc_params* prm, const double* D, const uint8_t* Z,
                      const double* S, double* out);
 
+/* Posterior-mean reconstruction over the last T samples of a chain: the mean
+ * of the T overlap-add reconstructions (samples stacked: D is T x K x P, Z and
+ * S are T x N x K). */
+void orc_reconstruct_mean(const orc_params* prm, int T, const double* D, const uint8_t* Z, const double* S,
+                          double* out);
+
 /* Number of OpenMP threads the sweeps use. */
 int orc_num_threads(void);
 
