@@ -9,7 +9,13 @@ oracle):
   the oracle's uniform lies within 2^20 of its threshold floor(sigmoid(L) 2^32)
   (an FP32 log-odds error of ~1e-3 near L = 0); the rest of that patch's sweep
   then follows a different path and is excluded;
-* s: per patch ||s_gpu - s_oracle|| <= 1e-5 max(||s_oracle||, 1e-3);
+* s: per patch ||s_gpu - s_oracle|| <= 1e-5 max(||s_oracle||, 1e-2).  The
+  floor is where "1e-5 relative in FP32" stops being attainable: the FP32
+  residual x - D w of frames with values up to 1 carries ~2^-24 absolute
+  rounding per pixel, which reaches the conditional mean of s as ~1e-7
+  absolute; an emulation of the FP32 sweep in any summation order puts
+  patches with ||s_i|| ~ 1.6e-3 at 2-4e-5 relative, and every patch within
+  7e-6 of 1e-5 max(||s_i||, 1e-2);
 * d: per atom ||d_gpu - d_oracle|| <= 1e-5 ||d_oracle||;
 * pi, gamma_s: 1e-9 relative (FP64 draws from identical integer / FP64 sums);
   gamma_eps: 1e-5 relative (its residual energy comes from FP32 residuals).
@@ -22,6 +28,7 @@ import oracle as O
 from paper_2311_15061_gb300 import synth
 
 S_TOL = 1e-5
+S_FLOOR = 1e-2
 D_TOL = 1e-5
 Z_MARGIN = 2 ** 20
 
@@ -88,7 +95,7 @@ def compare_codes(st_before, g, ost, L, patches=None):
     keep[flip_patches] = False
     sg = g["S"][idx][keep].astype(np.float64)
     so = ost.S[idx][keep]
-    err = np.linalg.norm(sg - so, axis=1) / np.maximum(np.linalg.norm(so, axis=1), 1e-3)
+    err = np.linalg.norm(sg - so, axis=1) / np.maximum(np.linalg.norm(so, axis=1), S_FLOOR)
     return len(flip_patches), float(err.max(initial=0.0))
 
 
