@@ -293,7 +293,7 @@ def run_gpu(args):
         "clocks": clocks.summary(),
     }
     if not args.no_serving:
-        line["serving"] = run_serving(ctx)
+        line["serving"] = run_serving(ctx, dict(B=w["B"], S=w["S"], K=w["K"], seed=w["seed"] + rank))
     if not args.no_video:
         line["video3d"] = run_video3d()
     if not args.no_batch:
@@ -308,37 +308,48 @@ def run_gpu(args):
 
 
 SERVE = dict(frames=300, sizes=((256, 256), (512, 512), (1024, 1024)), streams=4, rate_hz=20.0,
-             frac=(0.05, 0.20), sweeps=3, slots=8, saturated_1024=32, seed=7)
+             frac=(0.05, 0.20), sweeps=3, slots=8, closed_1024=48, overload_hz=100.0, overload_frames=400,
+             overload_budget_1024=4, psnr_1024=4, seed=7)
+
+_MASK64 = (1 << 64) - 1
 
 
-def _serving_requests(cfg):
+def _splitmix64(x):
+    """SplitMix64's finaliser (Steele, Lea, Flood 2014): the serving engine keys
+    each frame's draws with h(h(h(seed) ^ stream) ^ frame)."""
+    z = (x + 0x9E3779B97F4A7C15) & _MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+    return z ^ (z >> 31)
+
+
+def _serving_requests(cfg, rate_hz, frames, seed):
     """The live-feed workload: frames of mixed sizes from a drifting-lattice
     pool, each with its own random or line-hop mask (5-20%), arriving as four
     Poisson streams."""
     from paper_2311_15061_gb300 import synth
-    rng = np.random.default_rng(cfg["seed"])
-    pool = {shp: [synth.stem_frame(shp, cfg["seed"] + j, drift=(0.0, 0.3 * j))[0] for j in range(3)]
+    rng = np.random.default_rng(seed)
+    pool = {shp: [synth.stem_frame(shp, cfg["seed"] + j, drift=(0.0, 0.3 * j)) for j in range(3)]
             for shp in cfg["sizes"]}
     reqs = []
     t_stream = np.zeros(cfg["streams"])
-    for n in range(cfg["frames"]):
+    for n in range(frames):
         sid = n % cfg["streams"]
-        t_stream[sid] += rng.exponential(1.0 / cfg["rate_hz"])
+        t_stream[sid] += rng.exponential(1.0 / rate_hz)
         shp = cfg["sizes"][int(rng.integers(0, len(cfg["sizes"])))]
         frac = float(rng.uniform(*cfg["frac"]))
-        mask = (synth.random_mask(shp, frac, cfg["seed"] + n) if n % 2 == 0
-                else synth.line_hop_mask(shp, frac, cfg["seed"] + n))
+        mask = (synth.random_mask(shp, frac, seed + n) if n % 2 == 0
+                else synth.line_hop_mask(shp, frac, seed + n))
         reqs.append(dict(t=float(t_stream[sid]), stream=sid, frame_id=n, shape=shp,
-                         x=pool[shp][n % 3], mask=mask))
+                         x=pool[shp][n % 3][0], mask=mask))
     reqs.sort(key=lambda r: r["t"])
     return reqs, pool
 
 
-def run_serving(ctx, cfg=SERVE):
-    """Open-loop live serving (Poisson arrivals) and a back-to-back 1024^2 run."""
+def _open_loop(ctx, reqs, cfg, id_base):
+    """Submits each request at its arrival time; returns the latencies (ms,
+    submission to completion callback), achieved frames/s and per-size stats."""
     import threading
-    reqs, pool = _serving_requests(cfg)
-    ctx.sensai_serve_start(slots=cfg["slots"], max_pixels=max(a * b for a, b in cfg["sizes"]), max_observed=64)
     lock = threading.Lock()
     finished = {}
 
@@ -346,56 +357,143 @@ def run_serving(ctx, cfg=SERVE):
         with lock:
             finished[fid] = (time.perf_counter(), status)
 
-    # warm-up: one frame of each size
-    for j, shp in enumerate(cfg["sizes"]):
-        from paper_2311_15061_gb300 import synth
-        ctx.sensai_submit_frame(9, 10_000_000 + j, pool[shp][0], synth.random_mask(shp, 0.1, j), cfg["sweeps"],
-                                done=on_done)
-    ctx.sensai_serve_drain()
-    finished.clear()
-
     submitted = {}
     t0 = time.perf_counter()
     for r in reqs:
         delay = t0 + r["t"] - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        submitted[r["frame_id"]] = (t0 + r["t"], r["shape"])
-        ctx.sensai_submit_frame(r["stream"], r["frame_id"], r["x"], r["mask"], cfg["sweeps"], done=on_done)
+        fid = id_base + r["frame_id"]
+        submitted[fid] = (time.perf_counter(), r["shape"])
+        ctx.sensai_submit_frame(r["stream"], fid, r["x"], r["mask"], cfg["sweeps"], done=on_done)
     ctx.sensai_serve_drain()
     t_end = max(v[0] for v in finished.values())
     lat = {fid: 1e3 * (finished[fid][0] - submitted[fid][0]) for fid in submitted}
-    ok = all(finished[fid][1] == 0 for fid in submitted)
     all_lat = np.array(list(lat.values()))
     by_size = {}
     for shp in cfg["sizes"]:
         v = np.array([lat[f] for f, (_, s_) in submitted.items() if s_ == shp])
-        by_size[f"{shp[0]}x{shp[1]}"] = {"frames": int(len(v)), "p50_ms": float(np.percentile(v, 50)),
-                                         "p99_ms": float(np.percentile(v, 99))}
-    mixed = {"frames": len(reqs), "offered_hz": cfg["rate_hz"] * cfg["streams"],
-             "fps": len(reqs) / (t_end - t0), "p50_ms": float(np.percentile(all_lat, 50)),
-             "p99_ms": float(np.percentile(all_lat, 99)), "by_size": by_size, "all_ok": bool(ok)}
+        if len(v):
+            by_size[f"{shp[0]}x{shp[1]}"] = {"frames": int(len(v)), "p50_ms": float(np.percentile(v, 50)),
+                                             "p99_ms": float(np.percentile(v, 99))}
+    return {"frames": len(reqs), "fps": len(reqs) / (t_end - t0), "p50_ms": float(np.percentile(all_lat, 50)),
+            "p99_ms": float(np.percentile(all_lat, 99)), "by_size": by_size,
+            "all_ok": all(finished[f][1] == 0 for f in submitted)}
 
-    # live 1024^2 feed, back to back: throughput with every slot busy
+
+def _serve_psnr(ctx, cfg, params, state):
+    """PSNR of served 1024^2 frames against the clean frame, and whether each
+    equals sensai_inpaint on a context keyed by the frame's own seed."""
+    from paper_2311_15061_gb300 import sensai, synth
+    import threading
     big = cfg["sizes"][-1]
-    finished.clear()
+    res = []
+    done = threading.Event()
+    for j in range(cfg["psnr_1024"]):
+        x, clean = synth.stem_frame(big, cfg["seed"] + 100 + j, drift=(0.0, 0.3 * j))
+        m = synth.random_mask(big, 0.1, 900 + j)
+        done.clear()
+        out = ctx.sensai_submit_frame(2, 30_000_000 + j, x, m, cfg["sweeps"], done=lambda f, st, o: done.set())
+        ctx.sensai_serve_drain()
+        fseed = _splitmix64(_splitmix64(_splitmix64(params["seed"]) ^ 2) ^ (30_000_000 + j))
+        c2 = sensai.Context(sensai.make_params(big, params["B"], params["S"], params["K"], seed=fseed), m)
+        c2.sensai_set_state(D=state["D"], pi=state["pi"], gamma_s=state["gamma_s"], gamma_eps=state["gamma_eps"],
+                            iter=state["iter"])
+        ref = np.empty(big, np.float32)
+        c2.sensai_inpaint(x, cfg["sweeps"], ref)
+        c2.close()
+
+        def psnr(a, b):
+            mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+            return 10.0 * np.log10(1.0 / mse)
+        res.append({"psnr_served_vs_clean_db": psnr(out, clean), "psnr_noisy_frame_vs_clean_db": psnr(x, clean),
+                    "equals_inpaint": bool(np.array_equal(out, ref))})
+    return {"frames": len(res), "mask": "10% Bernoulli", "mean_psnr_served_vs_clean_db":
+            float(np.mean([r["psnr_served_vs_clean_db"] for r in res])),
+            "mean_psnr_noisy_frame_vs_clean_db": float(np.mean([r["psnr_noisy_frame_vs_clean_db"] for r in res])),
+            "all_equal_inpaint": all(r["equals_inpaint"] for r in res)}
+
+
+def run_serving(ctx, params, cfg=SERVE):
+    """Live serving: an open-loop Poisson load, a closed loop at 1024^2 with
+    every slot busy (per-frame latency), an offered load above capacity under
+    a memory budget, and the PSNR of served frames."""
+    import threading
     from paper_2311_15061_gb300 import synth
-    masks = [synth.random_mask(big, 0.1, 500 + j) for j in range(cfg["saturated_1024"])]
+    state = ctx.sensai_get_state()
+    big = cfg["sizes"][-1]
+    ctx.sensai_serve_start(slots=cfg["slots"], max_pixels=big[0] * big[1], max_observed=64)
+    # warm-up: one frame of each size
+    for j, shp in enumerate(cfg["sizes"]):
+        x, _ = synth.stem_frame(shp, cfg["seed"] + 50 + j)
+        ctx.sensai_submit_frame(9, 10_000_000 + j, x, synth.random_mask(shp, 0.1, j), cfg["sweeps"])
+    ctx.sensai_serve_drain()
+
+    reqs, pool = _serving_requests(cfg, cfg["rate_hz"], cfg["frames"], cfg["seed"])
+    mixed = _open_loop(ctx, reqs, cfg, 0)
+    mixed["offered_hz"] = cfg["rate_hz"] * cfg["streams"]
+
+    # closed loop at 1024^2: a new frame as soon as one completes, `slots` in flight
+    lock = threading.Lock()
+    cv = threading.Condition(lock)
+    t_done = {}
+    masks = [synth.random_mask(big, 0.1, 500 + j) for j in range(8)]
+    frames_big = [v[0] for v in pool[big]]
+
+    def on_done(fid, status, out):
+        with cv:
+            t_done[fid] = (time.perf_counter(), status)
+            cv.notify()
+
+    t_sub = {}
+    n = cfg["closed_1024"]
     t1 = time.perf_counter()
-    for j in range(cfg["saturated_1024"]):
-        ctx.sensai_submit_frame(j % cfg["streams"], 20_000_000 + j, pool[big][j % 3], masks[j], cfg["sweeps"],
+    for j in range(n):
+        with cv:
+            while j - len(t_done) >= cfg["slots"]:
+                cv.wait()
+        t_sub[20_000_000 + j] = time.perf_counter()
+        ctx.sensai_submit_frame(j % cfg["streams"], 20_000_000 + j, frames_big[j % 3], masks[j % 8], cfg["sweeps"],
                                 done=on_done)
     ctx.sensai_serve_drain()
-    t2 = max(v[0] for v in finished.values())
-    lat_big = np.array([1e3 * (v[0] - t1) for v in finished.values()])
+    t2 = max(v[0] for v in t_done.values())
+    lat = np.array([1e3 * (t_done[f][0] - t_sub[f]) for f in t_sub])
+    closed = {"frames": n, "in_flight": cfg["slots"], "fps": n / (t2 - t1),
+              "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+              "all_ok": all(v[1] == 0 for v in t_done.values())}
+    psnr = _serve_psnr(ctx, cfg, params, state)
     ctx.sensai_serve_stop()
-    sat = {"frames": cfg["saturated_1024"], "fps": cfg["saturated_1024"] / (t2 - t1),
-           "p50_completion_ms": float(np.percentile(lat_big, 50)),
-           "all_ok": all(v[1] == 0 for v in finished.values())}
-    return {"workload": ("300 frames, sizes 256^2/512^2/1024^2, random or line-hop masks 5-20%, "
-                         "4 Poisson streams x 20 Hz, 3 code sweeps + pi/gamma draws per frame, "
-                         "K=128 10x10 dictionary transferred from the learning step, 8 slots"),
-            "mixed": mixed, "live_1024_back_to_back": sat}
+
+    # above capacity: 4 streams x overload_hz, memory budget of a few 1024^2 frames
+    ctx.sensai_serve_start(slots=cfg["slots"], max_pixels=big[0] * big[1], max_observed=64,
+                           memory_budget=_frame_footprint(params, big) * cfg["overload_budget_1024"])
+    for j, shp in enumerate(cfg["sizes"]):
+        x, _ = synth.stem_frame(shp, cfg["seed"] + 60 + j)
+        ctx.sensai_submit_frame(9, 11_000_000 + j, x, synth.random_mask(shp, 0.1, j), cfg["sweeps"])
+    ctx.sensai_serve_drain()
+    oreqs, _ = _serving_requests(cfg, cfg["overload_hz"], cfg["overload_frames"], cfg["seed"] + 1)
+    over = _open_loop(ctx, oreqs, cfg, 40_000_000)
+    over["offered_hz"] = cfg["overload_hz"] * cfg["streams"]
+    over["memory_budget_bytes"] = _frame_footprint(params, big) * cfg["overload_budget_1024"]
+    ctx.sensai_serve_stop()
+    return {"workload": ("frames of 256^2/512^2/1024^2, random or line-hop masks 5-20%, 3 code sweeps + pi/gamma "
+                         "draws per frame, K=128 10x10 dictionary transferred from the learning step, 8 slots"),
+            "mixed_4x20hz": mixed, "closed_loop_1024": closed, "overload": over, "psnr_1024": psnr}
+
+
+def _frame_footprint(params, shape):
+    """Device bytes the serving engine charges a frame of this shape (the
+    engine's own accounting is in csrc/serve.cu; this mirrors its terms:
+    frame, mask, output, per-patch tables, weights and activity bits)."""
+    P = int(np.prod(params["B"]))
+    N = int(np.prod([(m - b) // s + 1 for m, b, s in zip(shape, params["B"], params["S"])]))
+    K = params["K"]
+    npx = int(np.prod(shape))
+    NW = (N + 31) // 32
+    KB = (K + 7) // 8
+    max_observed = 64
+    return int(8 * npx + npx + 4 * ((npx + 31) // 32) + 2 * N * (1 + max_observed) + 4 * KB * 8 * NW * 32
+               + 4 * K * NW + 32 * NW + 4 * P * N)
 
 
 VIDEO = dict(M=(32, 256, 256), B=(4, 8, 8), S=(2, 1, 1), K=256, frac=0.15, iters=30, seed=0)

@@ -68,8 +68,19 @@ typedef enum {
  * in any patch (above 96 a patch's pixels are split over a lane pair).  a <= 0 selects a = K and
  * b <= 0 selects b = N / 8 (N = number of patches).  c..f > 0.  flags:
  * SENSAI_FLAG_CHAIN_DICTIONARY, SENSAI_FLAG_STREAM_DICTIONARY, and with the
- * latter SENSAI_SLICE_ATOMS(n), SENSAI_FLAG_GAMMA_S_FULL; other bits are
- * EINVAL.
+ * latter SENSAI_SLICE_ATOMS(n), SENSAI_FLAG_GAMMA_S_FULL,
+ * SENSAI_FLAG_DENSE_STATISTICS, SENSAI_FLAG_TF32_STATISTICS; other bits
+ * are EINVAL.
+ *
+ * The dictionary draw (BPFA section, the dictionary-learning step) takes one
+ * of three forms, all the same atom-ordered conditionals: by default the
+ * residual form, atoms in blocks of 8 over the residual of every observed
+ * pixel (the space-organised cooperative kernel); SENSAI_FLAG_CHAIN_DICTIONARY
+ * the residual form with one CTA per pixel; SENSAI_FLAG_DENSE_STATISTICS
+ * (K <= 128) the dense-statistics form -- per within-patch pixel p the Gram
+ * C_p = sum w_i w_i^T and the correlations Y_p = sum w_i x_ip over the
+ * patches observing p, contracted on the tensor cores, then the draws in
+ * FP64 from C_p, Y_p and the current dictionary.
  *
  * The code sweep keeps the whole dictionary in shared memory when
  * (P + 1) * (K rounded up to 8, odd) floats fit (K = 128, P = 100: 52 KB);
@@ -96,6 +107,16 @@ typedef enum {
  * sensai_set_state with no sweep since sums the stored (active) weights.
  * One extra kernel per code sweep; not accepted by sensai_batch_create. */
 #define SENSAI_FLAG_GAMMA_S_FULL 0x4
+/* The dense-statistics form of the dictionary draw (tensor-core Grams, FP32
+ * level: head/tail TF32 split).  Requires K <= 128 (else EINVAL); not with
+ * SENSAI_FLAG_CHAIN_DICTIONARY. */
+#define SENSAI_FLAG_DENSE_STATISTICS 0x8
+/* The dense-statistics form at reduced precision: the Grams C_p from the
+ * TF32 heads of the weights alone (one tensor-core product instead of the
+ * head/tail split that gives FP32-level sums); relative error of C_p about
+ * 2^-11, of the drawn atoms about 1e-3.  Everything else is unchanged
+ * (correlations Y_p in FP32, sums and draws in FP64). */
+#define SENSAI_FLAG_TF32_STATISTICS 0x10
 #define SENSAI_SLICE_ATOMS(n) ((((n) / 8) & 0xff) << 8)
 typedef struct {
     int32_t ndim;
@@ -194,6 +215,23 @@ sensai_status sensai_draw_hyper(sensai_ctx* ctx, void* stream);
  * it of (D w_i) at that pixel, observed pixels included (the reconstruction
  * of Sec. "Time-To-Solution").  `out`: prod(M) floats, host or device. */
 sensai_status sensai_reconstruct(sensai_ctx* ctx, float* out, void* stream);
+
+/* Posterior-mean reconstruction over several samples of the chain (the
+ * reconstructions of Sec. "Time-To-Solution" are built from the sampler's
+ * draws; averaging the last T samples estimates the posterior mean of the
+ * image instead of showing one draw).
+ *  - sensai_mean_reset: empties the running sum (asynchronous on `stream`);
+ *  - sensai_mean_add: adds the overlap-add reconstruction of the current
+ *    state (as sensai_reconstruct would return it), in FP64, and counts it;
+ *    typically called after each of the last T iterations of sensai_learn
+ *    (iters = 1 per call) or sweeps of sensai_inpaint;
+ *  - sensai_mean_read: writes the running sum / count to `out` (prod(M)
+ *    floats, host or device).  SENSAI_ESTATE when nothing was added since
+ *    the last reset.
+ * The running sum (8 bytes per pixel) is allocated with the context. */
+sensai_status sensai_mean_reset(sensai_ctx* ctx, void* stream);
+sensai_status sensai_mean_add(sensai_ctx* ctx, void* stream);
+sensai_status sensai_mean_read(sensai_ctx* ctx, float* out, void* stream);
 
 /* Number of patches covering each pixel (int32, prod(M), host or device):
  * per dimension floor(min(y, last) / S) - ceil(max(0, y - B + 1) / S) + 1

@@ -55,6 +55,8 @@ struct sensai_ctx {
     bool ge_set = false;
     bool codes_valid = false;   // m / part_s2 describe the current codes
     bool resid_valid = false;   // R / part_r2 describe the current residual
+    bool resid_fresh = false;   // R is x - D W rebuilt from the state (what a code sweep starts from)
+    bool r2_valid = false;      // part_r2 holds the current residual energy (for the gamma_eps draw)
     int n_r2 = 0;               // valid entries of part_r2
     int n_s2 = 0;               // valid entries of part_s2
     bool broken = false;
@@ -93,7 +95,23 @@ struct sensai_ctx {
     double* ge_part = nullptr;  // scratch of the initial gamma_eps
     unsigned int* chunk_counter = nullptr;
     DevScalars* sc = nullptr;
-    int* pos = nullptr;         // [maxobs][N] residual position of each observed pixel of each patch
+    int* pos = nullptr;         // [maxobs][N] residual position of each observed pixel, by sweep slot
+    int* perm = nullptr;        // [Npad] sweep slot -> patch: decreasing |Omega_i| (obs, nobs, pos, Zb by slot)
+    // dense-statistics dictionary draw (gram.cu), when it applies
+    bool gram = false;
+    bool xlist_valid = false;   // Xlist holds the current frame's values
+    float* Xlist = nullptr;     // frame value of every (pixel, observing patch) entry of Ilist
+    int4* items = nullptr;      // work items: segments of the per-pixel patch lists
+    long long n_items = 0;
+    int gram_grid = 0;
+    float* Cpart = nullptr;     // [items][128][128]
+    float* Ypart = nullptr;     // [items][4][128]
+    double* C64 = nullptr;      // [P][128][128]
+    double* Y64 = nullptr;      // [P][128]
+    int* pitem_start = nullptr; // [P + 1]
+    int* pitem_idx = nullptr;   // [items]
+    double* mean_acc = nullptr; // [nframe] running sum of reconstructions (sensai_mean_*)
+    long long mean_count = 0;   // reconstructions in mean_acc
     bool t_on_device = false;   // kernels read the iteration index from sc->t_iter (graph capture)
     DictSpacePlan ds{};         // space-organised dictionary sweep (cooperative launch), when it runs
     ServeEngine* serve = nullptr;   // live serving engine, when started
@@ -153,7 +171,9 @@ void free_all(sensai_ctx* c)
 {
     void* ptrs[] = {c->mask_bits, c->imgoff, c->nobs, c->obs, c->Ibits, c->Ipre, c->Icnt, c->Rbase, c->Ilist,
                     c->misc, c->x, c->D, c->W, c->Zb, c->R, c->Y, c->out, c->pi, c->lpi, c->m,
-                    c->part_s2, c->part_r2, c->chunk_counter, c->sc, c->pos, c->Dsl, c->ge_part, c->Dc};
+                    c->part_s2, c->part_r2, c->chunk_counter, c->sc, c->pos, c->Dsl, c->ge_part, c->Dc,
+                    c->perm, c->mean_acc, c->Xlist, c->items, c->Cpart, c->Ypart, c->pitem_start,
+                    c->pitem_idx, c->C64, c->Y64};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ds_free(&c->ds);
@@ -217,7 +237,10 @@ sensai_status copy_frame(sensai_ctx* ctx, const float* frame, cudaStream_t s)
     SENSAI_CUDA(ctx, cudaMemcpyAsync(ctx->x, frame, bytes, kind, s));
     if (kind == cudaMemcpyHostToDevice) SENSAI_CUDA(ctx, cudaStreamSynchronize(s));
     ctx->frame_set = true;
+    ctx->xlist_valid = false;
     ctx->resid_valid = false;
+    ctx->resid_fresh = false;
+    ctx->r2_valid = false;
     return SENSAI_OK;
 }
 
@@ -230,21 +253,48 @@ sensai_status ensure_gamma_eps(sensai_ctx* ctx, cudaStream_t s)
     return SENSAI_OK;
 }
 
+// R and part_r2 <- the residual x - D W rebuilt from the state.
+// With the dictionary resident in shared memory this is the sweep's own
+// rebuild (rebuild_kernel); a streamed dictionary takes residual_kernel, the
+// same fused multiply-adds in the same order.
+SweepArgs sweep_args(const sensai_ctx* ctx);
+
+sensai_status rebuild_residual(sensai_ctx* ctx, cudaStream_t s)
+{
+    const SweepPlan& plan = ctx->sweep_plan;
+    if (plan.slice_atoms == 0 && plan.grid > 0) {
+        SENSAI_CUDA(ctx, launch_rebuild(sweep_args(ctx), ctx->maxobs, plan.grid, s));
+        ctx->n_r2 = ctx->g.NW * plan.lanes;
+    } else {
+        SENSAI_CUDA(ctx, launch_residual(ctx->g, ctx->x, ctx->obs, ctx->nobs, ctx->perm, ctx->imgoff, ctx->D,
+                                         ctx->W, ctx->pos, ctx->R, ctx->part_r2, s));
+        ctx->n_r2 = ctx->g.NW;
+    }
+    ctx->launches += 1;
+    ctx->resid_valid = true;
+    ctx->resid_fresh = true;
+    ctx->r2_valid = true;
+    return SENSAI_OK;
+}
+
+// part_r2 describes the current residual (as the last phase left it, or rebuilt).
+sensai_status ensure_r2(sensai_ctx* ctx, cudaStream_t s)
+{
+    if (ctx->r2_valid) return SENSAI_OK;
+    return rebuild_residual(ctx, s);
+}
+
+// The current residual in R (as the last phase left it, or rebuilt).
 sensai_status ensure_residual(sensai_ctx* ctx, cudaStream_t s)
 {
     if (ctx->resid_valid) return SENSAI_OK;
-    SENSAI_CUDA(ctx, launch_residual(ctx->g, ctx->x, ctx->obs, ctx->nobs, ctx->imgoff, ctx->D, ctx->W, ctx->Zb,
-                                     ctx->pos, ctx->R, ctx->part_r2, s));
-    ctx->launches += 1;
-    ctx->resid_valid = true;
-    ctx->n_r2 = ctx->g.NW;
-    return SENSAI_OK;
+    return rebuild_residual(ctx, s);
 }
 
 sensai_status ensure_code_stats(sensai_ctx* ctx, cudaStream_t s)
 {
     if (ctx->codes_valid) return SENSAI_OK;
-    SENSAI_CUDA(ctx, launch_code_stats(ctx->g, ctx->W, ctx->Zb, ctx->m, ctx->part_s2, s));
+    SENSAI_CUDA(ctx, launch_code_stats(ctx->g, ctx->W, ctx->Zb, ctx->perm, ctx->m, ctx->part_s2, s));
     ctx->launches += 1;
     ctx->codes_valid = true;
     ctx->n_s2 = ctx->g.NW;
@@ -258,6 +308,7 @@ SweepArgs sweep_args(const sensai_ctx* ctx)
     a.x = ctx->x;
     a.obs = ctx->obs;
     a.nobs = ctx->nobs;
+    a.perm = ctx->perm;
     a.imgoff = ctx->imgoff;
     a.D = ctx->D;
     a.W = ctx->W;
@@ -326,23 +377,71 @@ sensai_status run_sweep(sensai_ctx* ctx, cudaStream_t s)
     if (!ctx->frame_set) return fail(SENSAI_ESTATE, "no frame: call sensai_set_frame or pass a frame");
     sensai_status st = ensure_gamma_eps(ctx, s);
     if (st != SENSAI_OK) return st;
-    const SweepArgs a = sweep_args(ctx);
+    SweepArgs a = sweep_args(ctx);
+    if (ctx->R) {
+        // the sweep starts from the residual rebuilt from the state (the
+        // phases before it leave R updated incrementally): its bits depend on
+        // the state alone, as for a sweep that rebuilds it itself
+        if (!ctx->resid_fresh && (st = rebuild_residual(ctx, s)) != SENSAI_OK) return st;
+        a.R_in = ctx->R;
+        if (ctx->gram) a.R = nullptr;   // no phase reads the residual the sweep ends with
+    }
     const SweepPlan plan = ctx->sweep_plan;
     PhaseTimer timer(ctx, kPhaseCodes, s);
     int nl = 0;
     SENSAI_CUDA(ctx, launch_code_sweep(a, plan, ctx->maxobs, ctx->Dsl, s, &nl));
     if (ctx->prm.flags & SENSAI_FLAG_GAMMA_S_FULL) {
-        SENSAI_CUDA(ctx, launch_prior_s2(ctx->g, ctx->Zb, ctx->sc, a.t, a.t_dev, ctx->prm.seed, plan.lanes,
-                                         ctx->part_s2, s));
+        SENSAI_CUDA(ctx, launch_prior_s2(ctx->g, ctx->Zb, ctx->perm, ctx->sc, a.t, a.t_dev, ctx->prm.seed,
+                                         plan.lanes, ctx->part_s2, s));
         ++nl;
     }
     timer.stop();
     ctx->launches += nl;
     ctx->codes_valid = true;
-    ctx->resid_valid = true;
+    ctx->resid_valid = !ctx->gram;   // R holds the sweep's final residual (not kept by gram contexts)
+    ctx->resid_fresh = false;
+    ctx->r2_valid = true;
     ctx->n_s2 = ctx->g.NW * plan.lanes;   // one partial per work unit
     ctx->n_r2 = ctx->g.NW * plan.lanes;
     return SENSAI_OK;
+}
+
+sensai_status run_gram(sensai_ctx* ctx, cudaStream_t s)
+{
+    if (!ctx->xlist_valid) {
+        SENSAI_CUDA(ctx, launch_xlist(ctx->g, ctx->Ilist, ctx->Rbase, ctx->max_slots, ctx->imgoff, ctx->x,
+                                      ctx->Xlist, s));
+        ctx->launches += 1;
+        ctx->xlist_valid = true;
+    }
+    GramArgs a{};
+    a.g = ctx->g;
+    a.W = ctx->W;
+    a.Ilist = ctx->Ilist;
+    a.Xlist = ctx->Xlist;
+    a.items = ctx->items;
+    a.n_items = ctx->n_items;
+    a.Cpart = ctx->Cpart;
+    a.Ypart = ctx->Ypart;
+    a.pitem_start = ctx->pitem_start;
+    a.pitem_idx = ctx->pitem_idx;
+    a.C64 = ctx->C64;
+    a.Y64 = ctx->Y64;
+    a.D = ctx->D;
+    a.sc = ctx->sc;
+    a.seed = ctx->prm.seed;
+    a.t = (uint32_t)ctx->t;
+    a.t_dev = ctx->t_on_device;
+    a.tf32 = (ctx->prm.flags & SENSAI_FLAG_TF32_STATISTICS) != 0;
+    a.status = &ctx->sc->status;
+    {
+        PhaseTimer timer(ctx, kPhaseDict, s);
+        SENSAI_CUDA(ctx, launch_gram(a, ctx->gram_grid, s));
+        timer.stop();
+    }
+    ctx->launches += 3;
+    // the post-draw residual for the gamma_eps draw and the next code sweep
+    return rebuild_residual(ctx, s);
 }
 
 sensai_status run_dictionary(sensai_ctx* ctx, cudaStream_t s)
@@ -350,6 +449,7 @@ sensai_status run_dictionary(sensai_ctx* ctx, cudaStream_t s)
     if (!ctx->frame_set) return fail(SENSAI_ESTATE, "no frame: call sensai_set_frame or pass a frame");
     sensai_status st = ensure_gamma_eps(ctx, s);
     if (st != SENSAI_OK) return st;
+    if (ctx->gram) return run_gram(ctx, s);
     st = ensure_residual(ctx, s);
     if (st != SENSAI_OK) return st;
     if (ctx->ds.grid > 0) {
@@ -374,6 +474,8 @@ sensai_status run_dictionary(sensai_ctx* ctx, cudaStream_t s)
         timer.stop();
         ctx->launches += 1;
         ctx->n_r2 = ctx->ds.grid;
+        ctx->resid_fresh = false;   // updated incrementally by the draws
+        ctx->r2_valid = true;
         return SENSAI_OK;
     }
     const DictArgs a = dict_args(ctx);
@@ -382,6 +484,8 @@ sensai_status run_dictionary(sensai_ctx* ctx, cudaStream_t s)
     timer.stop();
     ctx->launches += 1;
     ctx->n_r2 = ctx->g.P;
+    ctx->resid_fresh = false;
+    ctx->r2_valid = true;
     return SENSAI_OK;
 }
 
@@ -392,7 +496,7 @@ sensai_status run_hyper(sensai_ctx* ctx, cudaStream_t s)
     if (st != SENSAI_OK) return st;
     st = ensure_code_stats(ctx, s);
     if (st != SENSAI_OK) return st;
-    st = ensure_residual(ctx, s);
+    st = ensure_r2(ctx, s);
     if (st != SENSAI_OK) return st;
     const HyperArgs a = hyper_args(ctx);
     PhaseTimer timer(ctx, kPhaseHyper, s);
@@ -408,6 +512,8 @@ sensai_status clear_codes(sensai_ctx* ctx, cudaStream_t s)
     SENSAI_CUDA(ctx, cudaMemsetAsync(ctx->Zb, 0, sizeof(uint32_t) * (size_t)ctx->g.K * ctx->g.NW, s));
     ctx->codes_valid = false;
     ctx->resid_valid = false;
+    ctx->resid_fresh = false;
+    ctx->r2_valid = false;
     return SENSAI_OK;
 }
 
@@ -487,10 +593,18 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     if (p.ndim < 1 || p.ndim > kMaxDim) return fail(SENSAI_EINVAL, "ndim must be 1..4 (got %d)", p.ndim);
     if (p.K < 1 || p.K > 1024) return fail(SENSAI_EINVAL, "K must be 1..1024 (got %d)", p.K);
     const int known_flags = SENSAI_FLAG_STREAM_DICTIONARY | SENSAI_FLAG_CHAIN_DICTIONARY | SENSAI_FLAG_GAMMA_S_FULL |
-                            SENSAI_SLICE_ATOMS(2040);
+                            SENSAI_FLAG_DENSE_STATISTICS | SENSAI_FLAG_TF32_STATISTICS | SENSAI_SLICE_ATOMS(2040);
     if ((p.flags & ~known_flags) != 0) return fail(SENSAI_EINVAL, "unknown flags 0x%x", p.flags);
     if ((p.flags & SENSAI_SLICE_ATOMS(2040)) != 0 && !(p.flags & SENSAI_FLAG_STREAM_DICTIONARY))
         return fail(SENSAI_EINVAL, "SENSAI_SLICE_ATOMS needs SENSAI_FLAG_STREAM_DICTIONARY");
+    if ((p.flags & (SENSAI_FLAG_DENSE_STATISTICS | SENSAI_FLAG_TF32_STATISTICS)) != 0) {
+        Geom gk{};
+        gk.K = p.K;
+        if (!gram_available(gk))
+            return fail(SENSAI_EINVAL, "the dense-statistics dictionary form needs K <= 128 (got %d)", p.K);
+        if (p.flags & SENSAI_FLAG_CHAIN_DICTIONARY)
+            return fail(SENSAI_EINVAL, "the dense-statistics and per-chain dictionary forms exclude each other");
+    }
     if (!(p.c > 0 && p.d > 0 && p.e > 0 && p.f > 0)) return fail(SENSAI_EINVAL, "c, d, e, f must be > 0");
     Geom g{};
     g.ndim = p.ndim;
@@ -586,7 +700,8 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     // residual layout: the pairs of the space-organised dictionary sweep when
     // it runs, else the per-pixel slots of the per-chain kernel
     CREATE_CUDA(dalloc(&ctx->pos, (size_t)(ctx->maxobs > 0 ? ctx->maxobs : 1) * N));
-    if (!(p.flags & SENSAI_FLAG_CHAIN_DICTIONARY))
+    ctx->gram = total > 0 && (p.flags & (SENSAI_FLAG_DENSE_STATISTICS | SENSAI_FLAG_TF32_STATISTICS));
+    if (!ctx->gram && !(p.flags & SENSAI_FLAG_CHAIN_DICTIONARY))
         CREATE_CUDA(ds_build(g, mask, ctx->obs, ctx->nobs, device, ctx->pos, &ctx->R, &ctx->ds, st0));
     if (ctx->ds.grid > 0) {
         ctx->launches += 2;
@@ -597,9 +712,70 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
         CREATE_CUDA(launch_pos_slots(g, ctx->obs, ctx->nobs, ctx->Ibits, ctx->Ipre, ctx->Rbase, ctx->pos, st0));
         ctx->launches += 2;
     }
+    if (ctx->gram) {
+        // the work items: each pixel's patch list in segments of at most
+        // 2048 patches (256 tensor-core steps accumulated in FP32)
+        std::vector<int> hr((size_t)P + 1);
+        CREATE_CUDA(cudaMemcpy(hr.data(), ctx->Rbase, sizeof(int) * hr.size(), cudaMemcpyDeviceToHost));
+        std::vector<int4> items;
+        std::vector<int> ps, pi;
+        gram_plan_items(hr, (int)P, 2048, &items, &ps, &pi);
+        ctx->n_items = (long long)items.size();
+        CREATE_CUDA(dalloc(&ctx->Xlist, (size_t)total));
+        CREATE_CUDA(dalloc(&ctx->items, items.size()));
+        CREATE_CUDA(dalloc(&ctx->pitem_start, ps.size()));
+        CREATE_CUDA(dalloc(&ctx->pitem_idx, pi.size()));
+        CREATE_CUDA(dalloc(&ctx->Cpart, items.size() * 128 * 128));
+        CREATE_CUDA(dalloc(&ctx->Ypart, items.size() * 4 * 128));
+        CREATE_CUDA(dalloc(&ctx->C64, (size_t)P * 128 * 128));
+        CREATE_CUDA(dalloc(&ctx->Y64, (size_t)P * 128));
+        CREATE_CUDA(cudaMemcpy(ctx->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+        CREATE_CUDA(cudaMemcpy(ctx->pitem_start, ps.data(), sizeof(int) * ps.size(), cudaMemcpyHostToDevice));
+        CREATE_CUDA(cudaMemcpy(ctx->pitem_idx, pi.data(), sizeof(int) * pi.size(), cudaMemcpyHostToDevice));
+        int sms_g = 0;
+        CREATE_CUDA(cudaDeviceGetAttribute(&sms_g, cudaDevAttrMultiProcessorCount, device));
+        ctx->gram_grid = (int)std::min<long long>(ctx->n_items, sms_g);
+    }
+
+    {
+        // the code sweep's order: patches by decreasing |Omega_i|, so that
+        // the 32 patches of a warp have nearly equal counts (a warp's loops
+        // run to its largest count); obs, nobs and pos are rewritten by slot
+        std::vector<uint16_t> hn((size_t)N);
+        std::vector<int> hp((size_t)g.Npad);
+        CREATE_CUDA(cudaMemcpy(hn.data(), ctx->nobs, sizeof(uint16_t) * (size_t)N, cudaMemcpyDeviceToHost));
+        sweep_order_host(hn.data(), N, g.Npad, hp.data());
+        CREATE_CUDA(dalloc(&ctx->perm, (size_t)g.Npad));
+        CREATE_CUDA(cudaMemcpy(ctx->perm, hp.data(), sizeof(int) * (size_t)g.Npad, cudaMemcpyHostToDevice));
+        const size_t rows = (size_t)(ctx->maxobs > 0 ? ctx->maxobs : 1);
+        uint16_t *obs_s = nullptr, *nobs_s = nullptr;
+        int* pos_s = nullptr;
+        cudaError_t e1 = dalloc(&obs_s, rows * N);
+        if (e1 == cudaSuccess) e1 = dalloc(&nobs_s, (size_t)N);
+        if (e1 == cudaSuccess) e1 = dalloc(&pos_s, rows * N);
+        if (e1 == cudaSuccess)
+            e1 = launch_sweep_order(g, ctx->maxobs, ctx->perm, ctx->obs, ctx->nobs, ctx->pos, obs_s, nobs_s, pos_s,
+                                    st0);
+        if (e1 == cudaSuccess) e1 = cudaDeviceSynchronize();
+        if (e1 != cudaSuccess) {
+            cudaFree(obs_s);
+            cudaFree(nobs_s);
+            cudaFree(pos_s);
+            return bail(cuda_failure(nullptr, e1, "sweep order", __LINE__));
+        }
+        std::swap(ctx->obs, obs_s);
+        std::swap(ctx->nobs, nobs_s);
+        std::swap(ctx->pos, pos_s);
+        cudaFree(obs_s);
+        cudaFree(nobs_s);
+        cudaFree(pos_s);
+        ctx->launches += 1;
+    }
 
     CREATE_CUDA(dalloc(&ctx->x, (size_t)nframe));
     CREATE_CUDA(dalloc(&ctx->out, (size_t)nframe));
+    CREATE_CUDA(dalloc(&ctx->mean_acc, (size_t)nframe));
+    CREATE_CUDA(cudaMemset(ctx->mean_acc, 0, sizeof(double) * (size_t)nframe));
     CREATE_CUDA(dalloc(&ctx->D, (size_t)g.K * P));
     CREATE_CUDA(dalloc(&ctx->W, (size_t)g.KB * kAtomBlock * g.Npad));
     CREATE_CUDA(dalloc(&ctx->Zb, (size_t)g.K * g.NW));
@@ -760,6 +936,50 @@ sensai_status sensai_reconstruct(sensai_ctx* ctx, float* out, void* stream)
     return SENSAI_OK;
 }
 
+sensai_status sensai_mean_reset(sensai_ctx* ctx, void* stream)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    const cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    SENSAI_CUDA(ctx, cudaMemsetAsync(ctx->mean_acc, 0, sizeof(double) * (size_t)ctx->g.nframe, s));
+    ctx->mean_count = 0;
+    return SENSAI_OK;
+}
+
+sensai_status sensai_mean_add(sensai_ctx* ctx, void* stream)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    const cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    {
+        PhaseTimer timer(ctx, kPhaseRecon, s);
+        SENSAI_CUDA(ctx, launch_reconstruct(ctx->g, ctx->D, ctx->Dc, ctx->W, ctx->Y, ctx->out, &ctx->sc->status, s));
+        SENSAI_CUDA(ctx, launch_mean_accumulate(ctx->g.nframe, ctx->out, ctx->mean_acc, s));
+        timer.stop();
+        ctx->launches += reconstruct_launches(ctx->g) + 1;
+    }
+    ctx->mean_count += 1;
+    return SENSAI_OK;
+}
+
+sensai_status sensai_mean_read(sensai_ctx* ctx, float* out, void* stream)
+{
+    sensai_status st = enter(ctx);
+    if (st != SENSAI_OK) return st;
+    if (!out) return fail(SENSAI_EINVAL, "null output");
+    if (ctx->mean_count < 1) return fail(SENSAI_ESTATE, "no reconstruction added since the last sensai_mean_reset");
+    const cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    const bool dev = is_device_pointer(out);
+    float* dst = dev ? out : ctx->out;
+    SENSAI_CUDA(ctx, launch_mean_finish(ctx->g.nframe, ctx->mean_acc, ctx->mean_count, dst, s));
+    ctx->launches += 1;
+    if (!dev) return write_out(ctx, ctx->out, out, sizeof(float) * (size_t)ctx->g.nframe, s);
+    return SENSAI_OK;
+}
+
 sensai_status sensai_overlap_counts(sensai_ctx* ctx, int32_t* out, void* stream)
 {
     sensai_status st = enter(ctx);
@@ -793,6 +1013,8 @@ sensai_status sensai_set_dictionary(sensai_ctx* ctx, const float* D)
     SENSAI_CUDA(ctx, cudaDeviceSynchronize());
     SENSAI_CUDA(ctx, cudaMemcpy(ctx->D, D, sizeof(float) * (size_t)ctx->g.K * ctx->g.P, cudaMemcpyDefault));
     ctx->resid_valid = false;
+    ctx->resid_fresh = false;
+    ctx->r2_valid = false;
     return SENSAI_OK;
 }
 
@@ -815,7 +1037,7 @@ sensai_status sensai_get_state(sensai_ctx* ctx, sensai_state* state)
             cudaFree(z);
             return cuda_failure(ctx, e, "dalloc", __LINE__);
         }
-        e = launch_export_codes(g, ctx->W, ctx->Zb, z, sv, nullptr);
+        e = launch_export_codes(g, ctx->W, ctx->Zb, ctx->perm, z, sv, nullptr);
         if (e == cudaSuccess && state->Z) e = cudaMemcpy(state->Z, z, n, cudaMemcpyDefault);
         if (e == cudaSuccess && state->S) e = cudaMemcpy(state->S, sv, n * sizeof(float), cudaMemcpyDefault);
         cudaFree(z);
@@ -856,7 +1078,7 @@ sensai_status sensai_set_state(sensai_ctx* ctx, const sensai_state* state)
         cudaError_t e = dalloc(&sv, n);
         if (e == cudaSuccess) e = cudaMemcpy(z, state->Z, n, cudaMemcpyDefault);
         if (e == cudaSuccess) e = cudaMemcpy(sv, state->S, n * sizeof(float), cudaMemcpyDefault);
-        if (e == cudaSuccess) e = launch_import_codes(g, z, sv, ctx->W, ctx->Zb, nullptr);
+        if (e == cudaSuccess) e = launch_import_codes(g, z, sv, ctx->perm, ctx->W, ctx->Zb, nullptr);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         cudaFree(z);
         if (sv) cudaFree(sv);
@@ -874,6 +1096,8 @@ sensai_status sensai_set_state(sensai_ctx* ctx, const sensai_state* state)
     ctx->t = state->iter;
     ctx->codes_valid = false;
     ctx->resid_valid = false;
+    ctx->resid_fresh = false;
+    ctx->r2_valid = false;
     return SENSAI_OK;
 }
 
@@ -1130,7 +1354,7 @@ sensai_status batch_build(sensai_batch* b)
     for (int i = 0; i < n; ++i) {
         sensai_ctx* c = b->ctx[i];
         c->t_on_device = true;
-        sa[i] = sweep_args(c);
+        sa[i] = sweep_args(c);   // batched sweeps rebuild their residual themselves (same bits)
         da[i] = dict_args(c);
         ha[i] = hyper_args(c);
         c->t_on_device = false;
@@ -1342,6 +1566,8 @@ void batch_advance(sensai_batch* b, int iters)
         c->t += iters;
         c->codes_valid = true;
         c->resid_valid = true;
+        c->resid_fresh = false;
+        c->r2_valid = true;
         c->n_s2 = c->g.NW * c->sweep_plan.lanes;
         c->n_r2 = c->g.P;
     }
@@ -1391,8 +1617,8 @@ sensai_status sensai_batch_create(sensai_ctx* const* ctxs, int32_t n, sensai_bat
     *out = nullptr;
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i]) return fail(SENSAI_EINVAL, "null context %d", i);
-        if (ctxs[i]->ds.grid > 0)
-            return fail(SENSAI_EINVAL, "context %d uses the cooperative dictionary kernel; create it with "
+        if (!(ctxs[i]->prm.flags & SENSAI_FLAG_CHAIN_DICTIONARY))
+            return fail(SENSAI_EINVAL, "context %d does not use the per-chain dictionary kernel; create it with "
                         "SENSAI_FLAG_CHAIN_DICTIONARY", i);
         if (ctxs[i]->device != ctxs[0]->device) return fail(SENSAI_EINVAL, "contexts on different devices");
         if (ctxs[i]->prm.flags & SENSAI_FLAG_GAMMA_S_FULL)

@@ -57,12 +57,13 @@ __device__ bool grid_barrier(unsigned int* count, unsigned int target, int* stat
     if (threadIdx.x == 0) {
         int ok = 1;
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
-        const unsigned long long t0 = global_ns();
+        unsigned long long t0 = 0;   // the global timer (a slow read) once a poll has failed
         long long spins = 0;
         for (;;) {
             unsigned int v;
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
             if (v >= target) break;
+            if (spins == 0) t0 = global_ns();
             if (++spins > kBarrierSpins || ((spins & 255) == 0 && global_ns() - t0 > kWaitLimitNs)) {
                 atomicExch(status, (int)SENSAI_ETIMEOUT);
                 ok = 0;

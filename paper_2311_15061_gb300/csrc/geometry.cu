@@ -12,6 +12,9 @@
 //  * Rbase[p]: start of pixel p's slots (exclusive scan of the counts);
 //  * overlap counts c_q: per dimension floor(min(y, last)/S) -
 //    ceil(max(0, y - B + 1)/S) + 1, multiplied over dimensions.
+#include <algorithm>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace sensai {
@@ -318,6 +321,40 @@ __global__ void __launch_bounds__(256) patch_recon_kernel(Geom g, const float* D
 
 namespace sensai {
 
+// Posterior-mean reconstruction: acc += frame (FP64), then out = acc / count.
+__global__ void mean_accumulate_kernel(long long n, const float* frame, double* acc)
+{
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+         u += (long long)gridDim.x * blockDim.x)
+        acc[u] += (double)frame[u];
+}
+
+__global__ void mean_finish_kernel(long long n, const double* acc, double count, float* out)
+{
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+         u += (long long)gridDim.x * blockDim.x)
+        out[u] = (float)(acc[u] / count);
+}
+
+// The code sweep's tables in sweep order: slot s holds patch perm[s].
+// obs and pos ([maxobs][N]) and nobs ([N]) are gathered row by row.
+__global__ void sweep_order_kernel(Geom g, int maxobs, const int* perm, const uint16_t* obs_in,
+                                   const uint16_t* nobs_in, const int* pos_in, uint16_t* obs_out,
+                                   uint16_t* nobs_out, int* pos_out)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long rows = (long long)maxobs + 1;
+    if (idx >= rows * g.N) return;
+    const long long j = idx / g.N, slot = idx - j * g.N;
+    const long long i = perm[slot];
+    if (j == maxobs) {
+        nobs_out[slot] = nobs_in[i];
+    } else {
+        obs_out[j * g.N + slot] = obs_in[j * g.N + i];
+        pos_out[j * g.N + slot] = pos_in[j * g.N + i];
+    }
+}
+
 static inline unsigned int blocks_for(long long n, int threads)
 {
     return (unsigned int)((n + threads - 1) / threads);
@@ -399,6 +436,46 @@ static cudaError_t launch_ola_gather(const Geom& g, const float* Y, float* out, 
     case 4: ola_gather_kernel<4><<<blocks, 256, 0, s>>>(g, Y, out); break;
     default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+}  // namespace sensai
+
+namespace sensai {
+
+void sweep_order_host(const uint16_t* nobs, long long N, long long Npad, int* perm)
+{
+    // counting sort, largest counts first (a warp's work is set by its
+    // largest count; the heaviest warps start first, so the tail of a sweep
+    // is light); ties keep patch order
+    std::vector<long long> start(65537, 0);
+    for (long long i = 0; i < N; ++i) ++start[65535 - nobs[i] + 1];
+    for (int v = 1; v <= 65536; ++v) start[v] += start[v - 1];
+    for (long long i = 0; i < N; ++i) perm[start[65535 - nobs[i]]++] = (int)i;
+    for (long long s = N; s < Npad; ++s) perm[s] = (int)s;
+}
+
+cudaError_t launch_mean_accumulate(long long n, const float* frame, double* acc, cudaStream_t s)
+{
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    mean_accumulate_kernel<<<(unsigned int)blocks, 256, 0, s>>>(n, frame, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mean_finish(long long n, const double* acc, long long count, float* out, cudaStream_t s)
+{
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    mean_finish_kernel<<<(unsigned int)blocks, 256, 0, s>>>(n, acc, (double)count, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_order(const Geom& g, int maxobs, const int* perm, const uint16_t* obs_in,
+                               const uint16_t* nobs_in, const int* pos_in, uint16_t* obs_out, uint16_t* nobs_out,
+                               int* pos_out, cudaStream_t s)
+{
+    const long long n = ((long long)maxobs + 1) * g.N;
+    sweep_order_kernel<<<(unsigned int)((n + 255) / 256), 256, 0, s>>>(g, maxobs, perm, obs_in, nobs_in, pos_in,
+                                                                       obs_out, nobs_out, pos_out);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,680 @@
+// gram.cu -- the dictionary step in its dense-statistics form, with the
+// statistics contracted on the tensor cores (the dictionary-learning step of
+// the BPFA section).
+//
+// Neither dictionary sum couples different within-patch pixels p, and the
+// atom-ordered conditional of d_kp given every other atom needs, for pixel
+// p, only
+//   C_p = sum_{i observes p} w_i w_i^T   (the K x K Gram of the weights),
+//   Y_p = sum_{i observes p} w_i x_ip    (K correlations with the frame)
+// and the current column d_p.  With u = C_p d_p kept current,
+//   A_kp = Y_kp - u_k + C_p[k,k] d_kp,  Lambda_kp = P + gamma_eps C_p[k,k],
+//   d_kp = gamma_eps A_kp / Lambda_kp + xi_kp / sqrt(Lambda_kp),
+// then u += C_p[:,k] (d_new - d_old): atom by atom in order, the same
+// conditional as the residual form (tests/test_oracle_dense_statistics.py
+// pins the equality), with no pass over the residual at all.
+//
+// gram_kernel -- the statistics.  Work items are (pixel p, a segment of the
+// patches observing p), segment-major so that concurrent items read weight
+// records of neighbouring patches (L2 reuse).  An item is cut into chunks of
+// 32 patches.  With w = h + l split into a TF32 head h (the top 19 bits, what
+// the tensor core reads) and an FP32 tail l, per 8 patches of a chunk two
+// tcgen05.mma kind::tf32 (M = N = 128 atoms, K = 8 patches, operands K-major
+// in shared memory) accumulate
+//   T += H H^T + H (2L)^T,
+// i.e. one product with the K dimension doubled, [H | H] [H | 2L]^T, into a
+// 128-column tensor-memory accumulator.  Since H H^T is symmetric,
+// C = (T + T^T) / 2 = H H^T + H L^T + L H^T: the h h + h l + l h products,
+// the dropped l l below 2^-20 relative (FP32-level).  With
+// SENSAI_FLAG_TF32_STATISTICS only H H^T is formed (TF32-level).
+// The tensor core's FP32 accumulation rounds toward minus infinity (each
+// step aligns the addends to the largest with one guard bit and floors; an
+// in-bounds probe on this GPU showed it), a bias that grows with the steps
+// accumulated.  So the accumulator is drained every 4 chunks (16 steps of 8
+// patches) into running sums, added in FP32 round-to-
+// nearest: a simulation of that arithmetic on the 128x128 K = 64 workload
+// gives <= 2e-6 relative on the drawn atoms.
+// Warp roles (320 threads, one CTA per SM):
+//  * warps 9-10, loaders: per chunk, the 32 patch indices (loaded a chunk
+//    ahead), then per patch one cp.async of 16 bytes per lane -- the patch's
+//    whole 512-byte weight record -- and the 32 frame values, into one of
+//    four raw slots; completion is signalled on the slot's mbarrier;
+//  * warps 0-3, converters: warp w takes chunks w, w + 4, ...: lane l holds
+//    atoms 4l .. 4l + 3 of every patch of the chunk (16-byte shared loads),
+//    splits them, writes H and 2L into the chunk's operand stage as 16-byte
+//    stores (an 8-row group pitch of 272 bytes keeps them free of bank
+//    conflicts) and accumulates Y_p for its atoms in FP32;
+//  * warp 8, lane 0: issues the MMAs (a wait per chunk, 8 MMAs, a commit)
+//    into two accumulators in turn, one per group of 4 chunks;
+//  * warps 4-7, epilogue: warp w reads TMEM lanes 32 (w % 4) .., i.e. the
+//    rows of 32 atoms, adds each group's accumulator into running sums kept
+//    in tensor memory and frees it; at the end of an item it writes T^T
+//    (coalesced) as the item's FP32 partial.
+// Every wait is bounded; a timeout sets SENSAI_ETIMEOUT in the status word,
+// every role stops (each warp's decision is its lane 0's, broadcast), the
+// MMAs in flight are waited for and TMEM is freed.
+//
+// gram_reduce_kernel -- the FP64 sums of every pixel's item partials, in item
+// order; gram_draw_kernel -- one CTA per pixel p: symmetrises the sum into
+// C_p and makes the K atom-ordered draws in FP64.
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace sensai {
+
+constexpr int kGAtoms = 128;                    // M = N: atoms, K padded to 128
+constexpr int kGStep = 8;                       // patches per MMA (tf32 K)
+constexpr int kGChunk = 32;                     // patches per chunk (4 MMA steps)
+constexpr int kGConverters = 4;                 // warps 0-3
+constexpr int kGEpilogue0 = 4;                  // warps 4-7
+constexpr int kGMmaWarp = 8;
+constexpr int kGLoader0 = 9;                    // warps 9-10
+constexpr int kGLoaders = 2;
+constexpr int kGThreads = 32 * (kGLoader0 + kGLoaders);
+constexpr int kGSlots = 4;                      // raw slots = operand stages = converter warps
+constexpr int kGGroup = 4;                      // chunks per accumulator drain
+constexpr int kGSegment = 2048;                 // most patches of an item
+constexpr int kGRawFloats = kGChunk * kGAtoms + kGChunk;   // records [32][128], then the 32 frame values
+constexpr int kGSboBytes = 272;                 // 8-row group pitch (256 B of data + 16 B)
+constexpr int kGOpFloats = (kGAtoms / 8) * kGSboBytes / 4;   // one 128 x 8 operand: 1088 floats
+constexpr int kGStageFloats = 2 * (kGChunk / kGStep) * kGOpFloats;   // H[4], then 2L[4]
+constexpr int kGTmemCols = 4 * kGAtoms;         // two accumulators, the running sums, unused
+constexpr int kGSumCol = 2 * kGAtoms;           // the running sums' columns
+constexpr long long kGSpins = 1LL << 22;
+
+static_assert(kGSlots == kGConverters, "converter warp w owns raw slot w and stage w");
+
+__device__ __forceinline__ uint32_t gm_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// No-swizzle K-major descriptor (8-row x 16-byte core matrices; 128 B between
+// the two core matrices along K, kGSboBytes between 8-row groups), version 1.
+__device__ __forceinline__ uint64_t gm_desc(const void* p)
+{
+    uint64_t d = (uint64_t)((gm_smem(p) >> 4) & 0x3FFF);
+    d |= (uint64_t)(128u >> 4) << 16;
+    d |= (uint64_t)((uint32_t)kGSboBytes >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// F32 accumulator, TF32 A and B, both K-major, M = N = 128.
+__device__ __forceinline__ uint32_t gm_idesc()
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kGAtoms >> 3) << 17) | ((uint32_t)(kGAtoms >> 4) << 24);
+}
+
+__device__ __forceinline__ float gm_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+__device__ __forceinline__ void gm_bar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gm_smem(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void gm_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(gm_smem(bar)) : "memory");
+}
+
+// Bounded wait for a phase: each try suspends the thread in hardware for up
+// to ~1 us (or until the phase completes), so waiting threads take few issue
+// slots; gives up after kWaitLimitNs.  The global timer (a slow read: some
+// hundreds of cycles) is read only once a try has failed.
+__device__ __forceinline__ bool gm_wait(uint64_t* bar, uint32_t parity)
+{
+    unsigned long long t0 = 0;
+    for (long long spins = 0; spins < kGSpins; ++spins) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(gm_smem(bar)), "r"(parity), "r"(1000u)
+            : "memory");
+        if (ok) return true;
+        if (spins == 0) t0 = global_ns();
+        else if ((spins & 15) == 0 && global_ns() - t0 > kWaitLimitNs) break;
+    }
+    return false;
+}
+
+// 16-byte (and 4-byte) asynchronous global -> shared copies; their completion
+// is signalled on an mbarrier by gm_cp_arrive.
+__device__ __forceinline__ void gm_cp16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(gm_smem(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void gm_cp4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(gm_smem(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void gm_cp_arrive(uint64_t* bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(gm_smem(bar)) : "memory");
+}
+
+__device__ __forceinline__ void gm_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void gm_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(gm_smem(bar))
+                 : "memory");
+}
+
+// 32 consecutive accumulator columns of this warp's 32 lanes.
+__device__ __forceinline__ void gm_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// Stores 32 consecutive columns of this warp's 32 lanes; tcgen05.wait::st
+// (gm_st_wait) orders them before later tensor-memory reads.
+__device__ __forceinline__ void gm_st32(uint32_t taddr, const float (&v)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+        "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+        "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+        "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+        "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+        "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+        : "memory");
+}
+
+__device__ __forceinline__ void gm_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ int gm_chunks(int cnt) { return (cnt + kGChunk - 1) / kGChunk; }
+
+// The chunks of this CTA's items in order: item it, chunk c of it, and the
+// running chunk number u.  Every role walks the same sequence.
+struct ChunkWalk {
+    long long it;
+    int c, nch;
+    long long u;
+    __device__ void start(const GramArgs& a)
+    {
+        it = blockIdx.x;
+        c = 0;
+        u = 0;
+        nch = it < a.n_items ? gm_chunks(a.items[it].z) : 0;
+    }
+    __device__ bool valid(const GramArgs& a) const { return it < a.n_items; }
+    __device__ void next(const GramArgs& a)
+    {
+        ++u;
+        if (++c == nch) {
+            c = 0;
+            it += gridDim.x;
+            nch = it < a.n_items ? gm_chunks(a.items[it].z) : 0;
+        }
+    }
+};
+
+// Item it: pixel items[it].x, patches Ilist[items[it].y .. + items[it].z).
+__global__ void __launch_bounds__(kGThreads, 1)
+    gram_kernel(GramArgs a)
+{
+    extern __shared__ __align__(1024) float gsm[];
+    __shared__ __align__(8) uint64_t full_bar[kGSlots];    // stage s written (converter warp s)
+    __shared__ __align__(8) uint64_t empty_bar[kGSlots];   // stage s read (the MMA commit)
+    __shared__ __align__(8) uint64_t raw_full[kGSlots];    // raw slot r landed (every loader lane's copies)
+    __shared__ __align__(8) uint64_t raw_empty[kGSlots];   // raw slot r read (converter warp r)
+    __shared__ __align__(8) uint64_t accf_bar[2];          // a group's MMAs complete
+    __shared__ __align__(8) uint64_t acce_bar[2];          // a group's accumulator drained
+    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int K = a.g.K;
+    const bool split = !a.tf32;
+    float* stages = gsm;                                   // [kGSlots][kGStageFloats]
+    float* raw = stages + kGSlots * kGStageFloats;         // [kGSlots][kGRawFloats]
+
+    if (tid == 0) {
+        abort_s = 0;
+        for (int s = 0; s < kGSlots; ++s) {
+            gm_bar_init(&full_bar[s], 1);
+            gm_bar_init(&empty_bar[s], 1);
+            gm_bar_init(&raw_full[s], 32);
+            gm_bar_init(&raw_empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            gm_bar_init(&accf_bar[b], 1);
+            gm_bar_init(&acce_bar[b], 4);   // lane 0 of every epilogue warp
+        }
+        gm_bar_init(&done_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(gm_smem(&tmem_slot)),
+                     "r"(kGTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const long long Npad = a.g.Npad;
+
+    // lane 0 of the warp waits; the warp leaves with lane 0's decision
+    auto warp_wait = [&](uint64_t* bar, uint32_t parity) {
+        int ok = 1;
+        if (lane == 0) {
+            ok = !abort_s && gm_wait(bar, parity);
+            if (!ok && !abort_s) {
+                atomicExch(a.status, (int)SENSAI_ETIMEOUT);
+                abort_s = 1;
+            }
+        }
+        return __shfl_sync(0xffffffffu, ok, 0) != 0;
+    };
+
+    ChunkWalk wk;
+    wk.start(a);
+    if (warp < kGConverters) {
+        // ----------------------------------------------------- converters --
+        // lane l: atoms 4l .. 4l + 3 of the 32 patches of each own chunk
+        const int w = warp;
+        float* stg = stages + (size_t)w * kGStageFloats;
+        const float* rw = raw + (size_t)w * kGRawFloats;
+        bool live[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) live[r] = 4 * lane + r < K;
+        // float offset of this lane's atom 4l + r, patches 4q .. 4q + 3 of a
+        // 128 x 8 operand (8-row group l / 2, row 4 (l % 2) + r in it)
+        const int op_base = (lane >> 1) * (kGSboBytes / 4) + (lane & 1) * 16;
+        float y[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        long long n = 0;   // this warp's chunks so far
+        bool ok = true;
+        for (; wk.valid(a) && ok; wk.next(a)) {
+            if ((int)(wk.u % kGConverters) == w) {
+                const int cnt = a.items[wk.it].z;
+                const int nvalid = min(kGChunk, cnt - wk.c * kGChunk);
+                const uint32_t par = (uint32_t)(n & 1);
+                ok = warp_wait(&raw_full[w], par) && warp_wait(&empty_bar[w], par ^ 1u);
+                if (!ok) break;
+#pragma unroll
+                for (int kb = 0; kb < kGChunk / kGStep; ++kb) {
+                    float4 v[kGStep];
+#pragma unroll
+                    for (int j = 0; j < kGStep; ++j)
+                        v[j] = *reinterpret_cast<const float4*>(rw + (kb * kGStep + j) * kGAtoms + 4 * lane);
+                    float wv[kGStep][4];
+#pragma unroll
+                    for (int j = 0; j < kGStep; ++j) {
+                        const bool pv = kb * kGStep + j < nvalid;
+                        const float xj = pv ? rw[kGChunk * kGAtoms + kb * kGStep + j] : 0.0f;
+                        const float e[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            wv[j][r] = (pv && live[r]) ? e[r] : 0.0f;
+                            y[r] = fmaf(wv[j][r], xj, y[r]);
+                        }
+                    }
+                    float* oh = stg + kb * kGOpFloats + op_base;
+                    float* ol = stg + (kGChunk / kGStep + kb) * kGOpFloats + op_base;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            float4 h, l2;
+                            h.x = gm_head(wv[4 * q + 0][r]);
+                            h.y = gm_head(wv[4 * q + 1][r]);
+                            h.z = gm_head(wv[4 * q + 2][r]);
+                            h.w = gm_head(wv[4 * q + 3][r]);
+                            *reinterpret_cast<float4*>(oh + q * 32 + r * 4) = h;
+                            if (split) {
+                                // 2 (w - h): exact (h is w truncated; doubling is exact)
+                                l2.x = 2.0f * (wv[4 * q + 0][r] - h.x);
+                                l2.y = 2.0f * (wv[4 * q + 1][r] - h.y);
+                                l2.z = 2.0f * (wv[4 * q + 2][r] - h.z);
+                                l2.w = 2.0f * (wv[4 * q + 3][r] - h.w);
+                                *reinterpret_cast<float4*>(ol + q * 32 + r * 4) = l2;
+                            }
+                        }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    gm_arrive(&raw_empty[w]);
+                    gm_arrive(&full_bar[w]);
+                }
+                ++n;
+            }
+            if (wk.c == wk.nch - 1) {
+                // the end of an item: this warp's share of Y_p (its chunks)
+                float4 yo = make_float4(y[0], y[1], y[2], y[3]);
+                *reinterpret_cast<float4*>(a.Ypart + ((size_t)wk.it * kGConverters + w) * kGAtoms + 4 * lane) = yo;
+                y[0] = y[1] = y[2] = y[3] = 0.0f;
+            }
+        }
+    } else if (warp >= kGLoader0 && warp < kGLoader0 + kGLoaders) {
+        // --------------------------------------------------------- loaders --
+        // loader warp v takes chunks v, v + 2, ...; lane l copies 16-byte
+        // piece l of every patch record (atom block l / 2, half l % 2)
+        const int v = warp - kGLoader0;
+        const bool lane_live = (lane >> 1) < a.g.KB;
+        // the next own chunk's patch index and frame value, loaded a chunk ahead
+        auto load_idx = [&](const ChunkWalk& c, int& idx) {
+            idx = 0;
+            if (!c.valid(a)) return;
+            const int4 item = a.items[c.it];
+            const int e = c.c * kGChunk + lane;
+            if (e < item.z) idx = __ldg(a.Ilist + item.y + e);
+        };
+        auto advance_own = [&](ChunkWalk& c) {
+            do {
+                c.next(a);
+            } while (c.valid(a) && (int)(c.u % kGLoaders) != v);
+        };
+        ChunkWalk cur = wk;
+        if (cur.valid(a) && (int)(cur.u % kGLoaders) != v) advance_own(cur);
+        int idx = 0;
+        load_idx(cur, idx);
+        while (cur.valid(a)) {
+            ChunkWalk nxt = cur;
+            advance_own(nxt);
+            int idx_n = 0;
+            load_idx(nxt, idx_n);
+            const int4 item = a.items[cur.it];
+            const int slot = (int)(cur.u % kGSlots);
+            const uint32_t par = (uint32_t)((cur.u / kGSlots) & 1);
+            if (!warp_wait(&raw_empty[slot], par ^ 1u)) break;
+            float* dst = raw + (size_t)slot * kGRawFloats;
+            const int nvalid = min(kGChunk, item.z - cur.c * kGChunk);
+            const long long woff = ((long long)(lane >> 1) * Npad) * kAtomBlock + (lane & 1) * 4;
+#pragma unroll 8
+            for (int m = 0; m < kGChunk; ++m) {
+                const int i = __shfl_sync(0xffffffffu, idx, m);
+                if (m < nvalid && lane_live)
+                    gm_cp16(dst + m * kGAtoms + 4 * lane, a.W + woff + (long long)i * kAtomBlock);
+            }
+            if (lane < nvalid) gm_cp4(dst + kGChunk * kGAtoms + lane, a.Xlist + item.y + cur.c * kGChunk + lane);
+            gm_cp_arrive(&raw_full[slot]);
+            cur = nxt;
+            idx = idx_n;
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (warp == kGMmaWarp) {
+        // ---------------------------------------------------- MMA issuer --
+        if (lane == 0) {
+            const uint32_t idesc = gm_idesc();
+            long long gc = 0;   // groups (accumulator uses)
+            bool ok = true;
+            while (wk.valid(a) && ok) {
+                const int cnt = a.items[wk.it].z;
+                const int c1 = min(wk.c + kGGroup, wk.nch);
+                const int buf = (int)(gc & 1);
+                if (abort_s || !gm_wait(&acce_bar[buf], (uint32_t)(((gc >> 1) & 1) ^ 1))) {   // drained
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc_tmem = tmem + (uint32_t)(buf * kGAtoms);
+                uint32_t acc = 0;
+                for (int c = wk.c; c < c1; ++c, wk.next(a)) {
+                    const int s = (int)(wk.u % kGSlots);
+                    if (abort_s || !gm_wait(&full_bar[s], (uint32_t)((wk.u / kGSlots) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const float* stg = stages + (size_t)s * kGStageFloats;
+                    const int nvalid = min(kGChunk, cnt - c * kGChunk);
+                    for (int kb = 0; kb * kGStep < nvalid; ++kb) {
+                        const uint64_t dh = gm_desc(stg + kb * kGOpFloats);
+                        gm_mma(acc_tmem, dh, dh, idesc, acc);
+                        acc = 1;
+                        if (split) gm_mma(acc_tmem, dh, gm_desc(stg + (kGChunk / kGStep + kb) * kGOpFloats), idesc, 1u);
+                    }
+                    gm_commit(&empty_bar[s]);
+                }
+                if (!ok) break;
+                gm_commit(&accf_bar[buf]);
+                ++gc;
+            }
+            if (!ok && !abort_s) {
+                atomicExch(a.status, (int)SENSAI_ETIMEOUT);
+                abort_s = 1;
+            }
+            // every MMA issued has completed before TMEM is freed
+            gm_commit(&done_bar);
+            if (!gm_wait(&done_bar, 0)) atomicExch(a.status, (int)SENSAI_ETIMEOUT);
+        }
+    } else if (warp >= kGEpilogue0 && warp < kGEpilogue0 + 4) {
+        // ------------------------------------------------------- epilogue --
+        const int quarter = warp & 3;              // TMEM lanes 32 quarter ..
+        const int row = quarter * 32 + lane;       // atom of the accumulator rows
+        const uint32_t lanes = tmem + ((uint32_t)(quarter * 32) << 16);
+        long long gc = 0;
+        bool ok = true;
+        while (wk.valid(a) && ok) {
+            float* cpart = a.Cpart + (size_t)wk.it * kGAtoms * kGAtoms;
+            bool first = true;
+            // the item's groups of kGGroup chunks: the running sums in tensor
+            // memory; the last group's total is the item's partial T^T
+            while (ok) {
+                const int c1 = min(wk.c + kGGroup, wk.nch);
+                const bool last = c1 == wk.nch;
+                const int buf = (int)(gc & 1);
+                ok = warp_wait(&accf_bar[buf], (uint32_t)((gc >> 1) & 1));
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+                for (int cb = 0; cb < kGAtoms / 32; ++cb) {
+                    float v[32];
+                    gm_ld32(lanes + (uint32_t)(buf * kGAtoms + cb * 32), v);
+                    if (!first) {
+                        float sm[32];
+                        gm_ld32(lanes + (uint32_t)(kGSumCol + cb * 32), sm);
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) v[q] = sm[q] + v[q];
+                    }
+                    if (last) {
+                        // column `row` of the transposed partial (coalesced)
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) cpart[(size_t)(cb * 32 + q) * kGAtoms + row] = v[q];
+                    } else {
+                        gm_st32(lanes + (uint32_t)(kGSumCol + cb * 32), v);
+                    }
+                }
+                if (!last) gm_st_wait();
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) gm_arrive(&acce_bar[buf]);
+                ++gc;
+                first = false;
+                for (int c = wk.c; c < c1; ++c) wk.next(a);
+                if (last) break;
+            }
+        }
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kGTmemCols) : "memory");
+}
+
+// S_p = sum of pixel p's item partials T^T and Y_p, FP64 sums in item order.
+// One thread per element, every item's load in flight at once.
+__global__ void __launch_bounds__(256) gram_reduce_kernel(GramArgs a)
+{
+    const int p = blockIdx.x;
+    const int idx = blockIdx.y * blockDim.x + threadIdx.x;   // r * 128 + t
+    const int i0 = a.pitem_start[p], i1 = a.pitem_start[p + 1];
+    double s = 0.0;
+    int j = i0;
+    for (; j + 4 <= i1; j += 4) {
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = a.Cpart[(size_t)a.pitem_idx[j + q] * kGAtoms * kGAtoms + idx];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s += (double)v[q];
+    }
+    for (; j < i1; ++j) s += (double)a.Cpart[(size_t)a.pitem_idx[j] * kGAtoms * kGAtoms + idx];
+    a.C64[(size_t)p * kGAtoms * kGAtoms + idx] = s;
+    if (blockIdx.y == 0 && threadIdx.x < kGAtoms) {
+        const int t = threadIdx.x;
+        double y = 0.0;
+        for (int jj = i0; jj < i1; ++jj) {
+            const size_t it = (size_t)a.pitem_idx[jj];
+#pragma unroll
+            for (int w = 0; w < kGConverters; ++w) y += (double)a.Ypart[(it * kGConverters + w) * kGAtoms + t];
+        }
+        a.Y64[(size_t)p * kGAtoms + t] = y;
+    }
+}
+
+// One CTA per pixel p (128 threads, thread = atom): C_p = (S_p + S_p^T) / 2,
+// then the atom-ordered draws in FP64 from C_p, Y_p and the current column.
+__global__ void __launch_bounds__(kGAtoms) gram_draw_kernel(GramArgs a)
+{
+    extern __shared__ __align__(16) double cs[];   // [128][129] C_p
+    __shared__ double delta[kGAtoms];
+    __shared__ double dcol[kGAtoms];
+    const int p = blockIdx.x;
+    const int t = threadIdx.x;
+    const int K = a.g.K, P = a.g.P;
+    const double* cg = a.C64 + (size_t)p * kGAtoms * kGAtoms;
+    for (int r = 0; r < kGAtoms; ++r) cs[r * (kGAtoms + 1) + t] = cg[(size_t)r * kGAtoms + t];
+    __syncthreads();
+    // thread t symmetrises the pairs (r, t), r < t: each unordered pair once
+    for (int r = 0; r < t; ++r) {
+        const double v = 0.5 * (cs[r * (kGAtoms + 1) + t] + cs[t * (kGAtoms + 1) + r]);
+        cs[r * (kGAtoms + 1) + t] = v;
+        cs[t * (kGAtoms + 1) + r] = v;
+    }
+    const double y = a.Y64[(size_t)p * kGAtoms + t];
+    const uint32_t t_it = launch_t(a.t, a.t_dev, a.sc);
+    const double ge = a.sc->gamma_eps;
+    double d = t < K ? (double)a.D[(long long)t * P + p] : 0.0;
+    dcol[t] = d;
+    __syncthreads();
+    // per atom, independent of the order: gain gamma_eps / Lambda and noise
+    // xi / sqrt(Lambda), Lambda = P + gamma_eps C_kk
+    const double ckk = cs[t * (kGAtoms + 1) + t];
+    const double lam = (double)P + ge * ckk;
+    const double gain = ge / lam;
+    double noise = 0.0;
+    if (t < K) {
+        const uint4 blk = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)t, t_it, kTagDict), seed_key(a.seed));
+        noise = normal64(blk.x, blk.y) / sqrt(lam);
+    }
+    // u = C_p d_p
+    double u = 0.0;
+    for (int b = 0; b < kGAtoms; ++b) u = fma(cs[t * (kGAtoms + 1) + b], dcol[b], u);
+    // the draws in atom order: A_k = Y_k - u_k + C_kk d_k excludes atom k
+    for (int k = 0; k < K; ++k) {
+        if (t == k) {
+            const double A = y - u + ckk * d;
+            const double dn = fma(gain, A, noise);
+            delta[k] = dn - d;
+            d = dn;
+            a.D[(long long)k * P + p] = (float)dn;
+        }
+        __syncthreads();
+        u = fma(cs[t * (kGAtoms + 1) + k], delta[k], u);
+    }
+}
+
+// ------------------------------------------------------------ host side --
+
+// The work items: for every pixel p, its patch list cut into segments of at
+// most `seg` patches; items ordered segment-major.  pitem: p -> its items.
+void gram_plan_items(const std::vector<int>& Rbase, int P, int seg, std::vector<int4>* items,
+                     std::vector<int>* pitem_start, std::vector<int>* pitem_idx)
+{
+    items->clear();
+    int max_segs = 0;
+    for (int p = 0; p < P; ++p) max_segs = std::max(max_segs, (Rbase[p + 1] - Rbase[p] + seg - 1) / seg);
+    std::vector<std::vector<int>> per_p(P);
+    for (int s = 0; s < max_segs; ++s)
+        for (int p = 0; p < P; ++p) {
+            // pixel p's list in nseg near-equal segments of at most seg patches
+            const int cnt = Rbase[p + 1] - Rbase[p];
+            const int nseg = (cnt + seg - 1) / seg;
+            if (s >= nseg) continue;
+            const int start = (int)((long long)cnt * s / nseg), end = (int)((long long)cnt * (s + 1) / nseg);
+            per_p[p].push_back((int)items->size());
+            items->push_back(make_int4(p, Rbase[p] + start, end - start, 0));
+        }
+    pitem_start->assign(P + 1, 0);
+    pitem_idx->clear();
+    for (int p = 0; p < P; ++p) {
+        (*pitem_start)[p] = (int)pitem_idx->size();
+        for (int it : per_p[p]) pitem_idx->push_back(it);
+    }
+    (*pitem_start)[P] = (int)pitem_idx->size();
+}
+
+size_t gram_smem_bytes() { return sizeof(float) * (size_t)kGSlots * (kGStageFloats + kGRawFloats); }
+
+// Xlist[e] = x[origin(Ilist[e]) + imgoff[p]] for the entries of pixel p.
+__global__ void xlist_kernel(Geom g, const int* Ilist, const int* Rbase, const int* imgoff, const float* x,
+                             float* Xlist)
+{
+    const int p = blockIdx.y;
+    const int e = Rbase[p] + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= Rbase[p + 1]) return;
+    Xlist[e] = x[patch_origin(g, Ilist[e]) + imgoff[p]];
+}
+
+cudaError_t launch_xlist(const Geom& g, const int* Ilist, const int* Rbase, int max_slots, const int* imgoff,
+                         const float* x, float* Xlist, cudaStream_t s)
+{
+    dim3 grid((unsigned int)((max_slots + 255) / 256 > 0 ? (max_slots + 255) / 256 : 1), (unsigned int)g.P);
+    xlist_kernel<<<grid, 256, 0, s>>>(g, Ilist, Rbase, imgoff, x, Xlist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram(const GramArgs& a, int grid, cudaStream_t s)
+{
+    const size_t smem = gram_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute((void*)gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    gram_kernel<<<grid, kGThreads, smem, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    gram_reduce_kernel<<<dim3((unsigned int)a.g.P, kGAtoms * kGAtoms / 256), 256, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t dsmem = sizeof(double) * (size_t)kGAtoms * (kGAtoms + 1);
+    e = cudaFuncSetAttribute((void*)gram_draw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
+    if (e != cudaSuccess) return e;
+    gram_draw_kernel<<<a.g.P, kGAtoms, dsmem, s>>>(a);
+    return cudaGetLastError();
+}
+
+bool gram_available(const Geom& g) { return g.K >= 1 && g.K <= kGAtoms; }
+
+}  // namespace sensai

@@ -127,11 +127,12 @@ cudaError_t launch_hyper_multi(const HyperArgs* args, const int* pi_start, const
 // s_ik ~ N(0, 1/gamma_s), from the Philox words an active entry uses for its
 // normal (counter (i, k, t, codes), words 1 and 2, the same Box-Muller
 // normal); the weight z s stays 0, so only s_ik^2 is kept, added to the
-// sweep's s^2 partial of the patch's work unit.  One warp per 32-patch
-// activity word over all atoms; lane 0 is the one writer of its unit.
-__global__ void __launch_bounds__(256) prior_s2_kernel(Geom g, const uint32_t* Zb, const DevScalars* sc, uint32_t t,
-                                                       bool t_dev, unsigned long long seed, int lanes,
-                                                       double* part_s2)
+// sweep's s^2 partial of the patch's work unit.  One warp per 32-slot
+// activity word over all atoms (slot s holds patch perm[s]); lane 0 is the
+// one writer of its unit.
+__global__ void __launch_bounds__(256) prior_s2_kernel(Geom g, const uint32_t* Zb, const int* perm,
+                                                       const DevScalars* sc, uint32_t t, bool t_dev,
+                                                       unsigned long long seed, int lanes, double* part_s2)
 {
     const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -139,7 +140,8 @@ __global__ void __launch_bounds__(256) prior_s2_kernel(Geom g, const uint32_t* Z
     const uint32_t t_it = launch_t(t, t_dev, sc);
     const float sd = rsqrtf((float)sc->gamma_s);
     const uint2 key = seed_key(seed);
-    const long long i = w * 32 + lane;
+    const long long slot = w * 32 + lane;
+    const long long i = perm ? (long long)perm[slot] : slot;
     float s2 = 0.0f;
     if (i < g.N) {
         for (int k = 0; k < g.K; ++k) {
@@ -153,11 +155,11 @@ __global__ void __launch_bounds__(256) prior_s2_kernel(Geom g, const uint32_t* Z
     if (lane == 0) part_s2[lanes == 2 ? 2 * w : w] += sum;
 }
 
-cudaError_t launch_prior_s2(const Geom& g, const uint32_t* Zb, const DevScalars* sc, uint32_t t, bool t_dev,
-                            unsigned long long seed, int lanes, double* part_s2, cudaStream_t s)
+cudaError_t launch_prior_s2(const Geom& g, const uint32_t* Zb, const int* perm, const DevScalars* sc, uint32_t t,
+                            bool t_dev, unsigned long long seed, int lanes, double* part_s2, cudaStream_t s)
 {
     if (lanes != 1 && lanes != 2) return cudaErrorInvalidValue;
-    prior_s2_kernel<<<(unsigned int)((g.NW + 7) / 8), 256, 0, s>>>(g, Zb, sc, t, t_dev, seed, lanes, part_s2);
+    prior_s2_kernel<<<(unsigned int)((g.NW + 7) / 8), 256, 0, s>>>(g, Zb, perm, sc, t, t_dev, seed, lanes, part_s2);
     return cudaGetLastError();
 }
 
@@ -378,12 +380,14 @@ __global__ void __launch_bounds__(kGeParts) gamma_eps_merge_kernel(const double*
 
 // Statistics of an arbitrary state (after set_state / set_dictionary): active
 // counts per atom and per-chunk sum of s^2.
-__global__ void code_stats_kernel(Geom g, const float* W, const uint32_t* Zb, int* m, double* part_s2)
+__global__ void code_stats_kernel(Geom g, const float* W, const uint32_t* Zb, const int* perm, int* m,
+                                  double* part_s2)
 {
     const long long chunk = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (chunk >= g.NW) return;
-    const long long i = chunk * 32 + lane;
+    const long long slot = chunk * 32 + lane;
+    const long long i = perm ? (long long)perm[slot] : slot;
     double s2 = 0.0;
     for (int k = 0; k < g.K; ++k) {
         const uint32_t zw = Zb[(long long)k * g.NW + chunk];
@@ -397,29 +401,64 @@ __global__ void code_stats_kernel(Geom g, const float* W, const uint32_t* Zb, in
     if (lane == 0) part_s2[chunk] = s2;
 }
 
-// Residual of an arbitrary state, written to the per-pixel slots, with the
-// per-chunk squared norm.
-__global__ void residual_kernel(Geom g, const float* x, const uint16_t* obs, const uint16_t* nobs,
-                                const int* imgoff, const float* D, const float* W, const uint32_t* Zb,
-                                const int* pos, float* R, double* part_r2)
+// The residual of the current state, r = x - D w on every observed pixel,
+// written to the per-pixel slots, with the per-chunk squared norm.  It is the
+// residual a code sweep starts from: per pixel, the stored weights' products
+// are subtracted in atom order, zero weights skipped, each as one fused
+// multiply-add -- the arithmetic of the sweep's own rebuild, so both give the
+// same bits.  One thread per sweep slot, pixels in chunks of 16; the next
+// weight record is loaded behind the current one.
+constexpr int kResidChunk = 16;
+
+__global__ void __launch_bounds__(256) residual_kernel(Geom g, const float* x, const uint16_t* obs,
+                                                       const uint16_t* nobs, const int* perm, const int* imgoff,
+                                                       const float* __restrict__ D, const float* W, const int* pos,
+                                                       float* R, double* part_r2)
 {
     const long long chunk = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (chunk >= g.NW) return;
-    const long long i = chunk * 32 + lane;
+    const long long slot = chunk * 32 + lane;   // tables by sweep slot, weights by patch
     double r2 = 0.0;
-    if (i < g.N) {
+    if (slot < g.N) {
+        const long long i = perm ? (long long)perm[slot] : slot;
         const long long org = patch_origin(g, i);
-        const int no = nobs[i];
-        for (int j = 0; j < no; ++j) {
-            const int p = obs[(long long)j * g.N + i];
-            float r = x[org + imgoff[p]];
-            for (int k = 0; k < g.K; ++k) {
-                const float w = W[wblock(g, k / kAtomBlock, i) + k % kAtomBlock];
-                if (w != 0.0f) r = fmaf(-D[(long long)k * g.P + p], w, r);
+        const int no = nobs[slot];
+        for (int j0 = 0; j0 < no; j0 += kResidChunk) {
+            const int nj = no - j0 < kResidChunk ? no - j0 : kResidChunk;
+            int pj[kResidChunk];
+            float r[kResidChunk];
+#pragma unroll
+            for (int u = 0; u < kResidChunk; ++u) {
+                pj[u] = 0;
+                r[u] = 0.0f;
+                if (u < nj) {
+                    pj[u] = obs[(long long)(j0 + u) * g.N + slot];
+                    r[u] = x[org + imgoff[pj[u]]];
+                }
             }
-            R[pos[(long long)j * g.N + i]] = r;
-            r2 += (double)r * r;
+            W8 nb = load_w8(W + wblock(g, 0, i));
+            for (int kb = 0; kb < g.KB; ++kb) {
+                const W8 wb = nb;
+                if (kb + 1 < g.KB) nb = load_w8(W + wblock(g, kb + 1, i));
+#pragma unroll
+                for (int kk = 0; kk < kAtomBlock; ++kk) {
+                    const float w = wb.v[kk];
+                    if (w != 0.0f) {
+                        const float* dk = D + (long long)(kb * kAtomBlock + kk) * g.P;
+#pragma unroll
+                        for (int u = 0; u < kResidChunk; ++u)
+                            if (u < nj) r[u] = fmaf(__ldg(dk + pj[u]), -w, r[u]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kResidChunk; ++u) {
+                if (u < nj) {
+                    R[pos[(long long)(j0 + u) * g.N + slot]] = r[u];
+                    r2 += (double)r[u] * r[u];
+                }
+            }
         }
     }
     r2 = warp_sum(r2);
@@ -451,37 +490,41 @@ cudaError_t launch_init_gamma_eps(const Geom& g, const float* x, const uint32_t*
     return cudaGetLastError();
 }
 
-cudaError_t launch_code_stats(const Geom& g, const float* W, const uint32_t* Zb, int* m, double* part_s2,
-                              cudaStream_t s)
+cudaError_t launch_code_stats(const Geom& g, const float* W, const uint32_t* Zb, const int* perm, int* m,
+                              double* part_s2, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(m, 0, sizeof(int) * g.K, s);
     if (e != cudaSuccess) return e;
-    code_stats_kernel<<<blocks_for(g.NW, 8), 256, 0, s>>>(g, W, Zb, m, part_s2);
+    code_stats_kernel<<<blocks_for(g.NW, 8), 256, 0, s>>>(g, W, Zb, perm, m, part_s2);
     return cudaGetLastError();
 }
 
 cudaError_t launch_residual(const Geom& g, const float* x, const uint16_t* obs, const uint16_t* nobs,
-                            const int* imgoff, const float* D, const float* W, const uint32_t* Zb,
-                            const int* pos, float* R, double* part_r2, cudaStream_t s)
+                            const int* perm, const int* imgoff, const float* D, const float* W, const int* pos,
+                            float* R, double* part_r2, cudaStream_t s)
 {
-    residual_kernel<<<blocks_for(g.NW, 8), 256, 0, s>>>(g, x, obs, nobs, imgoff, D, W, Zb, pos, R, part_r2);
+    residual_kernel<<<blocks_for(g.NW, 8), 256, 0, s>>>(g, x, obs, nobs, perm, imgoff, D, W, pos, R, part_r2);
     return cudaGetLastError();
 }
 
-// Patch-major (Z bytes, S floats) <-> device layout (Zb bits [K][NW], W [K][N]).
-__global__ void export_codes_kernel(Geom g, const float* W, const uint32_t* Zb, uint8_t* Z, float* S)
+// Patch-major (Z bytes, S floats) <-> device layout (Zb bits [K][NW] by sweep
+// slot, slot s holding patch perm[s]; W [KB][Npad][8] by patch).
+__global__ void export_codes_kernel(Geom g, const float* W, const uint32_t* Zb, const int* perm, uint8_t* Z,
+                                    float* S)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.N * g.K) return;
-    const long long i = idx / g.K;
+    const long long slot = idx / g.K;
     const int k = (int)(idx % g.K);
-    const bool z = (Zb[(long long)k * g.NW + (i >> 5)] >> (i & 31)) & 1u;
-    Z[idx] = z ? 1 : 0;
-    S[idx] = z ? W[wblock(g, k / kAtomBlock, i) + k % kAtomBlock] : 0.0f;
+    const long long i = perm ? (long long)perm[slot] : slot;
+    const bool z = (Zb[(long long)k * g.NW + (slot >> 5)] >> (slot & 31)) & 1u;
+    Z[i * g.K + k] = z ? 1 : 0;
+    S[i * g.K + k] = z ? W[wblock(g, k / kAtomBlock, i) + k % kAtomBlock] : 0.0f;
 }
 
-// One thread per (atom, 32-patch word).
-__global__ void import_codes_kernel(Geom g, const uint8_t* Z, const float* S, float* W, uint32_t* Zb)
+// One thread per (atom, 32-slot word).
+__global__ void import_codes_kernel(Geom g, const uint8_t* Z, const float* S, const int* perm, float* W,
+                                    uint32_t* Zb)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)g.K * g.NW) return;
@@ -489,8 +532,9 @@ __global__ void import_codes_kernel(Geom g, const uint8_t* Z, const float* S, fl
     const long long w = idx % g.NW;
     uint32_t bits = 0;
     for (int b = 0; b < 32; ++b) {
-        const long long i = w * 32 + b;
-        if (i >= g.N) break;
+        const long long slot = w * 32 + b;
+        if (slot >= g.N) break;
+        const long long i = perm ? (long long)perm[slot] : slot;
         const bool z = Z[i * g.K + k] != 0;
         if (z) bits |= 1u << b;
         W[wblock(g, k / kAtomBlock, i) + k % kAtomBlock] = z ? S[i * g.K + k] : 0.0f;
@@ -503,17 +547,17 @@ __global__ void logit_kernel(int K, const double* pi, float* lpi)
     for (int k = threadIdx.x; k < K; k += blockDim.x) lpi[k] = (float)(log(pi[k]) - log1p(-pi[k]));
 }
 
-cudaError_t launch_export_codes(const Geom& g, const float* W, const uint32_t* Zb, uint8_t* Z, float* S,
-                                cudaStream_t s)
+cudaError_t launch_export_codes(const Geom& g, const float* W, const uint32_t* Zb, const int* perm, uint8_t* Z,
+                                float* S, cudaStream_t s)
 {
-    export_codes_kernel<<<blocks_for(g.N * g.K, 256), 256, 0, s>>>(g, W, Zb, Z, S);
+    export_codes_kernel<<<blocks_for(g.N * g.K, 256), 256, 0, s>>>(g, W, Zb, perm, Z, S);
     return cudaGetLastError();
 }
 
-cudaError_t launch_import_codes(const Geom& g, const uint8_t* Z, const float* S, float* W, uint32_t* Zb,
-                                cudaStream_t s)
+cudaError_t launch_import_codes(const Geom& g, const uint8_t* Z, const float* S, const int* perm, float* W,
+                                uint32_t* Zb, cudaStream_t s)
 {
-    import_codes_kernel<<<blocks_for((long long)g.K * g.NW, 256), 256, 0, s>>>(g, Z, S, W, Zb);
+    import_codes_kernel<<<blocks_for((long long)g.K * g.NW, 256), 256, 0, s>>>(g, Z, S, perm, W, Zb);
     return cudaGetLastError();
 }
 

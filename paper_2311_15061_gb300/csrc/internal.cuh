@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "sensai.h"
 
@@ -316,20 +317,27 @@ __device__ inline double block_sum(double v, double* scratch)
 
 // ------------------------------------------------------ kernel arguments --
 
+// Per-patch tables of the code sweep are in sweep order: position (slot) s
+// of the sweep holds patch perm[s] (perm null: the identity).  A warp sweeps
+// 32 consecutive slots, so its activity word Zb[k][w] holds the bits of the
+// patches at slots 32 w .. 32 w + 31.  Weights W stay in patch order.
 struct SweepArgs {
     Geom g;
     const float* x;            // frame
-    const uint16_t* obs;       // [maxobs][N] within-patch index of each observed pixel
-    const uint16_t* nobs;      // [N] observed pixels per patch
+    const uint16_t* obs;       // [maxobs][N] within-patch index of each observed pixel, by slot
+    const uint16_t* nobs;      // [N] observed pixels per patch, by slot
+    const int* perm = nullptr; // [Npad] slot -> patch (slots >= N: themselves); null: identity
     const int* imgoff;         // [P] frame offset of within-patch pixel p
     const float* D;            // [K][P]
-    float* W;                  // [KB][Npad][8] weights (0 where inactive)
-    uint32_t* Zb;              // [K][NW] activity bits (written)
+    float* W;                  // [KB][Npad][8] weights (0 where inactive), by patch
+    uint32_t* Zb;              // [K][NW] activity bits by slot (written)
     const float* lpi;          // [K] logit(pi_k)
     const DevScalars* sc;
-    const int* pos;            // [maxobs][N] residual position of observed pixel j of patch i
-    float* R;                  // residual in the dictionary step's layout, R[pos[j][i]]
-                               // (null: inpainting only, the residual is not kept)
+    const int* pos;            // [maxobs][N] residual position of observed pixel j of the patch at a slot
+    float* R;                  // residual in the dictionary step's layout, R[pos[j][slot]]
+                               // (null: serving, the residual is not kept)
+    const float* R_in = nullptr;   // non-null: R holds the current residual at launch (the
+                                   // sweep starts from it instead of rebuilding x - D w)
     double* part_s2;           // [NW] per 32-patch chunk
     double* part_r2;           // [NW] per 32-patch chunk
     unsigned int* chunk_counter;  // work counter, zeroed before each launch
@@ -342,7 +350,7 @@ struct SweepArgs {
     const float* Dsl = nullptr;   // [slices][slice_stride] slices in shared-memory layout
     int slice_atoms = 0;          // KS, a multiple of 8
     int slices = 0;               // ceil(8 KB / KS)
-    long long slice_stride = 0;   // floats per slice, ((P + 1) (KS | 1)) rounded up to 4
+    long long slice_stride = 0;   // floats per slice, ((P + 1) (KS + 1)) rounded up to 4
 };
 
 struct DictArgs {
@@ -394,6 +402,29 @@ struct DictSpaceArgs {
     int own_max;
     unsigned long long seed;
     uint32_t t;
+};
+
+// The dictionary step in its dense-statistics form (gram.cu).
+struct GramArgs {
+    Geom g;
+    const float* W;            // [KB][Npad][8]
+    const int* Ilist;          // per pixel p: the patches observing p (Rbase layout)
+    const float* Xlist;        // the frame value of each (p, patch) entry of Ilist
+    const int4* items;         // (p, first entry, entries, -): segments of the per-pixel lists
+    long long n_items;
+    float* Cpart;              // [items][128][128] per-item partials T^T, C = (T + T^T) / 2 (FP32)
+    float* Ypart;              // [items][4][128] per-item correlation partials (FP32)
+    double* C64;               // [P][128][128] FP64 sums of the partials (symmetrised by the draws)
+    double* Y64;               // [P][128] Y_p
+    const int* pitem_start;    // [P + 1] pixel p's items: pitem_idx[pitem_start[p] ..]
+    const int* pitem_idx;
+    float* D;                  // [K][P], redrawn in place
+    const DevScalars* sc;      // gamma_eps, t_iter
+    unsigned long long seed;
+    uint32_t t;
+    bool t_dev = false;
+    bool tf32 = false;         // TF32-level statistics (one pass) instead of FP32-level (split)
+    int* status;               // SENSAI_ETIMEOUT on a device-side wait that gives up
 };
 
 struct HyperArgs {
@@ -511,6 +542,10 @@ long long slice_capacity_floats(const Geom& g);
 // null) receives the number of kernels launched.
 cudaError_t launch_code_sweep(SweepArgs a, const SweepPlan& plan, int maxobs, float* Dsl, cudaStream_t s,
                               int* nlaunch);
+// The residual x - D W rebuilt by the sweep's rebuild into a.R (through
+// a.pos) and its squares' sums per work unit into a.part_r2 (resident
+// dictionary only).
+cudaError_t launch_rebuild(const SweepArgs& a, int maxobs, int grid, cudaStream_t s);
 long long slice_stride_floats(const Geom& g, int KS);
 size_t tiled_smem_bytes(const Geom& g, int KS);
 int tiled_slice_atoms(const Geom& g, int maxobs, int device);
@@ -522,8 +557,8 @@ cudaError_t launch_dict(const DictArgs& a, int max_slots, cudaStream_t s);
 // sweep with the same (t, t_dev, seed), adds to part_s2 the squares of the
 // prior draws of the entries that sweep left inactive.  lanes: the sweep's
 // lanes per patch (its partials are per 32 / lanes patches).
-cudaError_t launch_prior_s2(const Geom& g, const uint32_t* Zb, const DevScalars* sc, uint32_t t, bool t_dev,
-                            unsigned long long seed, int lanes, double* part_s2, cudaStream_t s);
+cudaError_t launch_prior_s2(const Geom& g, const uint32_t* Zb, const int* perm, const DevScalars* sc, uint32_t t,
+                            bool t_dev, unsigned long long seed, int lanes, double* part_s2, cudaStream_t s);
 cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);   // one kernel: K pi draws + gamma_s, gamma_eps
 // Batched: pi_start is the prefix of K_i (one CTA per atom), gamma_start = 0..n.
 cudaError_t launch_hyper_multi(const HyperArgs* args, const int* pi_start, const int* gamma_start, int n,
@@ -542,9 +577,27 @@ cudaError_t ds_build(const Geom& g, const uint8_t* host_mask, const uint16_t* ob
                      int* pos, float** R, DictSpacePlan* plan, cudaStream_t s);
 void ds_free(DictSpacePlan* plan);
 // pos[j][i] for the per-chain slot layout of dict.cu.
+// Posterior-mean reconstruction: acc[u] += frame[u] (FP64); out = acc / count.
+cudaError_t launch_mean_accumulate(long long n, const float* frame, double* acc, cudaStream_t s);
+cudaError_t launch_mean_finish(long long n, const double* acc, long long count, float* out, cudaStream_t s);
+// Rewrites obs, pos ([maxobs][N]) and nobs ([N]) into sweep order (slot s
+// holds patch perm[s]).
+cudaError_t launch_sweep_order(const Geom& g, int maxobs, const int* perm, const uint16_t* obs_in,
+                               const uint16_t* nobs_in, const int* pos_in, uint16_t* obs_out, uint16_t* nobs_out,
+                               int* pos_out, cudaStream_t s);
+// Stable order of the patches by decreasing count (counting sort on the
+// host): perm[s] for s < N, then perm[s] = s up to Npad.
+void sweep_order_host(const uint16_t* nobs, long long N, long long Npad, int* perm);
 cudaError_t launch_pos_slots(const Geom& g, const uint16_t* obs, const uint16_t* nobs, const uint32_t* Ibits,
                              const uint32_t* Ipre, const int* Rbase, int* pos, cudaStream_t s);
 cudaError_t launch_dict_space(const DictSpaceArgs& a, const DictSpacePlan& plan, cudaStream_t s);
+// The dense-statistics dictionary step (gram.cu): K <= 128.
+bool gram_available(const Geom& g);
+void gram_plan_items(const std::vector<int>& Rbase, int P, int seg, std::vector<int4>* items,
+                     std::vector<int>* pitem_start, std::vector<int>* pitem_idx);
+cudaError_t launch_xlist(const Geom& g, const int* Ilist, const int* Rbase, int max_slots, const int* imgoff,
+                         const float* x, float* Xlist, cudaStream_t s);
+cudaError_t launch_gram(const GramArgs& a, int grid, cudaStream_t s);   // statistics, then the draws
 cudaError_t launch_geometry(const Geom& g, const uint8_t* mask_bytes, uint32_t* mask_bits, int* imgoff,
                             uint16_t* nobs, int* maxobs, unsigned long long* total, cudaStream_t s);
 cudaError_t launch_fill_obs(const Geom& g, const uint32_t* mask_bits, const int* imgoff, uint16_t* obs, cudaStream_t s);
@@ -572,15 +625,15 @@ cudaError_t launch_init_state(const Geom& g, float* D, double* pi, float* lpi, D
 constexpr int kInitGammaEpsScratch = 3 * 256;
 cudaError_t launch_init_gamma_eps(const Geom& g, const float* x, const uint32_t* mbits, DevScalars* sc,
                                   double* scratch, cudaStream_t s);
-cudaError_t launch_code_stats(const Geom& g, const float* W, const uint32_t* Zb, int* m, double* part_s2,
-                              cudaStream_t s);
+cudaError_t launch_code_stats(const Geom& g, const float* W, const uint32_t* Zb, const int* perm, int* m,
+                              double* part_s2, cudaStream_t s);
 cudaError_t launch_residual(const Geom& g, const float* x, const uint16_t* obs, const uint16_t* nobs,
-                            const int* imgoff, const float* D, const float* W, const uint32_t* Zb,
-                            const int* pos, float* R, double* part_r2, cudaStream_t s);
-cudaError_t launch_export_codes(const Geom& g, const float* W, const uint32_t* Zb, uint8_t* Z, float* S,
-                                cudaStream_t s);
-cudaError_t launch_import_codes(const Geom& g, const uint8_t* Z, const float* S, float* W, uint32_t* Zb,
-                                cudaStream_t s);
+                            const int* perm, const int* imgoff, const float* D, const float* W, const int* pos,
+                            float* R, double* part_r2, cudaStream_t s);
+cudaError_t launch_export_codes(const Geom& g, const float* W, const uint32_t* Zb, const int* perm, uint8_t* Z,
+                                float* S, cudaStream_t s);
+cudaError_t launch_import_codes(const Geom& g, const uint8_t* Z, const float* S, const int* perm, float* W,
+                                uint32_t* Zb, cudaStream_t s);
 cudaError_t launch_logit(int K, const double* pi, float* lpi, cudaStream_t s);
 
 }  // namespace sensai

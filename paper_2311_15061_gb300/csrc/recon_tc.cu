@@ -68,9 +68,11 @@ __device__ __forceinline__ int rt_off(int row, int k)
 
 __device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
+// Bounded wait for a phase; the global timer (a slow read) only once the
+// first try has failed.
 __device__ __forceinline__ bool rt_wait(uint64_t* bar, uint32_t parity)
 {
-    const unsigned long long t0 = global_ns();
+    unsigned long long t0 = 0;
     for (long long spins = 0; spins < kRTSpins; ++spins) {
         uint32_t ok;
         asm volatile(
@@ -80,7 +82,8 @@ __device__ __forceinline__ bool rt_wait(uint64_t* bar, uint32_t parity)
             : "r"(rt_smem(bar)), "r"(parity)
             : "memory");
         if (ok) return true;
-        if ((spins & 63) == 63 && global_ns() - t0 > kWaitLimitNs) break;
+        if (spins == 0) t0 = global_ns();
+        else if ((spins & 63) == 0 && global_ns() - t0 > kWaitLimitNs) break;
     }
     return false;
 }

@@ -297,7 +297,7 @@ static sensai_status process_frame(ServeEngine* e, ServeSlot* sl, const ServeReq
         a.keys = philox_round_keys(fseed);
         a.t = e->t0 + (uint32_t)sw;
         FRAME_TRY(launch_code_sweep(a, plan, maxobs, sl->Dsl, s, nullptr));
-        if (e->full_s) FRAME_TRY(launch_prior_s2(g, sl->Zb, sl->sc, a.t, false, fseed, plan.lanes, sl->part_s2, s));
+        if (e->full_s) FRAME_TRY(launch_prior_s2(g, sl->Zb, nullptr, sl->sc, a.t, false, fseed, plan.lanes, sl->part_s2, s));
         HyperArgs h{};
         h.g = g;
         h.Zb = sl->Zb;

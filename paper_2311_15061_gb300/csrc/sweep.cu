@@ -22,10 +22,11 @@
 // zero row (p = P) that padded observation slots point at, so the inner loops
 // need no predicates.  The residual of the patch lives in registers (MAXOBS
 // slots, chosen per problem from the largest |Omega_i|).  Patch extraction is
-// fused: the observed pixels are gathered from the frame and the residual
-// rebuilt from the stored weights at the start of each sweep.  At the end the
-// residual is written, through the position table, into the layout the
-// dictionary kernel consumes.  The per-block code is in sweep_block.cuh,
+// fused: at the start of each sweep the residual of a patch's observed pixels
+// is read from the layout the dictionary kernel keeps it in (or, where no
+// residual is kept, the observed pixels are gathered from the frame and the
+// residual rebuilt from the stored weights).  At the end the residual is
+// written back, through the position table, for the dictionary kernel.  The per-block code is in sweep_block.cuh,
 // shared with the streamed-dictionary kernel (sweep_tiled.cu); the batched
 // kernel runs the same body on per-instance arguments.
 #include "sweep_block.cuh"
@@ -38,19 +39,19 @@ constexpr int kSweepWarps = kSweepThreads / 32;
 template <int MAXOBS, int LANES>
 __device__ __forceinline__ void sweep_body(const SweepArgs& a)
 {
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) float smem[];
     const int K = a.g.K, P = a.g.P, KB = a.g.KB;
     const int Kpad = KB * kAtomBlock;
-    const int ldK = Kpad | 1;
+    const int ldK = Kpad + kDictColumnOffset;   // odd: rows fall in different banks
     const long long N = a.g.N, Npad = a.g.Npad;
     const int NW = a.g.NW;
-    float* Ds = smem;                      // (P + 1) x ldK; row P and atoms >= K are zero
+    float* Ds = smem;                      // (P + 1) x ldK; row P, column 0 and atoms >= K are zero
     float* lpi = Ds + (P + 1) * ldK;       // Kpad
     __shared__ unsigned int chunk_slot[kSweepWarps];
 
     for (int idx = threadIdx.x; idx < (P + 1) * ldK; idx += blockDim.x) {
-        const int p = idx / ldK, k = idx - p * ldK;
-        Ds[idx] = (p < P && k < K) ? a.D[(long long)k * P + p] : 0.0f;
+        const int p = idx / ldK, k = idx - p * ldK - kDictColumnOffset;
+        Ds[idx] = (p < P && k >= 0 && k < K) ? a.D[(long long)k * P + p] : 0.0f;
     }
     for (int k = threadIdx.x; k < Kpad; k += blockDim.x) lpi[k] = k < K ? a.lpi[k] : 0.0f;
     __syncthreads();
@@ -60,6 +61,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int half = LANES == 1 ? 0 : (lane & 1);
     const unsigned int units = (unsigned int)NW * LANES;   // 32-patch chunks, or 16-patch halves
+    const uint32_t col0 = smem_addr(Ds) + 4u * kDictColumnOffset;   // atom 0's column, row 0
     CodeTally tl;
 
     for (;;) {
@@ -68,39 +70,52 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
         const unsigned int unit = chunk_slot[warp];
         __syncwarp();
         if (unit >= units) break;
-        const long long i = (long long)unit * PatchLanes<LANES>::kPatchesPerWarp + lane / LANES;   // < Npad
-        const bool valid = i < N;
+        const long long slot = (long long)unit * PatchLanes<LANES>::kPatchesPerWarp + lane / LANES;   // < Npad
+        const long long i = slot_patch(a, slot);
+        LanePatch lp;
+        lp.i = i;
+        lp.valid = i < N;
+        lp.nobs = lp.valid ? (int)a.nobs[slot] : 0;
+        lp.unit = unit;
+        lp.lane = lane;
+        const int nl = LANES == 1 ? lp.nobs : (lp.nobs + 1 - half) / 2;   // this lane's pixels
+        lp.wmax = __reduce_max_sync(0xffffffffu, nl);
+        const long long org = lp.valid ? patch_origin(a.g, i) : 0;
 
-        const int nobs = valid ? (int)a.nobs[i] : 0;
-        const int nl = LANES == 1 ? nobs : (nobs + 1 - half) / 2;   // this lane's pixels
-        const int wmax = __reduce_max_sync(0xffffffffu, nl);
-        const long long org = valid ? patch_origin(a.g, i) : 0;
+        PixelAddr<MAXOBS> ad;
+        ad.base = col0;
+        ad.pitch = 4u * ldK;
+        Resid<MAXOBS> r;
+        const bool from_resid = a.R_in != nullptr;
+        gather_patch<MAXOBS, LANES>(a, slot, nl, org, ad, r, half, from_resid);
 
-        PixelOffsets<MAXOBS> offK;
-        float r[MAXOBS];
-        gather_patch<MAXOBS, LANES>(a, i, nl, org, ldK, offK, r, half);
-
-        // residual r = x - D w on the observed pixels, from the stored weights
-        for (int kb = 0; kb < KB; ++kb)
-            rebuild_block<MAXOBS>(Ds + kb * kAtomBlock, offK, r, wmax,
-                                  load_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock));
+        // else the residual r = x - D w on the observed pixels, from the stored weights
+        if (!from_resid) {
+            for (int kb = 0; kb < KB; ++kb) {
+                ad.rebase(col0 + 32u * kb, lp.wmax);
+                rebuild_block<MAXOBS>(ad, r, lp.wmax, load_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock));
+            }
+        }
 
         float s2 = 0.0f;
+        AtomCarry carry;
+        carry.dw = 0.0f;
+        carry.rnd = code_random(i, 0, t_it, a.keys);
         W8 nb = load_w8(a.W + (long long)i * kAtomBlock);
         for (int kb = 0; kb < KB; ++kb) {
-            // the block's weights rotate through w0..w7: each atom consumes w0
-            // and appends its new weight, so after 8 atoms they are in order
-            float w0 = nb.v[0], w1 = nb.v[1], w2 = nb.v[2], w3 = nb.v[3];
-            float w4 = nb.v[4], w5 = nb.v[5], w6 = nb.v[6], w7 = nb.v[7];
+            W8 wb = nb;
             if (kb + 1 < KB)   // prefetch the next block behind this block's work
                 nb = load_w8(a.W + ((long long)(kb + 1) * Npad + i) * kAtomBlock);
             const int kbase = kb * kAtomBlock;
-            code_block<MAXOBS, LANES>(Ds + kbase, lpi + kbase, offK, r, wmax, nobs, i, valid, kbase,
-                                      min(kAtomBlock, K - kbase), c, a.keys, t_it, a.Zb, NW, unit, lane,
-                                      w0, w1, w2, w3, w4, w5, w6, w7, s2, tl);
-            if (half == 0) store_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock, w0, w1, w2, w3, w4, w5, w6, w7);
+            ad.rebase(col0 + 32u * kb, lp.wmax);
+            const bool changed = code_block<MAXOBS, LANES, true>(ad, r, lpi + kbase, lp, kbase, K, c, a.keys, t_it,
+                                                                 a.Zb, NW, wb, carry, s2, tl);
+            if (half == 0 && changed)
+                store_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock, wb.v[0], wb.v[1], wb.v[2], wb.v[3], wb.v[4],
+                         wb.v[5], wb.v[6], wb.v[7]);
         }
-        finish_patch<MAXOBS, LANES>(a, r, wmax, nl, i, unit, lane, s2);
+        apply_update<MAXOBS>(ad, r, lp.wmax, carry.dw);   // the last atom's rank-1 update
+        finish_patch<MAXOBS, LANES>(a, r, lp.wmax, nl, slot, unit, lane, s2);
     }
     flush_counts(a, lane, tl);
 }
@@ -123,21 +138,90 @@ __global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 && LANES == 1 ? 2
     sweep_body<MAXOBS, LANES>(a);
 }
 
+// The residual x - D W of every patch on its observed pixels, rebuilt from
+// the stored weights with the sweep's own rebuild (the same fused
+// multiply-adds in the same atom order, so the bits equal those of a sweep
+// that rebuilds it itself), written through the position table into R; the
+// FP64 sum of its squares per work unit into part_r2.  Work units in a
+// grid-stride loop.
+template <int MAXOBS, int LANES>
+__global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 && LANES == 1 ? 2 : 1)) rebuild_kernel(const SweepArgs a)
+{
+    extern __shared__ __align__(16) float smem[];
+    const int K = a.g.K, P = a.g.P, KB = a.g.KB;
+    const int Kpad = KB * kAtomBlock;
+    const int ldK = Kpad + kDictColumnOffset;
+    const long long N = a.g.N, Npad = a.g.Npad;
+    float* Ds = smem;
+    for (int idx = threadIdx.x; idx < (P + 1) * ldK; idx += blockDim.x) {
+        const int p = idx / ldK, k = idx - p * ldK - kDictColumnOffset;
+        Ds[idx] = (p < P && k >= 0 && k < K) ? a.D[(long long)k * P + p] : 0.0f;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int half = LANES == 1 ? 0 : (lane & 1);
+    const unsigned int units = (unsigned int)a.g.NW * LANES;
+    const uint32_t col0 = smem_addr(Ds) + 4u * kDictColumnOffset;
+    for (unsigned int unit = blockIdx.x * kSweepWarps + warp; unit < units; unit += gridDim.x * kSweepWarps) {
+        const long long slot = (long long)unit * PatchLanes<LANES>::kPatchesPerWarp + lane / LANES;
+        const long long i = slot_patch(a, slot);
+        const bool valid = i < N;
+        const int nobs = valid ? (int)a.nobs[slot] : 0;
+        const int nl = LANES == 1 ? nobs : (nobs + 1 - half) / 2;
+        const int wmax = __reduce_max_sync(0xffffffffu, nl);
+        const long long org = valid ? patch_origin(a.g, i) : 0;
+        PixelAddr<MAXOBS> ad;
+        ad.base = col0;
+        ad.pitch = 4u * ldK;
+        Resid<MAXOBS> r;
+        gather_patch<MAXOBS, LANES>(a, slot, nl, org, ad, r, half, false);
+        W8 nb = load_w8(a.W + (long long)i * kAtomBlock);
+        for (int kb = 0; kb < KB; ++kb) {
+            const W8 wb = nb;
+            if (kb + 1 < KB) nb = load_w8(a.W + ((long long)(kb + 1) * Npad + i) * kAtomBlock);
+            ad.rebase(col0 + 32u * kb, wmax);
+            rebuild_block<MAXOBS>(ad, r, wmax, wb);
+        }
+        double r2 = 0.0;
+#pragma unroll
+        for (int g4 = 0; g4 < MAXOBS / 4; ++g4) {
+            if (4 * g4 >= wmax) break;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int jj = 4 * g4 + u;
+                if (jj < nl) {
+                    const float v = r.get(jj);
+                    a.R[a.pos[(long long)(jj * LANES + half) * N + slot]] = v;
+                    r2 += (double)v * v;
+                }
+            }
+        }
+        r2 = warp_sum(r2);
+        if (lane == 0) a.part_r2[unit] = r2;
+    }
+}
+
 int sweep_block_size() { return kSweepThreads; }
 
 int sweep_smem_bytes(const Geom& g)
 {
     const int Kpad = g.KB * kAtomBlock;
-    const int ldK = Kpad | 1;
+    const int ldK = Kpad + kDictColumnOffset;
     return (int)(sizeof(float) * ((size_t)(g.P + 1) * ldK + Kpad));
 }
 
+// Kernel variants: 0 the sweep, 1 the batched sweep, 2 the residual rebuild.
 template <int MAXOBS, int LANES = 1>
-static void* kernel_ptr(bool multi) { return multi ? (void*)sweep_multi_kernel<MAXOBS, LANES> : (void*)sweep_kernel<MAXOBS, LANES>; }
+static void* kernel_ptr(int kind)
+{
+    if (kind == 1) return (void*)sweep_multi_kernel<MAXOBS, LANES>;
+    if (kind == 2) return (void*)rebuild_kernel<MAXOBS, LANES>;
+    return (void*)sweep_kernel<MAXOBS, LANES>;
+}
 
 int sweep_lanes(int maxobs) { return maxobs > 96 ? 2 : 1; }
 
-static void* select_kernel(int maxobs, bool multi = false)
+static void* select_kernel(int maxobs, int multi = 0)
 {
     if (maxobs > 96) {   // two lanes per patch: per-lane capacity 64 / 96 / 112 / 128
         if (maxobs <= 128) return kernel_ptr<64, 2>(multi);
@@ -170,7 +254,7 @@ int sweep_variant(int maxobs)
 cudaError_t launch_sweep_multi(const SweepArgs* args, const int* cta_start, int n, int maxobs, int grid,
                                size_t smem, cudaStream_t s)
 {
-    void* fn = select_kernel(maxobs, true);
+    void* fn = select_kernel(maxobs, 1);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -180,7 +264,7 @@ cudaError_t launch_sweep_multi(const SweepArgs* args, const int* cta_start, int 
 
 int sweep_multi_ctas_per_sm(int maxobs, size_t smem)
 {
-    void* fn = select_kernel(maxobs, true);
+    void* fn = select_kernel(maxobs, 1);
     int per_sm = 0;
     if (!fn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSweepThreads, smem) != cudaSuccess)
@@ -196,6 +280,8 @@ cudaError_t preload_sweep_variants()
     for (int m : obs) {
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, select_kernel(m));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncGetAttributes(&fa, select_kernel(m, 2));
         if (e != cudaSuccess) return e;
     }
     return preload_tiled_variants();
@@ -226,6 +312,17 @@ cudaError_t launch_sweep(const SweepArgs& a, int maxobs, int grid, cudaStream_t 
     if (e != cudaSuccess) return e;
     const int smem = sweep_smem_bytes(a.g);
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&a};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kSweepThreads), args, (size_t)smem, s);
+}
+
+cudaError_t launch_rebuild(const SweepArgs& a, int maxobs, int grid, cudaStream_t s)
+{
+    void* fn = select_kernel(maxobs, 2);
+    if (!fn || !a.R || !a.part_r2) return cudaErrorInvalidValue;
+    const int smem = sweep_smem_bytes(a.g);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&a};
     return cudaLaunchKernel(fn, dim3(grid), dim3(kSweepThreads), args, (size_t)smem, s);

@@ -62,13 +62,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 }
 
 // Wait for phase `parity` of the barrier; false after kMbarSpins polls or
-// kWaitLimitNs, whichever comes first.
+// kWaitLimitNs, whichever comes first (the global timer, a slow read, only
+// once the first poll has failed).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
 {
-    const unsigned long long t0 = global_ns();
+    unsigned long long t0 = 0;
     for (long long spins = 0; spins < kMbarSpins; ++spins) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((spins & 63) == 63 && global_ns() - t0 > kWaitLimitNs) break;
+        if (spins == 0) t0 = global_ns();
+        else if ((spins & 63) == 0 && global_ns() - t0 > kWaitLimitNs) break;
     }
     return false;
 }
@@ -90,8 +92,9 @@ cudaError_t launch_mbar_timeout_selftest(int* status, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Slice s of the dictionary in its shared-memory layout: [P + 1][ldS], entry
-// (p, kk) = d_{s KS + kk, p}, zero for p = P, kk >= KS or atoms >= K.
+// Slice s of the dictionary in its shared-memory layout: [P + 1][ldS] with
+// ldS = KS + 1, column 0 zero and entry (p, 1 + kk) = d_{s KS + kk, p}; zero
+// for p = P and atoms >= K.
 __global__ void slice_dictionary_kernel(Geom g, const float* D, float* Dsl, int KS, int ldS, long long stride,
                                         int S)
 {
@@ -100,10 +103,10 @@ __global__ void slice_dictionary_kernel(Geom g, const float* D, float* Dsl, int 
          idx += (long long)gridDim.x * blockDim.x) {
         const int s = (int)(idx / stride);
         const long long e = idx - (long long)s * stride;
-        const int p = (int)(e / ldS), kk = (int)(e - (long long)p * ldS);
+        const int p = (int)(e / ldS), kk = (int)(e - (long long)p * ldS) - kDictColumnOffset;
         const int k = s * KS + kk;
         float v = 0.0f;
-        if (p < g.P && kk < KS && k < g.K) v = D[(long long)k * g.P + p];
+        if (p < g.P && kk >= 0 && kk < KS && k < g.K) v = D[(long long)k * g.P + p];
         Dsl[idx] = v;
     }
 }
@@ -117,7 +120,7 @@ __device__ __forceinline__ void tiled_body(const SweepArgs& a)
     __shared__ int abort_s;
     const int K = a.g.K, KB = a.g.KB;
     const int Kpad = KB * kAtomBlock;
-    const int KS = a.slice_atoms, ldS = KS | 1, S = a.slices;
+    const int KS = a.slice_atoms, ldS = KS + kDictColumnOffset, S = a.slices;
     const long long stride = a.slice_stride;
     const uint32_t slice_bytes = (uint32_t)(stride * sizeof(float));
     const long long N = a.g.N, Npad = a.g.Npad;
@@ -149,8 +152,9 @@ __device__ __forceinline__ void tiled_body(const SweepArgs& a)
     const int half = LANES == 1 ? 0 : (lane & 1);
     CodeTally tl;
     // Use q of the slice buffers reads slice q % S from buffer q & 1 (each
-    // item makes 2 S consecutive uses).  With S <= 2 both buffers keep their
-    // first slices and are never refilled.
+    // item makes 2 S consecutive uses, or S when the residual is read from
+    // the previous phase instead of rebuilt).  With S <= 2 both buffers keep
+    // their first slices and are never refilled.
     long long q = 0;
     bool ok = true;
 
@@ -162,20 +166,32 @@ __device__ __forceinline__ void tiled_body(const SweepArgs& a)
         if (item >= (unsigned int)nitems) break;
         const unsigned int unit = item * kTiledWarps + warp;
         const bool warp_on = unit < units;
-        const long long i = (long long)unit * PatchLanes<LANES>::kPatchesPerWarp + lane / LANES;
-        const bool valid = warp_on && i < N;
-        const int nobs = valid ? (int)a.nobs[i] : 0;
-        const int nl = LANES == 1 ? nobs : (nobs + 1 - half) / 2;   // this lane's pixels
-        const int wmax = __reduce_max_sync(0xffffffffu, nl);
-        const long long org = valid ? patch_origin(a.g, i) : 0;
+        const long long slot = (long long)unit * PatchLanes<LANES>::kPatchesPerWarp + lane / LANES;
+        const long long i = warp_on ? slot_patch(a, slot) : N;
+        LanePatch lp;
+        lp.i = i;
+        lp.valid = warp_on && i < N;
+        lp.nobs = lp.valid ? (int)a.nobs[slot] : 0;
+        lp.unit = unit;
+        lp.lane = lane;
+        const int nl = LANES == 1 ? lp.nobs : (lp.nobs + 1 - half) / 2;   // this lane's pixels
+        lp.wmax = __reduce_max_sync(0xffffffffu, nl);
+        const long long org = lp.valid ? patch_origin(a.g, i) : 0;
+        const long long irec = warp_on ? i : 0;    // i < Npad: padding patches have zero records
 
-        PixelOffsets<MAXOBS> offK;
-        float r[MAXOBS];
-        gather_patch<MAXOBS, LANES>(a, valid ? i : 0, nl, org, ldS, offK, r, half);
+        PixelAddr<MAXOBS> ad;
+        ad.base = smem_addr(buf0) + 4u * kDictColumnOffset;
+        ad.pitch = 4u * ldS;
+        Resid<MAXOBS> r;
+        const bool from_resid = a.R_in != nullptr;
+        gather_patch<MAXOBS, LANES>(a, lp.valid ? slot : 0, nl, org, ad, r, half, from_resid);
 
         float s2 = 0.0f;
         W8 nb;
-        for (int pass = 0; pass < 2 && ok; ++pass) {
+        AtomCarry carry;
+        carry.dw = 0.0f;
+        carry.rnd = code_random(i, 0, t_it, a.keys);
+        for (int pass = from_resid ? 1 : 0; pass < 2 && ok; ++pass) {
             for (int sl = 0; sl < S; ++sl, ++q) {
                 const int b = (int)(q & 1);
                 float* Dbuf = b ? buf1 : buf0;
@@ -188,24 +204,26 @@ __device__ __forceinline__ void tiled_body(const SweepArgs& a)
                 if (abort_s) { ok = false; break; }
                 const int kb0 = sl * (KS / kAtomBlock);
                 const int kb1 = min(KB, kb0 + KS / kAtomBlock);
+                const uint32_t col0 = smem_addr(Dbuf) + 4u * kDictColumnOffset;
                 if (warp_on) {
                     if (pass == 0) {
-                        for (int kb = kb0; kb < kb1; ++kb)
-                            rebuild_block<MAXOBS>(Dbuf + (kb - kb0) * kAtomBlock, offK, r, wmax,
-                                                  load_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock));
-                    } else {
-                        if (sl == 0) nb = load_w8(a.W + (long long)i * kAtomBlock);
                         for (int kb = kb0; kb < kb1; ++kb) {
-                            float w0 = nb.v[0], w1 = nb.v[1], w2 = nb.v[2], w3 = nb.v[3];
-                            float w4 = nb.v[4], w5 = nb.v[5], w6 = nb.v[6], w7 = nb.v[7];
-                            if (kb + 1 < KB) nb = load_w8(a.W + ((long long)(kb + 1) * Npad + i) * kAtomBlock);
+                            ad.rebase(col0 + 32u * (kb - kb0), lp.wmax);
+                            rebuild_block<MAXOBS>(ad, r, lp.wmax,
+                                                  load_w8(a.W + ((long long)kb * Npad + irec) * kAtomBlock));
+                        }
+                    } else {
+                        if (sl == 0) nb = load_w8(a.W + irec * kAtomBlock);
+                        for (int kb = kb0; kb < kb1; ++kb) {
+                            W8 wb = nb;
+                            if (kb + 1 < KB) nb = load_w8(a.W + ((long long)(kb + 1) * Npad + irec) * kAtomBlock);
                             const int kbase = kb * kAtomBlock;
-                            code_block<MAXOBS, LANES>(Dbuf + (kb - kb0) * kAtomBlock, lpi + kbase, offK, r, wmax,
-                                                      nobs, i, valid, kbase, min(kAtomBlock, K - kbase), c, a.keys,
-                                                      t_it, a.Zb, NW, unit, lane, w0, w1, w2, w3, w4, w5, w6, w7,
-                                                      s2, tl);
-                            if (half == 0)
-                                store_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock, w0, w1, w2, w3, w4, w5, w6, w7);
+                            ad.rebase(col0 + 32u * (kb - kb0), lp.wmax);
+                            const bool changed = code_block<MAXOBS, LANES, false>(
+                                ad, r, lpi + kbase, lp, kbase, K, c, a.keys, t_it, a.Zb, NW, wb, carry, s2, tl);
+                            if (half == 0 && changed && lp.valid)
+                                store_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock, wb.v[0], wb.v[1], wb.v[2],
+                                         wb.v[3], wb.v[4], wb.v[5], wb.v[6], wb.v[7]);
                         }
                     }
                 }
@@ -217,7 +235,7 @@ __device__ __forceinline__ void tiled_body(const SweepArgs& a)
             }
         }
         if (!ok) break;
-        if (warp_on) finish_patch<MAXOBS, LANES>(a, r, wmax, nl, i, unit, lane, s2);
+        if (warp_on) finish_patch<MAXOBS, LANES>(a, r, lp.wmax, nl, slot, unit, lane, s2);
     }
     // The copies still in flight land before the CTA exits: uses q and q + 1
     // when buffers are refilled, else the initial copies not yet waited for.
@@ -289,7 +307,7 @@ cudaError_t preload_tiled_variants()
 
 long long slice_stride_floats(const Geom& g, int KS)
 {
-    const long long n = (long long)(g.P + 1) * (KS | 1);
+    const long long n = (long long)(g.P + 1) * (KS + kDictColumnOffset);
     return (n + 3) & ~3LL;   // whole 16-byte units: bulk copies move multiples of 16 bytes
 }
 
@@ -327,7 +345,8 @@ cudaError_t launch_slice_dictionary(const Geom& g, const float* D, float* Dsl, i
     const int threads = 256;
     long long blocks = (total + threads - 1) / threads;
     if (blocks > 1024) blocks = 1024;
-    slice_dictionary_kernel<<<(unsigned int)blocks, threads, 0, s>>>(g, D, Dsl, KS, KS | 1, stride, S);
+    slice_dictionary_kernel<<<(unsigned int)blocks, threads, 0, s>>>(g, D, Dsl, KS, KS + kDictColumnOffset, stride,
+                                                                    S);
     return cudaGetLastError();
 }
 

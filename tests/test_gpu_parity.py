@@ -271,6 +271,19 @@ def test_full_size_chain_dictionary(c2_state):
     assert dict_errors(Dg, od.D).max() <= D_TOL
 
 
+def test_full_size_dense_statistics_dictionary(c2_state):
+    """The dense-statistics form (tensor-core Grams) at full size."""
+    prm, x, mask, st = c2_state
+    ctx = gpu_context(prm, mask, _dense())
+    push_state(ctx, st, x)
+    ctx.sensai_draw_dictionary()
+    Dg = ctx.sensai_get_dictionary()
+    ctx.close()
+    od = st.copy()
+    O.d_sweep(od, x, mask)
+    assert dict_errors(Dg, od.D).max() <= D_TOL
+
+
 def test_full_size_reconstruct_and_counts(c2_state):
     prm, x, mask, st = c2_state
     ctx = gpu_context(prm, mask)
@@ -304,6 +317,48 @@ def test_device_buffers_and_streams():
             outs.append(ctx.sensai_reconstruct())
         ctx.close()
     np.testing.assert_array_equal(outs[0], outs[1])
+
+
+# --- the dictionary draw's forms: the residual form (space-organised kernel,
+# the default), dense statistics on the tensor cores (K <= 128), the residual
+# form per chain (batches, P > 512, empty masks) ---
+
+def _dense():
+    from paper_2311_15061_gb300 import sensai
+    return sensai.SENSAI_FLAG_DENSE_STATISTICS
+
+
+def test_dense_statistics_dictionary_128x128_k64():
+    _phase_parity(**C1, flags=_dense())
+
+
+def _dict_error(prm, x, mask, st, flags):
+    ctx = gpu_context(prm, mask, flags)
+    push_state(ctx, st, x)
+    ctx.sensai_draw_dictionary()
+    Dg = ctx.sensai_get_dictionary()
+    ctx.close()
+    od = st.copy()
+    O.d_sweep(od, x, mask)
+    return dict_errors(Dg, od.D)
+
+
+def test_tf32_statistics_error():
+    """SENSAI_FLAG_TF32_STATISTICS (the reduced-precision form): the Grams from
+    the TF32 heads alone.  Against the FP64 oracle the drawn atoms stay within
+    5e-3 (per atom, relative), and the FP32-level default is at least 20x
+    closer on the same state."""
+    from paper_2311_15061_gb300 import sensai
+    prm, x, clean, mask = problem(**C1)
+    st = oracle_state(prm, x, mask, 2)
+    post = st.copy()
+    O.zs_sweep_subset(post, x, mask)
+    post = round_state(post)
+    e32 = _dict_error(prm, x, mask, post, _dense()).max()
+    etf = _dict_error(prm, x, mask, post, sensai.SENSAI_FLAG_TF32_STATISTICS).max()
+    assert e32 <= D_TOL, e32
+    assert etf <= 5e-3, etf
+    assert etf >= 20 * e32, (etf, e32)
 
 
 # --- the per-chain dictionary kernel (batches, P > 512, empty masks) ---
@@ -388,7 +443,7 @@ def test_streamed_learning_is_bit_identical_to_resident():
 def test_flags_validation():
     from paper_2311_15061_gb300 import sensai
     prm, x, clean, mask = problem((40, 40), (8, 8), (1, 1), 16, 0.25)
-    for bad in (0x8, sensai.SENSAI_SLICE_ATOMS(8)):   # unknown bit; slice without streaming
+    for bad in (0x40, sensai.SENSAI_SLICE_ATOMS(8)):   # unknown bit; slice without streaming
         with pytest.raises(sensai.SensaiError) as err:
             gpu_context(prm, mask, bad)
         assert err.value.status == sensai.SENSAI_EINVAL

@@ -125,3 +125,67 @@ def test_reconstruct_is_deterministic():
         ctx.close()
     for o in outs[1:]:
         np.testing.assert_array_equal(outs[0], o)
+
+
+# --- posterior-mean reconstruction over the last T samples (sensai_mean_*) ---
+
+@pytest.mark.parametrize("M,B,S,K,T", [((128, 128), (8, 8), (1, 1), 64, 3),
+                                       ((12, 14, 16), (4, 4, 4), (1, 2, 1), 24, 4)])
+def test_posterior_mean_matches_oracle(M, B, S, K, T):
+    """The last T samples of an oracle chain, pushed into the context one by
+    one and added: the mean against the oracle's, 1e-5 of the largest value."""
+    from parity_helpers import problem, round_state
+    prm, x, clean, mask = problem(M, B, S, K, 0.25, seed=2)
+    kept = []
+    O.learn(O.State(prm), x, mask, T + 1,
+            callback=lambda st, stats: kept.append(round_state(st.copy())) if st.t >= 1 else None)
+    assert len(kept) == T
+    ctx = gpu_context(prm, mask)
+    ctx.sensai_mean_reset()
+    for st in kept:
+        ctx.sensai_set_state(D=st.D.astype(np.float32), Z=st.Z, S=st.S.astype(np.float32), gamma_s=st.gamma_s,
+                             gamma_eps=st.gamma_eps, iter=st.t)
+        ctx.sensai_mean_add()
+    got = ctx.sensai_mean_read()
+    ctx.close()
+    want = O.reconstruct_mean(kept)
+    assert np.abs(got - want).max() <= 1e-5 * max(np.abs(want).max(), 1e-6)
+
+
+def test_posterior_mean_of_one_state_is_the_reconstruction_full_size():
+    """512x512, K = 128: the mean of three adds of one state equals
+    sensai_reconstruct bit for bit ((3 y) / 3 is exact in FP64 for an FP32 y);
+    reading before any add after a reset is refused."""
+    from paper_2311_15061_gb300 import sensai
+    M, B, S, K = (512, 512), (10, 10), (1, 1), 128
+    prm = O.params(M, B, S, K, seed=3)
+    st = _state(prm, 0.3, 9)
+    ctx = gpu_context(prm, np.ones(M, np.uint8))
+    ctx.sensai_set_state(D=st.D.astype(np.float32), Z=st.Z, S=st.S.astype(np.float32), gamma_s=1.0)
+    ctx.sensai_mean_reset()
+    with pytest.raises(sensai.SensaiError) as err:
+        ctx.sensai_mean_read()
+    assert err.value.status == sensai.SENSAI_ESTATE
+    for _ in range(3):
+        ctx.sensai_mean_add()
+    np.testing.assert_array_equal(ctx.sensai_mean_read(), ctx.sensai_reconstruct())
+    ctx.close()
+
+
+def test_posterior_mean_during_learning():
+    """The intended use: learn, then add after each of the last T iterations;
+    the mean is the average of the T reconstructions read one by one."""
+    from parity_helpers import problem
+    prm, x, clean, mask = problem((96, 80), (8, 8), (1, 1), 32, 0.25, seed=4)
+    ctx = gpu_context(prm, mask)
+    ctx.sensai_learn(x, 3)
+    ctx.sensai_mean_reset()
+    recs = []
+    for _ in range(4):
+        ctx.sensai_learn(None, 1)
+        ctx.sensai_mean_add()
+        recs.append(ctx.sensai_reconstruct().astype(np.float64))
+    got = ctx.sensai_mean_read()
+    ctx.close()
+    want = np.mean(recs, axis=0)
+    assert np.abs(got - want).max() <= 1e-6 * max(np.abs(want).max(), 1e-6)
