@@ -45,6 +45,8 @@ UNIT = "patch·atom updates/s"
 #   2 |Omega_i| FMAs (masked norm + correlation), 75 fixed (Philox4x32-10:
 #   60, log-odds / sigmoid / threshold: 15), 14 more when z = 1 (Box-Muller +
 #   weight), |Omega_i| FMAs when the weight changes (rank-1 residual update).
+# Plus patch extraction: |Omega_i| FMAs per non-zero stored weight where the
+# sweep rebuilds the residual x_i - D w_i itself (stats.rebuild_observed).
 OPS_FIXED, OPS_GAUSS = 75, 14
 LANES_PER_SM = 128   # FP32 / INT32 lanes per SM (4 sub-partitions x 32)
 
@@ -248,7 +250,7 @@ def run_gpu(args):
     sweep_ms, sweep_n = prof["codes"]
     n_obs = ctx.sensai_get_stats().n_observed
     ops = (sweep_n * K * (2.0 * n_obs + OPS_FIXED * N) + float(stats.changed_observed)
-           + OPS_GAUSS * float(stats.active_draws))
+           + OPS_GAUSS * float(stats.active_draws) + float(stats.rebuild_observed))
     peaks, peak_src = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(local).multi_processor_count

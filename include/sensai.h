@@ -21,7 +21,9 @@
  *
  * Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by `seed`,
  * counter (index0, index1, t, tag | attempt << 8); uniforms (x + 1) 2^-32;
- * Box-Muller normals; Marsaglia-Tsang Gamma.  Results depend only on the
+ * Box-Muller normals; Marsaglia-Tsang Gamma.  The code draws of atoms 2m and
+ * 2m + 1 of patch i share the block at (i, m, t, 2): word k % 2 decides
+ * z_ik, words 2-3 give one Box-Muller pair (cosine: even atom, sine: odd).  Results depend only on the
  * parameters, seed, frame, mask and iteration index.
  *
  * Conventions for every entry point:
@@ -163,6 +165,8 @@ typedef struct {
     int64_t active_draws;      /* code draws with z = 1, since the last profile start */
     int32_t slice_atoms;       /* code sweep: 0 = dictionary resident in shared memory, else atoms per streamed slice */
     int32_t slices;            /* code sweep: streamed slices per pass (0 when resident) */
+    int64_t rebuild_observed;  /* residual rebuilds inside code sweeps (patch extraction): sum of
+                                  |Omega_i| x non-zero stored weights, since the last profile start */
 } sensai_stats;
 
 /* Create a context on the current CUDA device.  `mask` is prod(M) host bytes

@@ -99,6 +99,7 @@ def lib():
         "orc_frame_size": (i64, [pp]),
         "orc_philox": (None, [P(u32), P(u32), P(u32)]),
         "orc_normal": (dbl, [ctypes.c_uint64, P(u32)]),
+        "orc_normal_pair": (dbl, [ctypes.c_uint64, P(u32), ctypes.c_int]),
         "orc_gamma": (dbl, [dbl, ctypes.c_uint64, u32, u32, u32, u32]),
         "orc_beta": (dbl, [dbl, dbl, ctypes.c_uint64, u32, u32]),
         "orc_overlap_counts": (None, [pp, P(i32)]),
@@ -136,6 +137,13 @@ def philox(ctr, key):
 def normal(seed, ctr):
     c = np.ascontiguousarray(ctr, dtype=np.uint32)
     return lib().orc_normal(seed, _p(c, ctypes.c_uint32))
+
+
+def normal_pair(seed, ctr, second):
+    """Normal of the Box-Muller pair from words 2-3 of the block at ctr (the
+    code draws' pair: cosine for the even atom, sine for the odd one)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    return lib().orc_normal_pair(seed, _p(c, ctypes.c_uint32), int(second))
 
 
 def gamma(shape, seed, c0, c1, t, tag):

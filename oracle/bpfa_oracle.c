@@ -67,6 +67,24 @@ static double box_muller(uint32_t x0, uint32_t x1)
     return sqrt(-2.0 * log(u1)) * cos(two_pi * u2);
 }
 
+/* The two normals of one Box-Muller transform, sqrt(-2 ln u1) cos(2 pi u2)
+ * and sqrt(-2 ln u1) sin(2 pi u2): independent standard normals.  second
+ * selects the sine. */
+static double box_muller_pair(uint32_t x0, uint32_t x1, int second)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    double u1 = unit_uniform(x0), u2 = unit_uniform(x1);
+    double rad = sqrt(-2.0 * log(u1));
+    return second ? rad * sin(two_pi * u2) : rad * cos(two_pi * u2);
+}
+
+double orc_normal_pair(uint64_t seed, const uint32_t ctr[4], int second)
+{
+    uint32_t blk[4];
+    block_at(seed, ctr[0], ctr[1], ctr[2], ctr[3], blk);
+    return box_muller_pair(blk[2], blk[3], second);
+}
+
 double orc_normal(uint64_t seed, const uint32_t ctr[4])
 {
     uint32_t blk[4];
@@ -334,18 +352,22 @@ const int64_t nvisit = patches ? npatches : N;
                 if (logodds) logodds[i * K + k] = L;
                 double sig = 1.0 / (1.0 + exp(-L));
                 uint64_t thr = (uint64_t)floor(sig * 4294967296.0);
+                /* atoms 2m and 2m + 1 share the block at counter (i, m, t):
+                 * word k % 2 decides z, words 2-3 give the Box-Muller pair
+                 * (the cosine for the even atom, the sine for the odd one) */
                 uint32_t blk[4];
-                block_at(prm->seed, (uint32_t)i, (uint32_t)k, (uint32_t)t, ORC_TAG_ZS, blk);
-                int z = (uint64_t)blk[0] < thr;
+                block_at(prm->seed, (uint32_t)i, (uint32_t)(k >> 1), (uint32_t)t, ORC_TAG_ZS, blk);
+                int z = (uint64_t)blk[k & 1] < thr;
+                const double nrm = box_muller_pair(blk[2], blk[3], k & 1);
                 double w_new = 0.0, s_new = 0.0;
                 if (z) {
-                    w_new = gamma_eps * g / lam + box_muller(blk[1], blk[2]) / sqrt(lam);
+                    w_new = gamma_eps * g / lam + nrm / sqrt(lam);
                     s_new = w_new;
                     zc += 1.0;
                     s2 += w_new * w_new;
                 } else if (prm->flags & ORC_FLAG_GAMMA_S_FULL) {
                     /* inactive: s from its prior; the weight z s stays 0 */
-                    s_new = box_muller(blk[1], blk[2]) / sqrt(gamma_s);
+                    s_new = nrm / sqrt(gamma_s);
                     s2 += s_new * s_new;
                 }
                 double dw = w_new - w_old;

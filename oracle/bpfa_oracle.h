@@ -74,7 +74,8 @@ enum { ORC_FLAG_GAMMA_S_FULL = 4 };
 
 enum {
     ORC_TAG_INIT = 1,  /* dictionary initialisation, counter (p, k, 0) */
-    ORC_TAG_ZS = 2,    /* sparse-code draw, counter (i, k, t) */
+    ORC_TAG_ZS = 2,    /* sparse-code draws of atoms 2m, 2m + 1, counter (i, m, t): word k % 2 -> z_ik,
+                          words 2-3 -> one Box-Muller pair (cosine: even atom, sine: odd atom) */
     ORC_TAG_D = 3,     /* dictionary draw, counter (p, k, t) */
     ORC_TAG_PI_A = 4,  /* first Gamma of the Beta draw of pi_k, counter (k, 0, t) */
     ORC_TAG_PI_B = 5,  /* second Gamma of the Beta draw of pi_k */
@@ -93,6 +94,10 @@ int64_t orc_frame_size(const orc_params* prm);
 void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* Standard normal from the block at counter ctr (words 0 and 1). */
 double orc_normal(uint64_t seed, const uint32_t ctr[4]);
+/* One of the two normals of the Box-Muller transform of words 2 and 3 of the
+ * block at counter ctr: the cosine one (second = 0) or the sine one; the pair
+ * the code draws of atoms 2m and 2m + 1 use. */
+double orc_normal_pair(uint64_t seed, const uint32_t ctr[4], int second);
 /* Gamma(shape, 1) and Beta(alpha, beta) with the counter conventions above;
  * c0 is the index word, tag the stream tag (attempts go in tag's high bits). */
 double orc_gamma(double shape, uint64_t seed, uint32_t c0, uint32_t c1, uint32_t t, uint32_t tag);

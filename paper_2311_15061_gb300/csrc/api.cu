@@ -104,6 +104,8 @@ struct sensai_ctx {
     int4* items = nullptr;      // work items: segments of the per-pixel patch lists
     long long n_items = 0;
     int gram_grid = 0;
+    CUtensorMap wmap;           // W for gram_kernel's record copies (set on first use)
+    bool wmap_set = false;
     float* Cpart = nullptr;     // [items][128][128]
     float* Ypart = nullptr;     // [items][4][128]
     double* C64 = nullptr;      // [P][128][128]
@@ -380,10 +382,16 @@ sensai_status run_sweep(sensai_ctx* ctx, cudaStream_t s)
     SweepArgs a = sweep_args(ctx);
     if (ctx->R) {
         // the sweep starts from the residual rebuilt from the state (the
-        // phases before it leave R updated incrementally): its bits depend on
-        // the state alone, as for a sweep that rebuilds it itself
-        if (!ctx->resid_fresh && (st = rebuild_residual(ctx, s)) != SENSAI_OK) return st;
-        a.R_in = ctx->R;
+        // phases before it leave R updated incrementally), so its bits depend
+        // on the state alone: read from R when R holds exactly that, else
+        // rebuilt inside the sweep (dictionary resident in shared memory) or
+        // by residual_kernel first (streamed dictionary)
+        if (ctx->resid_fresh) {
+            a.R_in = ctx->R;
+        } else if (ctx->sweep_plan.slice_atoms != 0) {
+            if ((st = rebuild_residual(ctx, s)) != SENSAI_OK) return st;
+            a.R_in = ctx->R;
+        }
         if (ctx->gram) a.R = nullptr;   // no phase reads the residual the sweep ends with
     }
     const SweepPlan plan = ctx->sweep_plan;
@@ -414,7 +422,12 @@ sensai_status run_gram(sensai_ctx* ctx, cudaStream_t s)
         ctx->launches += 1;
         ctx->xlist_valid = true;
     }
+    if (!ctx->wmap_set) {
+        SENSAI_CUDA(ctx, gram_weight_map(ctx->g, ctx->W, &ctx->wmap));
+        ctx->wmap_set = true;
+    }
     GramArgs a{};
+    a.wmap = ctx->wmap;
     a.g = ctx->g;
     a.W = ctx->W;
     a.Ilist = ctx->Ilist;
@@ -1125,6 +1138,7 @@ sensai_status sensai_get_stats(sensai_ctx* ctx, sensai_stats* stats)
     stats->changed_updates = (int64_t)sc.chg_n;
     stats->changed_observed = (int64_t)sc.chg_obs;
     stats->active_draws = (int64_t)sc.act_n;
+    stats->rebuild_observed = (int64_t)sc.rb_obs;
     stats->slice_atoms = ctx->sweep_plan.slice_atoms;
     stats->slices = ctx->sweep_plan.slices;
     return SENSAI_OK;
@@ -1234,7 +1248,7 @@ sensai_status sensai_profile(sensai_ctx* ctx, int32_t enable)
     if (enable) {
         SENSAI_CUDA(ctx, cudaDeviceSynchronize());
         clear_timers(ctx);
-        const unsigned long long zero[3] = {0, 0, 0};
+        const unsigned long long zero[4] = {0, 0, 0, 0};   // chg_n, chg_obs, act_n, rb_obs
         SENSAI_CUDA(ctx, cudaMemcpy(&ctx->sc->chg_n, zero, sizeof(zero), cudaMemcpyHostToDevice));
     }
     ctx->profiling = enable != 0;

@@ -35,15 +35,17 @@
 // nearest: a simulation of that arithmetic on the 128x128 K = 64 workload
 // gives <= 2e-6 relative on the drawn atoms.
 // Warp roles (320 threads, one CTA per SM):
-//  * warps 9-10, loaders: per chunk, the 32 patch indices (loaded a chunk
-//    ahead), then per patch one cp.async of 16 bytes per lane -- the patch's
-//    whole 512-byte weight record -- and the 32 frame values, into one of
-//    four raw slots; completion is signalled on the slot's mbarrier;
-//  * warps 0-3, converters: warp w takes chunks w, w + 4, ...: lane l holds
+//  * warp 9, loader: per chunk, lane j copies patch j's whole weight record
+//    (KB blocks of 32 bytes, 8 MB apart in W) with one tensor copy
+//    (cp.async.bulk.tensor, a 3-D box over W), into one of five raw slots;
+//    the patch indices and frame values are loaded a chunk ahead and the
+//    frame values stored beside the slot; completion is the slot's mbarrier
+//    (the loader's arrival and the copies' bytes);
+//  * warps 0-3, converters: warp w takes chunks w, w + 4, ...: lane l reads
 //    atoms 4l .. 4l + 3 of every patch of the chunk (16-byte shared loads),
-//    splits them, writes H and 2L into the chunk's operand stage as 16-byte
-//    stores (an 8-row group pitch of 272 bytes keeps them free of bank
-//    conflicts) and accumulates Y_p for its atoms in FP32;
+//    splits them, writes H and 2L into one of four operand stages as
+//    16-byte stores (an 8-row group pitch of 272 bytes keeps them free of
+//    bank conflicts) and accumulates Y_p for its atoms in FP32;
 //  * warp 8, lane 0: issues the MMAs (a wait per chunk, 8 MMAs, a commit)
 //    into two accumulators in turn, one per group of 4 chunks;
 //  * warps 4-7, epilogue: warp w reads TMEM lanes 32 (w % 4) .., i.e. the
@@ -54,8 +56,8 @@
 // every role stops (each warp's decision is its lane 0's, broadcast), the
 // MMAs in flight are waited for and TMEM is freed.
 //
-// gram_reduce_kernel -- the FP64 sums of every pixel's item partials, in item
-// order; gram_draw_kernel -- one CTA per pixel p: symmetrises the sum into
+// gram_reduce_kernel -- the compensated sums of every pixel's item partials,
+// in item order; gram_draw_kernel -- one CTA per pixel p: symmetrises the sum into
 // C_p and makes the K atom-ordered draws in FP64.
 #include <algorithm>
 #include <vector>
@@ -70,13 +72,13 @@ constexpr int kGChunk = 32;                     // patches per chunk (4 MMA step
 constexpr int kGConverters = 4;                 // warps 0-3
 constexpr int kGEpilogue0 = 4;                  // warps 4-7
 constexpr int kGMmaWarp = 8;
-constexpr int kGLoader0 = 9;                    // warps 9-10
-constexpr int kGLoaders = 2;
-constexpr int kGThreads = 32 * (kGLoader0 + kGLoaders);
-constexpr int kGSlots = 4;                      // raw slots = operand stages = converter warps
+constexpr int kGLoaderWarp = 9;
+constexpr int kGThreads = 32 * (kGLoaderWarp + 1);
+constexpr int kGRawSlots = 5;                   // raw record ring (TMA destination)
+constexpr int kGStages = 4;                     // operand stages
 constexpr int kGGroup = 4;                      // chunks per accumulator drain
 constexpr int kGSegment = 2048;                 // most patches of an item
-constexpr int kGRawFloats = kGChunk * kGAtoms + kGChunk;   // records [32][128], then the 32 frame values
+constexpr int kGRawFloats = kGChunk * kGAtoms;  // one chunk's records [32 patches][128 atoms]
 constexpr int kGSboBytes = 272;                 // 8-row group pitch (256 B of data + 16 B)
 constexpr int kGOpFloats = (kGAtoms / 8) * kGSboBytes / 4;   // one 128 x 8 operand: 1088 floats
 constexpr int kGStageFloats = 2 * (kGChunk / kGStep) * kGOpFloats;   // H[4], then 2L[4]
@@ -84,7 +86,12 @@ constexpr int kGTmemCols = 4 * kGAtoms;         // two accumulators, the running
 constexpr int kGSumCol = 2 * kGAtoms;           // the running sums' columns
 constexpr long long kGSpins = 1LL << 22;
 
-static_assert(kGSlots == kGConverters, "converter warp w owns raw slot w and stage w");
+// A converter waits on the stage and the raw slot of its next chunk only
+// after those of its previous chunk (kGConverters chunks earlier); with at
+// least as many stages and slots as converters, no barrier it waits on can
+// be two phases behind (a parity wait would then pass early).
+static_assert(kGStages >= kGConverters && kGRawSlots >= kGConverters, "phase aliasing");
+
 
 __device__ __forceinline__ uint32_t gm_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -117,43 +124,52 @@ __device__ __forceinline__ void gm_arrive(uint64_t* bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(gm_smem(bar)) : "memory");
 }
 
-// Bounded wait for a phase: each try suspends the thread in hardware for up
-// to ~1 us (or until the phase completes), so waiting threads take few issue
-// slots; gives up after kWaitLimitNs.  The global timer (a slow read: some
-// hundreds of cycles) is read only once a try has failed.
+// Bounded wait for a phase.  Between tries the thread sleeps, the sleep
+// doubling from 32 ns up to kGSleepCapNs: a waiting warp then takes almost no
+// issue slots from the warps doing the work on its scheduler (a try that
+// fails returns at once on this GPU, so an undelayed poll loop issues about
+// one instruction per cycle).  Gives up after kWaitLimitNs; the global timer
+// is read only every 16 tries.
+constexpr unsigned int kGSleepCapNs = 256;
+
 __device__ __forceinline__ bool gm_wait(uint64_t* bar, uint32_t parity)
 {
     unsigned long long t0 = 0;
+    unsigned int ns = 32;
     for (long long spins = 0; spins < kGSpins; ++spins) {
         uint32_t ok;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(ok)
-            : "r"(gm_smem(bar)), "r"(parity), "r"(1000u)
+            : "r"(gm_smem(bar)), "r"(parity)
             : "memory");
         if (ok) return true;
         if (spins == 0) t0 = global_ns();
         else if ((spins & 15) == 0 && global_ns() - t0 > kWaitLimitNs) break;
+        __nanosleep(ns);
+        ns = ns < kGSleepCapNs ? 2 * ns : kGSleepCapNs;
     }
     return false;
 }
 
-// 16-byte (and 4-byte) asynchronous global -> shared copies; their completion
-// is signalled on an mbarrier by gm_cp_arrive.
-__device__ __forceinline__ void gm_cp16(void* dst, const void* src)
+// Arrival that also expects tx more bytes of asynchronous copies.
+__device__ __forceinline__ void gm_arrive_tx(uint64_t* bar, uint32_t tx)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(gm_smem(dst)), "l"(src) : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(gm_smem(bar)), "r"(tx) : "memory");
 }
 
-__device__ __forceinline__ void gm_cp4(void* dst, const void* src)
+// One patch's weight record by the tensor-memory-access unit: the box
+// (8 floats, 1 patch, KB atom blocks) of the map over W [KB][Npad][8] at
+// patch i, into 512 contiguous bytes (atoms in order); completion counted
+// in bytes on bar.
+__device__ __forceinline__ void gm_tma_record(float* dst, const CUtensorMap* map, int i, uint64_t* bar)
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(gm_smem(dst)), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void gm_cp_arrive(uint64_t* bar)
-{
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(gm_smem(bar)) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(gm_smem(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(i), "r"(0), "r"(gm_smem(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void gm_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
@@ -239,13 +255,13 @@ struct ChunkWalk {
 
 // Item it: pixel items[it].x, patches Ilist[items[it].y .. + items[it].z).
 __global__ void __launch_bounds__(kGThreads, 1)
-    gram_kernel(GramArgs a)
+    gram_kernel(const __grid_constant__ GramArgs a)
 {
     extern __shared__ __align__(1024) float gsm[];
-    __shared__ __align__(8) uint64_t full_bar[kGSlots];    // stage s written (converter warp s)
-    __shared__ __align__(8) uint64_t empty_bar[kGSlots];   // stage s read (the MMA commit)
-    __shared__ __align__(8) uint64_t raw_full[kGSlots];    // raw slot r landed (every loader lane's copies)
-    __shared__ __align__(8) uint64_t raw_empty[kGSlots];   // raw slot r read (converter warp r)
+    __shared__ __align__(8) uint64_t full_bar[kGStages];     // stage written (a converter warp)
+    __shared__ __align__(8) uint64_t empty_bar[kGStages];    // stage read (the MMA commit)
+    __shared__ __align__(8) uint64_t raw_full[kGRawSlots];   // raw slot landed (loader arrival + TMA bytes)
+    __shared__ __align__(8) uint64_t raw_empty[kGRawSlots];  // raw slot read (a converter warp)
     __shared__ __align__(8) uint64_t accf_bar[2];          // a group's MMAs complete
     __shared__ __align__(8) uint64_t acce_bar[2];          // a group's accumulator drained
     __shared__ __align__(8) uint64_t done_bar;
@@ -254,16 +270,21 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int K = a.g.K;
     const bool split = !a.tf32;
-    float* stages = gsm;                                   // [kGSlots][kGStageFloats]
-    float* raw = stages + kGSlots * kGStageFloats;         // [kGSlots][kGRawFloats]
+    // 1024-byte aligned whatever the dynamic segment's base (tensor copies
+    // and the MMA operands want aligned shared addresses)
+    float* stages = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~(uintptr_t)1023);
+    float* raw = stages + kGStages * kGStageFloats;        // [kGRawSlots][kGRawFloats]
+    float* rawx = raw + kGRawSlots * kGRawFloats;          // [kGRawSlots][kGChunk] frame values
 
     if (tid == 0) {
         abort_s = 0;
-        for (int s = 0; s < kGSlots; ++s) {
+        for (int s = 0; s < kGStages; ++s) {
             gm_bar_init(&full_bar[s], 1);
             gm_bar_init(&empty_bar[s], 1);
-            gm_bar_init(&raw_full[s], 32);
-            gm_bar_init(&raw_empty[s], 1);
+        }
+        for (int r = 0; r < kGRawSlots; ++r) {
+            gm_bar_init(&raw_full[r], 1);
+            gm_bar_init(&raw_empty[r], 1);
         }
         for (int b = 0; b < 2; ++b) {
             gm_bar_init(&accf_bar[b], 1);
@@ -301,10 +322,10 @@ __global__ void __launch_bounds__(kGThreads, 1)
     wk.start(a);
     if (warp < kGConverters) {
         // ----------------------------------------------------- converters --
-        // lane l: atoms 4l .. 4l + 3 of the 32 patches of each own chunk
+        // chunks w, w + 4, ...: lane l takes atoms 4l .. 4l + 3 of the 32
+        // patches from the raw slot, 8 patches at a time, and writes them
+        // split into the chunk's operand stage
         const int w = warp;
-        float* stg = stages + (size_t)w * kGStageFloats;
-        const float* rw = raw + (size_t)w * kGRawFloats;
         bool live[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) live[r] = 4 * lane + r < K;
@@ -312,62 +333,72 @@ __global__ void __launch_bounds__(kGThreads, 1)
         // 128 x 8 operand (8-row group l / 2, row 4 (l % 2) + r in it)
         const int op_base = (lane >> 1) * (kGSboBytes / 4) + (lane & 1) * 16;
         float y[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        long long n = 0;   // this warp's chunks so far
         bool ok = true;
         for (; wk.valid(a) && ok; wk.next(a)) {
             if ((int)(wk.u % kGConverters) == w) {
                 const int cnt = a.items[wk.it].z;
                 const int nvalid = min(kGChunk, cnt - wk.c * kGChunk);
-                const uint32_t par = (uint32_t)(n & 1);
-                ok = warp_wait(&raw_full[w], par) && warp_wait(&empty_bar[w], par ^ 1u);
-                if (!ok) break;
+                const int rs = (int)(wk.u % kGRawSlots);
+                const int st = (int)(wk.u % kGStages);
+                if (!(ok = warp_wait(&raw_full[rs], (uint32_t)((wk.u / kGRawSlots) & 1)))) break;
+                if (!(ok = warp_wait(&empty_bar[st], (uint32_t)(((wk.u / kGStages) & 1) ^ 1)))) break;
+                const float* rw = raw + (size_t)rs * kGRawFloats;
+                const float xl = rawx[rs * kGChunk + lane];
+                float* stg = stages + (size_t)st * kGStageFloats;
 #pragma unroll
                 for (int kb = 0; kb < kGChunk / kGStep; ++kb) {
                     float4 v[kGStep];
 #pragma unroll
                     for (int j = 0; j < kGStep; ++j)
                         v[j] = *reinterpret_cast<const float4*>(rw + (kb * kGStep + j) * kGAtoms + 4 * lane);
-                    float wv[kGStep][4];
 #pragma unroll
                     for (int j = 0; j < kGStep; ++j) {
                         const bool pv = kb * kGStep + j < nvalid;
-                        const float xj = pv ? rw[kGChunk * kGAtoms + kb * kGStep + j] : 0.0f;
-                        const float e[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            wv[j][r] = (pv && live[r]) ? e[r] : 0.0f;
-                            y[r] = fmaf(wv[j][r], xj, y[r]);
-                        }
+                        const float xj = __shfl_sync(0xffffffffu, pv ? xl : 0.0f, kb * kGStep + j);
+                        v[j].x = (pv && live[0]) ? v[j].x : 0.0f;
+                        v[j].y = (pv && live[1]) ? v[j].y : 0.0f;
+                        v[j].z = (pv && live[2]) ? v[j].z : 0.0f;
+                        v[j].w = (pv && live[3]) ? v[j].w : 0.0f;
+                        y[0] = fmaf(v[j].x, xj, y[0]);
+                        y[1] = fmaf(v[j].y, xj, y[1]);
+                        y[2] = fmaf(v[j].z, xj, y[2]);
+                        y[3] = fmaf(v[j].w, xj, y[3]);
                     }
                     float* oh = stg + kb * kGOpFloats + op_base;
                     float* ol = stg + (kGChunk / kGStep + kb) * kGOpFloats + op_base;
 #pragma unroll
-                    for (int r = 0; r < 4; ++r)
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            float4 h, l2;
-                            h.x = gm_head(wv[4 * q + 0][r]);
-                            h.y = gm_head(wv[4 * q + 1][r]);
-                            h.z = gm_head(wv[4 * q + 2][r]);
-                            h.w = gm_head(wv[4 * q + 3][r]);
-                            *reinterpret_cast<float4*>(oh + q * 32 + r * 4) = h;
-                            if (split) {
-                                // 2 (w - h): exact (h is w truncated; doubling is exact)
-                                l2.x = 2.0f * (wv[4 * q + 0][r] - h.x);
-                                l2.y = 2.0f * (wv[4 * q + 1][r] - h.y);
-                                l2.z = 2.0f * (wv[4 * q + 2][r] - h.z);
-                                l2.w = 2.0f * (wv[4 * q + 3][r] - h.w);
-                                *reinterpret_cast<float4*>(ol + q * 32 + r * 4) = l2;
-                            }
+                    for (int q = 0; q < 2; ++q) {
+                        const float4* e = v + 4 * q;   // patches 4q .. 4q + 3 of the block
+                        const float4 hx = make_float4(gm_head(e[0].x), gm_head(e[1].x), gm_head(e[2].x), gm_head(e[3].x));
+                        const float4 hy = make_float4(gm_head(e[0].y), gm_head(e[1].y), gm_head(e[2].y), gm_head(e[3].y));
+                        const float4 hz = make_float4(gm_head(e[0].z), gm_head(e[1].z), gm_head(e[2].z), gm_head(e[3].z));
+                        const float4 hw = make_float4(gm_head(e[0].w), gm_head(e[1].w), gm_head(e[2].w), gm_head(e[3].w));
+                        *reinterpret_cast<float4*>(oh + q * 32 + 0) = hx;
+                        *reinterpret_cast<float4*>(oh + q * 32 + 4) = hy;
+                        *reinterpret_cast<float4*>(oh + q * 32 + 8) = hz;
+                        *reinterpret_cast<float4*>(oh + q * 32 + 12) = hw;
+                        if (split) {
+                            // 2 (w - h): exact (h is w truncated; doubling is exact)
+                            *reinterpret_cast<float4*>(ol + q * 32 + 0) =
+                                make_float4(2.0f * (e[0].x - hx.x), 2.0f * (e[1].x - hx.y), 2.0f * (e[2].x - hx.z),
+                                            2.0f * (e[3].x - hx.w));
+                            *reinterpret_cast<float4*>(ol + q * 32 + 4) =
+                                make_float4(2.0f * (e[0].y - hy.x), 2.0f * (e[1].y - hy.y), 2.0f * (e[2].y - hy.z),
+                                            2.0f * (e[3].y - hy.w));
+                            *reinterpret_cast<float4*>(ol + q * 32 + 8) =
+                                make_float4(2.0f * (e[0].z - hz.x), 2.0f * (e[1].z - hz.y), 2.0f * (e[2].z - hz.z),
+                                            2.0f * (e[3].z - hz.w));
+                            *reinterpret_cast<float4*>(ol + q * 32 + 12) =
+                                make_float4(2.0f * (e[0].w - hw.x), 2.0f * (e[1].w - hw.y), 2.0f * (e[2].w - hw.z),
+                                            2.0f * (e[3].w - hw.w));
                         }
+                    }
                 }
+                __syncwarp();
+                if (lane == 0) gm_arrive(&raw_empty[rs]);   // the slot may be refilled
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
-                if (lane == 0) {
-                    gm_arrive(&raw_empty[w]);
-                    gm_arrive(&full_bar[w]);
-                }
-                ++n;
+                if (lane == 0) gm_arrive(&full_bar[st]);
             }
             if (wk.c == wk.nch - 1) {
                 // the end of an item: this warp's share of Y_p (its chunks)
@@ -376,53 +407,59 @@ __global__ void __launch_bounds__(kGThreads, 1)
                 y[0] = y[1] = y[2] = y[3] = 0.0f;
             }
         }
-    } else if (warp >= kGLoader0 && warp < kGLoader0 + kGLoaders) {
-        // --------------------------------------------------------- loaders --
-        // loader warp v takes chunks v, v + 2, ...; lane l copies 16-byte
-        // piece l of every patch record (atom block l / 2, half l % 2)
-        const int v = warp - kGLoader0;
-        const bool lane_live = (lane >> 1) < a.g.KB;
-        // the next own chunk's patch index and frame value, loaded a chunk ahead
-        auto load_idx = [&](const ChunkWalk& c, int& idx) {
-            idx = 0;
+    } else if (warp == kGLoaderWarp) {
+        // ---------------------------------------------------------- loader --
+        // per chunk: lane j fetches patch j's record with one tensor copy;
+        // the patch indices and frame values are loaded a chunk ahead
+        const uint32_t rec_bytes = (uint32_t)a.g.KB * kAtomBlock * sizeof(float);
+        int idx = 0;
+        float xv = 0.0f;
+        auto load_lane = [&](const ChunkWalk& c, int& i_out, float& x_out) {
+            i_out = 0;
+            x_out = 0.0f;
             if (!c.valid(a)) return;
             const int4 item = a.items[c.it];
             const int e = c.c * kGChunk + lane;
-            if (e < item.z) idx = __ldg(a.Ilist + item.y + e);
-        };
-        auto advance_own = [&](ChunkWalk& c) {
-            do {
-                c.next(a);
-            } while (c.valid(a) && (int)(c.u % kGLoaders) != v);
+            if (e < item.z) {
+                i_out = __ldg(a.Ilist + item.y + e);
+                x_out = __ldg(a.Xlist + item.y + e);
+            }
         };
         ChunkWalk cur = wk;
-        if (cur.valid(a) && (int)(cur.u % kGLoaders) != v) advance_own(cur);
-        int idx = 0;
-        load_idx(cur, idx);
+        load_lane(cur, idx, xv);
+        long long last_u[kGRawSlots];   // the last chunk copied into each slot
+#pragma unroll
+        for (int r = 0; r < kGRawSlots; ++r) last_u[r] = -1;
         while (cur.valid(a)) {
             ChunkWalk nxt = cur;
-            advance_own(nxt);
-            int idx_n = 0;
-            load_idx(nxt, idx_n);
-            const int4 item = a.items[cur.it];
-            const int slot = (int)(cur.u % kGSlots);
-            const uint32_t par = (uint32_t)((cur.u / kGSlots) & 1);
-            if (!warp_wait(&raw_empty[slot], par ^ 1u)) break;
-            float* dst = raw + (size_t)slot * kGRawFloats;
-            const int nvalid = min(kGChunk, item.z - cur.c * kGChunk);
-            const long long woff = ((long long)(lane >> 1) * Npad) * kAtomBlock + (lane & 1) * 4;
-#pragma unroll 8
-            for (int m = 0; m < kGChunk; ++m) {
-                const int i = __shfl_sync(0xffffffffu, idx, m);
-                if (m < nvalid && lane_live)
-                    gm_cp16(dst + m * kGAtoms + 4 * lane, a.W + woff + (long long)i * kAtomBlock);
-            }
-            if (lane < nvalid) gm_cp4(dst + kGChunk * kGAtoms + lane, a.Xlist + item.y + cur.c * kGChunk + lane);
-            gm_cp_arrive(&raw_full[slot]);
+            nxt.next(a);
+            int idx_n;
+            float xv_n;
+            load_lane(nxt, idx_n, xv_n);
+            const int cnt = a.items[cur.it].z;
+            const int nvalid = min(kGChunk, cnt - cur.c * kGChunk);
+            const int rs = (int)(cur.u % kGRawSlots);
+            if (!warp_wait(&raw_empty[rs], (uint32_t)(((cur.u / kGRawSlots) & 1) ^ 1))) break;
+            if (lane < nvalid) rawx[rs * kGChunk + lane] = xv;
+            __syncwarp();
+            if (lane == 0) gm_arrive_tx(&raw_full[rs], (uint32_t)nvalid * rec_bytes);
+            __syncwarp();
+            if (lane < nvalid) gm_tma_record(raw + (size_t)rs * kGRawFloats + lane * kGAtoms, &a.wmap, idx, &raw_full[rs]);
+#pragma unroll
+            for (int r = 0; r < kGRawSlots; ++r)
+                if (r == rs) last_u[r] = cur.u;
             cur = nxt;
             idx = idx_n;
+            xv = xv_n;
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");
+        // no copy may still be writing shared memory when the CTA ends (the
+        // converters have consumed every slot unless a wait gave up)
+        if (lane == 0) {
+#pragma unroll
+            for (int r = 0; r < kGRawSlots; ++r)
+                if (last_u[r] >= 0 && !gm_wait(&raw_full[r], (uint32_t)((last_u[r] / kGRawSlots) & 1)))
+                    atomicExch(a.status, (int)SENSAI_ETIMEOUT);
+        }
     } else if (warp == kGMmaWarp) {
         // ---------------------------------------------------- MMA issuer --
         if (lane == 0) {
@@ -441,8 +478,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
                 const uint32_t acc_tmem = tmem + (uint32_t)(buf * kGAtoms);
                 uint32_t acc = 0;
                 for (int c = wk.c; c < c1; ++c, wk.next(a)) {
-                    const int s = (int)(wk.u % kGSlots);
-                    if (abort_s || !gm_wait(&full_bar[s], (uint32_t)((wk.u / kGSlots) & 1))) {
+                    const int s = (int)(wk.u % kGStages);
+                    if (abort_s || !gm_wait(&full_bar[s], (uint32_t)((wk.u / kGStages) & 1))) {
                         ok = false;
                         break;
                     }
@@ -525,33 +562,47 @@ __global__ void __launch_bounds__(kGThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kGTmemCols) : "memory");
 }
 
-// S_p = sum of pixel p's item partials T^T and Y_p, FP64 sums in item order.
-// One thread per element, every item's load in flight at once.
+// Compensated FP32 summation: (s, c) with s + c the running sum; TwoSum
+// (Knuth) gives the rounding error of each addition exactly, so the result
+// is as accurate as an FP64 sum of these few FP32 terms, at FP32 speed (the
+// FP64 units of this GPU are a small fraction of its FP32 rate).
+__device__ __forceinline__ void gm_sum2(float& s, float& c, float v)
+{
+    const float t = s + v;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (v - bp);
+    s = t;
+    c += e;
+}
+
+// S_p = sum of pixel p's item partials T^T and Y_p, in item order, by
+// compensated FP32 summation, stored in FP64.  One thread per element,
+// every item's load in flight at once.
 __global__ void __launch_bounds__(256) gram_reduce_kernel(GramArgs a)
 {
     const int p = blockIdx.x;
     const int idx = blockIdx.y * blockDim.x + threadIdx.x;   // r * 128 + t
     const int i0 = a.pitem_start[p], i1 = a.pitem_start[p + 1];
-    double s = 0.0;
+    float s = 0.0f, c = 0.0f;
     int j = i0;
-    for (; j + 4 <= i1; j += 4) {
-        float v[4];
+    for (; j + 8 <= i1; j += 8) {
+        float v[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = a.Cpart[(size_t)a.pitem_idx[j + q] * kGAtoms * kGAtoms + idx];
+        for (int q = 0; q < 8; ++q) v[q] = a.Cpart[(size_t)a.pitem_idx[j + q] * kGAtoms * kGAtoms + idx];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) s += (double)v[q];
+        for (int q = 0; q < 8; ++q) gm_sum2(s, c, v[q]);
     }
-    for (; j < i1; ++j) s += (double)a.Cpart[(size_t)a.pitem_idx[j] * kGAtoms * kGAtoms + idx];
-    a.C64[(size_t)p * kGAtoms * kGAtoms + idx] = s;
+    for (; j < i1; ++j) gm_sum2(s, c, a.Cpart[(size_t)a.pitem_idx[j] * kGAtoms * kGAtoms + idx]);
+    a.C64[(size_t)p * kGAtoms * kGAtoms + idx] = (double)s + (double)c;
     if (blockIdx.y == 0 && threadIdx.x < kGAtoms) {
         const int t = threadIdx.x;
-        double y = 0.0;
+        float ys = 0.0f, yc = 0.0f;
         for (int jj = i0; jj < i1; ++jj) {
             const size_t it = (size_t)a.pitem_idx[jj];
 #pragma unroll
-            for (int w = 0; w < kGConverters; ++w) y += (double)a.Ypart[(it * kGConverters + w) * kGAtoms + t];
+            for (int w = 0; w < kGConverters; ++w) gm_sum2(ys, yc, a.Ypart[(it * kGConverters + w) * kGAtoms + t]);
         }
-        a.Y64[(size_t)p * kGAtoms + t] = y;
+        a.Y64[(size_t)p * kGAtoms + t] = (double)ys + (double)yc;
     }
 }
 
@@ -566,6 +617,7 @@ __global__ void __launch_bounds__(kGAtoms) gram_draw_kernel(GramArgs a)
     const int t = threadIdx.x;
     const int K = a.g.K, P = a.g.P;
     const double* cg = a.C64 + (size_t)p * kGAtoms * kGAtoms;
+#pragma unroll 16
     for (int r = 0; r < kGAtoms; ++r) cs[r * (kGAtoms + 1) + t] = cg[(size_t)r * kGAtoms + t];
     __syncthreads();
     // thread t symmetrises the pairs (r, t), r < t: each unordered pair once
@@ -637,7 +689,10 @@ void gram_plan_items(const std::vector<int>& Rbase, int P, int seg, std::vector<
     (*pitem_start)[P] = (int)pitem_idx->size();
 }
 
-size_t gram_smem_bytes() { return sizeof(float) * (size_t)kGSlots * (kGStageFloats + kGRawFloats); }
+size_t gram_smem_bytes()
+{
+    return 1024 + sizeof(float) * ((size_t)kGStages * kGStageFloats + (size_t)kGRawSlots * (kGRawFloats + kGChunk));
+}
 
 // Xlist[e] = x[origin(Ilist[e]) + imgoff[p]] for the entries of pixel p.
 __global__ void xlist_kernel(Geom g, const int* Ilist, const int* Rbase, const int* imgoff, const float* x,
@@ -673,6 +728,27 @@ cudaError_t launch_gram(const GramArgs& a, int grid, cudaStream_t s)
     if (e != cudaSuccess) return e;
     gram_draw_kernel<<<a.g.P, kGAtoms, dsmem, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t gram_weight_map(const Geom& g, const float* W, CUtensorMap* map)
+{
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (!fn || q != cudaDriverEntryPointSuccess) return cudaErrorNotSupported;
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    const cuuint64_t dims[3] = {(cuuint64_t)kAtomBlock, (cuuint64_t)g.Npad, (cuuint64_t)g.KB};
+    const cuuint64_t strides[2] = {(cuuint64_t)kAtomBlock * sizeof(float), (cuuint64_t)g.Npad * kAtomBlock * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)kAtomBlock, 1u, (cuuint32_t)g.KB};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const CUresult r = reinterpret_cast<Encode>(fn)(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(W), dims,
+                                                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 bool gram_available(const Geom& g) { return g.K >= 1 && g.K <= kGAtoms; }

@@ -146,8 +146,11 @@ __global__ void __launch_bounds__(256) prior_s2_kernel(Geom g, const uint32_t* Z
     if (i < g.N) {
         for (int k = 0; k < g.K; ++k) {
             if ((Zb[(long long)k * g.NW + w] >> lane) & 1u) continue;
-            const uint4 blk = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)k, t_it, kTagCodes), key);
-            const float sp = normal32(blk.y, blk.z) * sd;
+            // the normal the code draw of atom k takes from its pair's block
+            const uint4 blk = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(k >> 1), t_it, kTagCodes), key);
+            float nc, ns;
+            normal32_pair(blk.z, blk.w, nc, ns);
+            const float sp = ((k & 1) ? ns : nc) * sd;
             s2 = fmaf(sp, sp, s2);
         }
     }
@@ -280,6 +283,7 @@ __global__ void init_scalars_kernel(int K, double* pi, float* lpi, DevScalars* s
         sc->chg_n = 0;
         sc->chg_obs = 0;
         sc->act_n = 0;
+        sc->rb_obs = 0;
         sc->ge_set = 0;
         sc->status = 0;
     }

@@ -7,6 +7,7 @@
 // with the U^(1/alpha) boost below shape 1, Beta as a ratio of Gammas.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -19,7 +20,7 @@ namespace sensai {
 
 enum : uint32_t {
     kTagInit = 1,   // dictionary initialisation, counter (p, k, 0)
-    kTagCodes = 2,  // sparse-code draw, counter (i, k, t)
+    kTagCodes = 2,  // sparse-code draws of atoms 2m, 2m + 1, counter (i, m, t)
     kTagDict = 3,   // dictionary draw, counter (p, k, t)
     kTagPiA = 4,    // Beta draw of pi_k: numerator Gamma, counter (k, 0, t)
     kTagPiB = 5,    // Beta draw of pi_k: denominator Gamma
@@ -57,6 +58,7 @@ struct DevScalars {
     unsigned long long chg_n;    // code updates whose weight changed
     unsigned long long chg_obs;  // sum of |Omega_i| over those updates
     unsigned long long act_n;    // code draws with z = 1
+    unsigned long long rb_obs;   // in-sweep residual rebuilds: sum over patches of |Omega_i| x non-zero weights
     int ge_set;        // gamma_eps initialised from a frame
     int status;        // sticky error word written by kernels (0 = ok)
     uint32_t t_iter;   // iteration index for kernels replayed from a CUDA graph
@@ -191,19 +193,20 @@ __device__ __forceinline__ double normal64(uint32_t x0, uint32_t x1)
     return sqrt(-2.0 * log(uniform64(x0))) * cospi(2.0 * uniform64(x1));
 }
 
-// Box-Muller in FP32 (used for the code draws): sqrt(-2 ln u1) cos(2 pi u2)
-// with u = (x + 1) 2^-32, evaluated so that no FP32 rounding of the 32-bit
-// words is amplified:
+// Box-Muller in FP32 (used for the code draws): the pair
+// sqrt(-2 ln u1) (cos, sin)(2 pi u2) with u = (x + 1) 2^-32, evaluated so
+// that no FP32 rounding of the 32-bit words is amplified:
 //  * ln u1: for u1 <= 1/2 the hardware log2 (relative error ~2^-22 there);
 //    for u1 > 1/2, with v = 1 - u1 = (2^32-1 - x0) 2^-32 formed in integers,
 //    ln(1 - v) = -(v + v^2/2 + ... + v^8/8) when v < 1/8 (relative
 //    truncation error below 1e-8) and the hardware log2 of 1 - v otherwise
 //    (there |ln(1 - v)| >= 0.13);
 //  * the angle 2 pi (x1 + 1) / 2^32 is split in integers into the nearest
-//    multiple of pi/2 and a remainder d in [-2^29, 2^29), so the cosine is
-//    +-cos or +-sin of t = pi d / 2^31 with |t| <= pi/4, evaluated by their
-//    Taylor series (to t^10 and t^9; remainders below 2e-9).
-__device__ __forceinline__ float normal32(uint32_t x0, uint32_t x1)
+//    multiple of pi/2 (quarter q) and a remainder d in [-2^29, 2^29), so the
+//    cosine and sine are +-cos or +-sin of t = pi d / 2^31 with
+//    |t| <= pi/4, evaluated by their Taylor series (to t^10 and t^9;
+//    remainders below 2e-9).
+__device__ __forceinline__ void normal32_pair(uint32_t x0, uint32_t x1, float& n_cos, float& n_sin)
 {
     const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
     const float ln2 = 0.69314718055994531f;
@@ -243,10 +246,17 @@ __device__ __forceinline__ float normal32(uint32_t x0, uint32_t x1)
     cs = fmaf(-t2 * (1.0f / 30.0f), cs, 1.0f);
     cs = fmaf(-t2 * (1.0f / 12.0f), cs, 1.0f);
     cs = fmaf(-t2 * 0.5f, cs, 1.0f);
-    const float c = (quarter & 1u) ? sn : cs;
-    const float sign = ((quarter + 1u) & 2u) ? -1.0f : 1.0f;   // quarters 1, 2 negative
+    // cos(q pi/2 + t): cos t, -sin t, -cos t, sin t; sin(q pi/2 + t): sin t,
+    // cos t, -sin t, -cos t (q mod 4)
+    const bool odd = (quarter & 1u) != 0;
+    const float c = odd ? sn : cs;
+    const float sv = odd ? cs : sn;
+    const float sign_c = ((quarter + 1u) & 2u) ? -1.0f : 1.0f;   // quarters 1, 2 negative
+    const float sign_s = (quarter & 2u) ? -1.0f : 1.0f;          // quarters 2, 3 negative
     const float m = -2.0f * ln_u1;
-    return sign * c * (m * rsqrtf(fmaxf(m, 1e-30f)));
+    const float rad = m * rsqrtf(fmaxf(m, 1e-30f));
+    n_cos = sign_c * c * rad;
+    n_sin = sign_s * sv * rad;
 }
 
 // Marsaglia-Tsang for shape >= 1; attempt a uses block (c0, c1, t, tag | a << 8):
@@ -406,6 +416,7 @@ struct DictSpaceArgs {
 
 // The dictionary step in its dense-statistics form (gram.cu).
 struct GramArgs {
+    CUtensorMap wmap;          // W as a 3-D tensor (8 floats, Npad patches, KB blocks) for one-record copies
     Geom g;
     const float* W;            // [KB][Npad][8]
     const int* Ilist;          // per pixel p: the patches observing p (Rbase layout)
@@ -597,7 +608,9 @@ void gram_plan_items(const std::vector<int>& Rbase, int P, int seg, std::vector<
                      std::vector<int>* pitem_start, std::vector<int>* pitem_idx);
 cudaError_t launch_xlist(const Geom& g, const int* Ilist, const int* Rbase, int max_slots, const int* imgoff,
                          const float* x, float* Xlist, cudaStream_t s);
-cudaError_t launch_gram(const GramArgs& a, int grid, cudaStream_t s);   // statistics, then the draws
+cudaError_t launch_gram(const GramArgs& a, int grid, cudaStream_t s);
+// The tensor map of W for gram_kernel's record copies (box: one patch's KB blocks).
+cudaError_t gram_weight_map(const Geom& g, const float* W, CUtensorMap* map);   // statistics, then the draws
 cudaError_t launch_geometry(const Geom& g, const uint8_t* mask_bytes, uint32_t* mask_bits, int* imgoff,
                             uint16_t* nobs, int* maxobs, unsigned long long* total, cudaStream_t s);
 cudaError_t launch_fill_obs(const Geom& g, const uint32_t* mask_bits, const int* imgoff, uint16_t* obs, cudaStream_t s);

@@ -6,8 +6,8 @@
 //   n   = sum_{p in Omega_i} d_kp^2,   g = sum_{p in Omega_i} d_kp r_ip + w_ik n
 //   lam = gamma_s + gamma_eps n
 //   L   = logit(pi_k) + 1/2 ln(gamma_s / lam) + gamma_eps^2 g^2 / (2 lam)
-//   z_ik = [ x0 < floor(sigmoid(L) 2^32) ],  x = Philox(i, k, t, CODES)
-//   s_ik = gamma_eps g / lam + lam^-1/2 BoxMuller(x1, x2)   if z_ik = 1
+//   z_ik = [ x_{k%2} < floor(sigmoid(L) 2^32) ],  x = Philox(i, floor(k/2), t, CODES)
+//   s_ik = gamma_eps g / lam + lam^-1/2 BoxMuller_{k%2}(x2, x3)   if z_ik = 1
 //   r_i -= d_k (w_new - w_old) on Omega_i
 // (z with s integrated out, then s | z = 1; inactive weights are not stored).
 //
@@ -89,18 +89,26 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
         const bool from_resid = a.R_in != nullptr;
         gather_patch<MAXOBS, LANES>(a, slot, nl, org, ad, r, half, from_resid);
 
-        // else the residual r = x - D w on the observed pixels, from the stored weights
+        // else the residual r = x - D w on the observed pixels, from the stored
+        // weights (two blocks loaded ahead of their use)
         if (!from_resid) {
+            W8 p0 = load_w8(a.W + (long long)i * kAtomBlock);
+            W8 p1 = p0;
+            if (KB > 1) p1 = load_w8(a.W + (Npad + i) * kAtomBlock);
             for (int kb = 0; kb < KB; ++kb) {
+                const W8 wb = p0;
+                p0 = p1;
+                if (kb + 2 < KB) p1 = load_w8(a.W + ((long long)(kb + 2) * Npad + i) * kAtomBlock);
                 ad.rebase(col0 + 32u * kb, lp.wmax);
-                rebuild_block<MAXOBS>(ad, r, lp.wmax, load_w8(a.W + ((long long)kb * Npad + i) * kAtomBlock));
+                rebuild_block<MAXOBS>(ad, r, lp.wmax, wb);
+                tl.rb_obs += (unsigned int)nl * w8_nonzero(wb);
             }
         }
 
         float s2 = 0.0f;
         AtomCarry carry;
         carry.dw = 0.0f;
-        carry.rnd = code_random(i, 0, t_it, a.keys);
+        carry.cur = code_pair(i, 0, t_it, a.keys);
         W8 nb = load_w8(a.W + (long long)i * kAtomBlock);
         for (int kb = 0; kb < KB; ++kb) {
             W8 wb = nb;

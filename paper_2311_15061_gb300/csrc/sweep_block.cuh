@@ -19,8 +19,9 @@
 //  * the block's 8 atoms are unrolled at compile time, so each dictionary
 //    read is one shared load at a register address plus an immediate column
 //    offset (the per-pixel row addresses are rebased once per block);
-//  * the Philox block and Box-Muller normal of atom k+1 are computed inside
-//    atom k's scalar chain, on which they do not depend.
+//  * one Philox block and one Box-Muller pair serve two atoms (2m, 2m + 1);
+//    the next pair's are computed inside atom 2m's scalar chain, on which
+//    they do not depend.
 #pragma once
 #include <type_traits>
 
@@ -208,22 +209,35 @@ __device__ __forceinline__ uint32_t even_lane_bits(uint32_t b)
 // Work tallies of one thread (changed updates, their |Omega_i|, z = 1 draws).
 struct CodeTally {
     unsigned int chg_n = 0, chg_obs = 0, act_n = 0;
+    unsigned int rb_obs = 0;   // in-sweep residual rebuild: this lane's pixels x non-zero stored weights
 };
 
-// The random numbers of one code draw: word 0 of the Philox block at counter
-// (i, k, t, codes) decides z; words 1-2 give the Box-Muller normal.
-struct CodeRandom {
-    uint32_t x0;
-    float nrm;
-};
-
-__device__ __forceinline__ CodeRandom code_random(long long i, int k, uint32_t t, const PhiloxKeys& keys)
+// Non-zero weights of a stored 8-atom block.
+__device__ __forceinline__ unsigned int w8_nonzero(const W8& wb)
 {
-    const uint4 blk = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)k, t, kTagCodes), keys);
-    CodeRandom cr;
-    cr.x0 = blk.x;
-    cr.nrm = normal32(blk.y, blk.z);
-    return cr;
+    unsigned int c = 0;
+#pragma unroll
+    for (int kk = 0; kk < kAtomBlock; ++kk) c += wb.v[kk] != 0.0f ? 1u : 0u;
+    return c;
+}
+
+// The random numbers of the code draws of atoms 2m and 2m + 1: one Philox
+// block at counter (i, m, t, codes); word k % 2 decides z_ik, words 2-3 give
+// one Box-Muller pair (the cosine normal for the even atom, the sine one for
+// the odd atom).
+struct CodePair {
+    uint32_t x0[2];
+    float nrm[2];
+};
+
+__device__ __forceinline__ CodePair code_pair(long long i, int m, uint32_t t, const PhiloxKeys& keys)
+{
+    const uint4 blk = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)m, t, kTagCodes), keys);
+    CodePair cp;
+    cp.x0[0] = blk.x;
+    cp.x0[1] = blk.y;
+    normal32_pair(blk.z, blk.w, cp.nrm[0], cp.nrm[1]);
+    return cp;
 }
 
 // Per-lane facts of the patch being swept.
@@ -237,17 +251,18 @@ struct LanePatch {
 };
 
 // Carried from one atom to the next: the pending rank-1 update of the
-// previous atom and the random numbers of the next one.
+// previous atom, the random numbers of the current atom pair and, from the
+// pair's even atom on, those of the next pair.
 struct AtomCarry {
     float dw;
-    CodeRandom rnd;
+    CodePair cur, nxt;
 };
 
 // The block's atoms kbase .. kbase + 7 in order (atoms >= K are padding: their
 // columns are zero and their z is 0).  ad is at the block.  On entry
 // carry.dw is the previous atom's update, still to be applied (FUSE: its
 // column is the one before the block; otherwise it must be 0), and
-// carry.rnd the random numbers of atom kbase.  wb holds the stored weights;
+// carry.cur the random numbers of atoms kbase, kbase + 1.  wb holds the stored weights;
 // on return, the new ones, and carry.dw atom kbase + 7's update, applied to r
 // unless FUSE (then the next block's first pass applies it).  Returns whether
 // a weight of the block changed.
@@ -268,8 +283,13 @@ __device__ __forceinline__ bool code_block(const PixelAddr<MAXOBS>& ad, Resid<MA
             n += __shfl_xor_sync(0xffffffffu, n, 1);
             h += __shfl_xor_sync(0xffffffffu, h, 1);
         }
-        const CodeRandom rnd = carry.rnd;
-        carry.rnd = code_random(lp.i, k + 1, t, keys);   // the next atom's, independent of this chain
+        // kbase is a multiple of 8, so k and KK have the same parity
+        const uint32_t x0 = carry.cur.x0[KK & 1];
+        const float nrm = carry.cur.nrm[KK & 1];
+        if constexpr ((KK & 1) == 0)
+            carry.nxt = code_pair(lp.i, (k >> 1) + 1, t, keys);   // the next pair's, independent of this chain
+        else
+            carry.cur = carry.nxt;
         const bool owner = LANES == 1 || (lp.lane & 1) == 0;
         const float w_old = wb.v[KK];
         const float g = fmaf(w_old, n, h);
@@ -282,10 +302,10 @@ __device__ __forceinline__ bool code_block(const PixelAddr<MAXOBS>& ad, Resid<MA
         // 2^32) accepts every word (a 64-bit conversion would run on the
         // FP64 pipe)
         const uint32_t thr = __float2uint_rz(sig * 4294967296.0f);
-        const bool z = lp.valid && k < K && (rnd.x0 < thr || sig >= 1.0f);
+        const bool z = lp.valid && k < K && (x0 < thr || sig >= 1.0f);
         // branch-free from here to the ballot: one basic block per atom lets
         // the next atom's random numbers interleave with this chain
-        const float w_new = z ? fmaf(rnd.nrm, sqrtf(rlam), c.ge * g * rlam) : 0.0f;
+        const float w_new = z ? fmaf(nrm, sqrtf(rlam), c.ge * g * rlam) : 0.0f;
         const bool zo = z && owner;
         s2 = zo ? fmaf(w_new, w_new, s2) : s2;
         tl.act_n += zo ? 1u : 0u;
@@ -398,17 +418,19 @@ __device__ __forceinline__ long long slot_patch(const SweepArgs& a, long long sl
 // A warp's work counters, once per launch.
 __device__ __forceinline__ void flush_counts(const SweepArgs& a, int lane, const CodeTally& tl)
 {
-    unsigned long long cn = tl.chg_n, co = tl.chg_obs, ca = tl.act_n;
+    unsigned long long cn = tl.chg_n, co = tl.chg_obs, ca = tl.act_n, rb = tl.rb_obs;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         cn += __shfl_down_sync(0xffffffffu, cn, o);
         co += __shfl_down_sync(0xffffffffu, co, o);
         ca += __shfl_down_sync(0xffffffffu, ca, o);
+        rb += __shfl_down_sync(0xffffffffu, rb, o);
     }
-    if (lane == 0 && (cn | ca)) {
+    if (lane == 0 && (cn | ca | rb)) {
         atomicAdd(&a.sc_out->chg_n, cn);
         atomicAdd(&a.sc_out->chg_obs, co);
         atomicAdd(&a.sc_out->act_n, ca);
+        atomicAdd(&a.sc_out->rb_obs, rb);
     }
 }
 

@@ -190,7 +190,7 @@ __device__ __forceinline__ void tiled_body(const SweepArgs& a)
         W8 nb;
         AtomCarry carry;
         carry.dw = 0.0f;
-        carry.rnd = code_random(i, 0, t_it, a.keys);
+        carry.cur = code_pair(i, 0, t_it, a.keys);
         for (int pass = from_resid ? 1 : 0; pass < 2 && ok; ++pass) {
             for (int sl = 0; sl < S; ++sl, ++q) {
                 const int b = (int)(q & 1);
@@ -209,8 +209,9 @@ __device__ __forceinline__ void tiled_body(const SweepArgs& a)
                     if (pass == 0) {
                         for (int kb = kb0; kb < kb1; ++kb) {
                             ad.rebase(col0 + 32u * (kb - kb0), lp.wmax);
-                            rebuild_block<MAXOBS>(ad, r, lp.wmax,
-                                                  load_w8(a.W + ((long long)kb * Npad + irec) * kAtomBlock));
+                            const W8 wb = load_w8(a.W + ((long long)kb * Npad + irec) * kAtomBlock);
+                            rebuild_block<MAXOBS>(ad, r, lp.wmax, wb);
+                            tl.rb_obs += (unsigned int)nl * w8_nonzero(wb);
                         }
                     } else {
                         if (sl == 0) nb = load_w8(a.W + irec * kAtomBlock);

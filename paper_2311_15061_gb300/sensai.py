@@ -87,6 +87,7 @@ class sensai_stats(ctypes.Structure):
         ("active_draws", ctypes.c_int64),
         ("slice_atoms", ctypes.c_int32),
         ("slices", ctypes.c_int32),
+        ("rebuild_observed", ctypes.c_int64),
     ]
 
 

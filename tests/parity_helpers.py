@@ -87,7 +87,7 @@ def compare_codes(st_before, g, ost, L, patches=None):
     for r in flip_patches:
         i = int(idx[r])
         k = int(np.argmax(diff[r]))
-        x0 = int(O.philox([i, k, st_before.t & 0xFFFFFFFF, O.TAG_ZS], key)[0])
+        x0 = int(O.philox([i, k >> 1, st_before.t & 0xFFFFFFFF, O.TAG_ZS], key)[k & 1])
         sig = 1.0 / (1.0 + np.exp(-L[i, k]))
         thr = int(np.floor(sig * 4294967296.0))
         assert abs(x0 - thr) <= Z_MARGIN, (i, k, x0, thr, L[i, k])

@@ -82,6 +82,23 @@ def test_box_muller_is_standard_normal():
     assert abs(x.var() - 1.0) < 5 * np.sqrt(2.0 / len(x))
 
 
+def test_box_muller_pair_is_two_independent_normals():
+    """The code draws' pair (cosine for the even atom, sine for the odd one):
+    each component standard normal, uncorrelated, and their squared radius
+    chi-square with 2 degrees of freedom (exponential, mean 2) -- which fails
+    if both took the cosine or the radius were not shared."""
+    n = 60000
+    a = np.array([O.normal_pair(7, [j, 3, 5, O.TAG_ZS], 0) for j in range(n)])
+    b = np.array([O.normal_pair(7, [j, 3, 5, O.TAG_ZS], 1) for j in range(n)])
+    for x in (a, b):
+        assert stats.kstest(x, "norm").pvalue > 1e-3
+    assert abs(np.corrcoef(a, b)[0, 1]) < 5 / np.sqrt(n)
+    assert stats.kstest(a * a + b * b, stats.expon(scale=2.0).cdf).pvalue > 1e-3
+    # independent of the words 0-1 normal of the same block
+    c = np.array([O.normal(7, [j, 3, 5, O.TAG_ZS]) for j in range(n)])
+    assert abs(np.corrcoef(a, c)[0, 1]) < 5 / np.sqrt(n)
+
+
 @pytest.mark.parametrize("shape", [0.05, 0.3, 1.0, 2.5, 50.0, 3e4])
 def test_gamma_matches_scipy(shape):
     n = 40000
