@@ -107,7 +107,7 @@ struct sensai_ctx {
     CUtensorMap wmap;           // W for gram_kernel's record copies (set on first use)
     bool wmap_set = false;
     float* Cpart = nullptr;     // [items][128][128]
-    float* Ypart = nullptr;     // [items][4][128]
+    float* Ypart = nullptr;     // [items][128]
     double* C64 = nullptr;      // [P][128][128]
     double* Y64 = nullptr;      // [P][128]
     int* pitem_start = nullptr; // [P + 1]
@@ -175,9 +175,12 @@ void free_all(sensai_ctx* c)
                     c->misc, c->x, c->D, c->W, c->Zb, c->R, c->Y, c->out, c->pi, c->lpi, c->m,
                     c->part_s2, c->part_r2, c->chunk_counter, c->sc, c->pos, c->Dsl, c->ge_part, c->Dc,
                     c->perm, c->mean_acc, c->Xlist, c->items, c->Cpart, c->Ypart, c->pitem_start,
-                    c->pitem_idx, c->C64, c->Y64};
+                    c->pitem_idx, c->C64, c->Y64, c->sweep_plan.counter2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (c->sweep_plan.fork) cudaEventDestroy(c->sweep_plan.fork);
+    if (c->sweep_plan.join) cudaEventDestroy(c->sweep_plan.join);
+    if (c->sweep_plan.side) cudaStreamDestroy(c->sweep_plan.side);
     ds_free(&c->ds);
 }
 
@@ -739,7 +742,7 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
         CREATE_CUDA(dalloc(&ctx->pitem_start, ps.size()));
         CREATE_CUDA(dalloc(&ctx->pitem_idx, pi.size()));
         CREATE_CUDA(dalloc(&ctx->Cpart, items.size() * 128 * 128));
-        CREATE_CUDA(dalloc(&ctx->Ypart, items.size() * 4 * 128));
+        CREATE_CUDA(dalloc(&ctx->Ypart, items.size() * 128));
         CREATE_CUDA(dalloc(&ctx->C64, (size_t)P * 128 * 128));
         CREATE_CUDA(dalloc(&ctx->Y64, (size_t)P * 128));
         CREATE_CUDA(cudaMemcpy(ctx->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
@@ -750,6 +753,7 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
         ctx->gram_grid = (int)std::min<long long>(ctx->n_items, sms_g);
     }
 
+    unsigned int split_units = 0;
     {
         // the code sweep's order: patches by decreasing |Omega_i|, so that
         // the 32 patches of a warp have nearly equal counts (a warp's loops
@@ -758,6 +762,12 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
         std::vector<int> hp((size_t)g.Npad);
         CREATE_CUDA(cudaMemcpy(hn.data(), ctx->nobs, sizeof(uint16_t) * (size_t)N, cudaMemcpyDeviceToHost));
         sweep_order_host(hn.data(), N, g.Npad, hp.data());
+        // work units (32 slots) whose largest count exceeds the light
+        // kernel's capacity: a prefix, slots being in decreasing order
+        split_units = 0;
+        while ((long long)split_units < g.NW && (long long)split_units * 32 < N &&
+               hn[(size_t)hp[(size_t)split_units * 32]] > kSplitObs)
+            ++split_units;
         CREATE_CUDA(dalloc(&ctx->perm, (size_t)g.Npad));
         CREATE_CUDA(cudaMemcpy(ctx->perm, hp.data(), sizeof(int) * (size_t)g.Npad, cudaMemcpyHostToDevice));
         const size_t rows = (size_t)(ctx->maxobs > 0 ? ctx->maxobs : 1);
@@ -818,6 +828,21 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
             return bail(SENSAI_EINVAL);
         }
         if (ctx->sweep_plan.slice_atoms > 0) CREATE_CUDA(dalloc(&ctx->Dsl, (size_t)slice_capacity_floats(g)));
+        SweepPlan& sp = ctx->sweep_plan;
+        if (sp.slice_atoms == 0 && sp.lanes == 1 && ctx->maxobs > kSplitObs && split_units > 0 &&
+            (long long)split_units < g.NW && !stream) {
+            sp.split_units = split_units;
+            sp.split_grid = std::min(sp.grid, (int)((split_units + 7) / 8));
+            sp.light_grid = sweep_grid_size(g, kSplitObs, device);
+            if (sp.light_grid > 0) {
+                CREATE_CUDA(cudaStreamCreateWithFlags(&sp.side, cudaStreamNonBlocking));
+                CREATE_CUDA(cudaEventCreateWithFlags(&sp.fork, cudaEventDisableTiming));
+                CREATE_CUDA(cudaEventCreateWithFlags(&sp.join, cudaEventDisableTiming));
+                CREATE_CUDA(dalloc(&sp.counter2, 1));
+            } else {
+                sp.split_units = 0;
+            }
+        }
     }
     if (reset_state(ctx, st0) != SENSAI_OK) return bail(SENSAI_ECUDA);
     CREATE_CUDA(cudaDeviceSynchronize());

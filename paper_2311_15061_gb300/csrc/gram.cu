@@ -74,23 +74,24 @@ constexpr int kGEpilogue0 = 4;                  // warps 4-7
 constexpr int kGMmaWarp = 8;
 constexpr int kGLoaderWarp = 9;
 constexpr int kGThreads = 32 * (kGLoaderWarp + 1);
-constexpr int kGRawSlots = 5;                   // raw record ring (TMA destination)
-constexpr int kGStages = 4;                     // operand stages
+constexpr int kGRawSlots = 8;                   // raw record ring (TMA destination)
+constexpr int kGStages = 2;                     // operand stages (A in TMEM, B in shared memory)
 constexpr int kGGroup = 4;                      // chunks per accumulator drain
 constexpr int kGSegment = 2048;                 // most patches of an item
 constexpr int kGRawFloats = kGChunk * kGAtoms;  // one chunk's records [32 patches][128 atoms]
 constexpr int kGSboBytes = 272;                 // 8-row group pitch (256 B of data + 16 B)
 constexpr int kGOpFloats = (kGAtoms / 8) * kGSboBytes / 4;   // one 128 x 8 operand: 1088 floats
-constexpr int kGStageFloats = 2 * (kGChunk / kGStep) * kGOpFloats;   // H[4], then 2L[4]
-constexpr int kGTmemCols = 4 * kGAtoms;         // two accumulators, the running sums, unused
-constexpr int kGSumCol = 2 * kGAtoms;           // the running sums' columns
+constexpr int kGStageFloats = (kGChunk / kGStep) * kGOpFloats;   // B = H of a chunk: 4 operands
+constexpr int kGTmemCols = 4 * kGAtoms;         // two accumulators, the A stages, the running sums
+constexpr int kGACol0 = 2 * kGAtoms;            // stage s's A operands: columns kGACol0 + 64 s ..
+constexpr int kGAStageCols = 2 * kGChunk;       // H (32 patch columns), then 2L (32)
+constexpr int kGSumCol = kGACol0 + kGStages * kGAStageCols;   // the running sums' 128 columns
+static_assert(kGSumCol + kGAtoms <= kGTmemCols, "tensor memory columns");
 constexpr long long kGSpins = 1LL << 22;
 
-// A converter waits on the stage and the raw slot of its next chunk only
-// after those of its previous chunk (kGConverters chunks earlier); with at
-// least as many stages and slots as converters, no barrier it waits on can
-// be two phases behind (a parity wait would then pass early).
-static_assert(kGStages >= kGConverters && kGRawSlots >= kGConverters, "phase aliasing");
+// Every converter warp takes part in every chunk (its quarter of the atoms),
+// so each waits on every phase of every barrier in order.
+static_assert(kGConverters == 4, "converter warp q writes TMEM lane quarter q");
 
 
 __device__ __forceinline__ uint32_t gm_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -179,6 +180,31 @@ __device__ __forceinline__ void gm_mma(uint32_t tmem, uint64_t a, uint64_t b, ui
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
+}
+
+// D (+)= A B^T with A (M = 128 rows, one per TMEM lane; K = 8 columns) in
+// tensor memory and B described in shared memory.
+__device__ __forceinline__ void gm_mma_tmem_a(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// 16 consecutive accumulator columns of this warp's 32 lanes.
+__device__ __forceinline__ void gm_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
 __device__ __forceinline__ void gm_commit(uint64_t* bar)
@@ -279,12 +305,12 @@ __global__ void __launch_bounds__(kGThreads, 1)
     if (tid == 0) {
         abort_s = 0;
         for (int s = 0; s < kGStages; ++s) {
-            gm_bar_init(&full_bar[s], 1);
-            gm_bar_init(&empty_bar[s], 1);
+            gm_bar_init(&full_bar[s], kGConverters);   // lane 0 of every converter warp
+            gm_bar_init(&empty_bar[s], 1);             // the MMA commit
         }
         for (int r = 0; r < kGRawSlots; ++r) {
-            gm_bar_init(&raw_full[r], 1);
-            gm_bar_init(&raw_empty[r], 1);
+            gm_bar_init(&raw_full[r], 1);              // the loader (and the copies' bytes)
+            gm_bar_init(&raw_empty[r], kGConverters);
         }
         for (int b = 0; b < 2; ++b) {
             gm_bar_init(&accf_bar[b], 1);
@@ -322,89 +348,57 @@ __global__ void __launch_bounds__(kGThreads, 1)
     wk.start(a);
     if (warp < kGConverters) {
         // ----------------------------------------------------- converters --
-        // chunks w, w + 4, ...: lane l takes atoms 4l .. 4l + 3 of the 32
-        // patches from the raw slot, 8 patches at a time, and writes them
-        // split into the chunk's operand stage
-        const int w = warp;
-        bool live[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) live[r] = 4 * lane + r < K;
-        // float offset of this lane's atom 4l + r, patches 4q .. 4q + 3 of a
-        // 128 x 8 operand (8-row group l / 2, row 4 (l % 2) + r in it)
-        const int op_base = (lane >> 1) * (kGSboBytes / 4) + (lane & 1) * 16;
-        float y[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        // warp q, every chunk: lane l holds atom a = 32 q + l of the chunk's
+        // 32 patches; writes its row of the A operands H and 2L into tensor
+        // memory (TMEM lane a, one column per patch) and its row of B = H
+        // into the chunk's shared-memory stage, and accumulates Y_pa
+        const int q = warp;
+        const int atom = 32 * q + lane;
+        const bool live = atom < K;
+        // float offset of (row atom, patches 4 c4 .. + 3) in a 128 x 8 operand
+        const int b_base = (atom >> 3) * (kGSboBytes / 4) + (atom & 7) * 4;
+        const uint32_t tm_lanes = tmem + ((uint32_t)(32 * q) << 16);
+        float y = 0.0f;
         bool ok = true;
         for (; wk.valid(a) && ok; wk.next(a)) {
-            if ((int)(wk.u % kGConverters) == w) {
-                const int cnt = a.items[wk.it].z;
-                const int nvalid = min(kGChunk, cnt - wk.c * kGChunk);
-                const int rs = (int)(wk.u % kGRawSlots);
-                const int st = (int)(wk.u % kGStages);
-                if (!(ok = warp_wait(&raw_full[rs], (uint32_t)((wk.u / kGRawSlots) & 1)))) break;
-                if (!(ok = warp_wait(&empty_bar[st], (uint32_t)(((wk.u / kGStages) & 1) ^ 1)))) break;
-                const float* rw = raw + (size_t)rs * kGRawFloats;
-                const float xl = rawx[rs * kGChunk + lane];
-                float* stg = stages + (size_t)st * kGStageFloats;
+            const int cnt = a.items[wk.it].z;
+            const int nvalid = min(kGChunk, cnt - wk.c * kGChunk);
+            const int rs = (int)(wk.u % kGRawSlots);
+            const int st = (int)(wk.u % kGStages);
+            if (!(ok = warp_wait(&raw_full[rs], (uint32_t)((wk.u / kGRawSlots) & 1)))) break;
+            if (!(ok = warp_wait(&empty_bar[st], (uint32_t)(((wk.u / kGStages) & 1) ^ 1)))) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const float* rw = raw + (size_t)rs * kGRawFloats;
+            const float* rx = rawx + rs * kGChunk;
+            float h[kGChunk], l2[kGChunk];
 #pragma unroll
-                for (int kb = 0; kb < kGChunk / kGStep; ++kb) {
-                    float4 v[kGStep];
+            for (int j = 0; j < kGChunk; ++j) {
+                const bool pv = j < nvalid;
+                const float w = (pv && live) ? rw[j * kGAtoms + atom] : 0.0f;
+                y = fmaf(w, pv ? rx[j] : 0.0f, y);
+                h[j] = gm_head(w);
+                l2[j] = 2.0f * (w - h[j]);   // exact: h is w truncated, doubling is exact
+            }
+            const uint32_t acol = (uint32_t)(kGACol0 + st * kGAStageCols);
+            gm_st32(tm_lanes + acol, h);
+            if (split) gm_st32(tm_lanes + acol + kGChunk, l2);
+            float* stg = stages + (size_t)st * kGStageFloats;
 #pragma unroll
-                    for (int j = 0; j < kGStep; ++j)
-                        v[j] = *reinterpret_cast<const float4*>(rw + (kb * kGStep + j) * kGAtoms + 4 * lane);
-#pragma unroll
-                    for (int j = 0; j < kGStep; ++j) {
-                        const bool pv = kb * kGStep + j < nvalid;
-                        const float xj = __shfl_sync(0xffffffffu, pv ? xl : 0.0f, kb * kGStep + j);
-                        v[j].x = (pv && live[0]) ? v[j].x : 0.0f;
-                        v[j].y = (pv && live[1]) ? v[j].y : 0.0f;
-                        v[j].z = (pv && live[2]) ? v[j].z : 0.0f;
-                        v[j].w = (pv && live[3]) ? v[j].w : 0.0f;
-                        y[0] = fmaf(v[j].x, xj, y[0]);
-                        y[1] = fmaf(v[j].y, xj, y[1]);
-                        y[2] = fmaf(v[j].z, xj, y[2]);
-                        y[3] = fmaf(v[j].w, xj, y[3]);
-                    }
-                    float* oh = stg + kb * kGOpFloats + op_base;
-                    float* ol = stg + (kGChunk / kGStep + kb) * kGOpFloats + op_base;
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const float4* e = v + 4 * q;   // patches 4q .. 4q + 3 of the block
-                        const float4 hx = make_float4(gm_head(e[0].x), gm_head(e[1].x), gm_head(e[2].x), gm_head(e[3].x));
-                        const float4 hy = make_float4(gm_head(e[0].y), gm_head(e[1].y), gm_head(e[2].y), gm_head(e[3].y));
-                        const float4 hz = make_float4(gm_head(e[0].z), gm_head(e[1].z), gm_head(e[2].z), gm_head(e[3].z));
-                        const float4 hw = make_float4(gm_head(e[0].w), gm_head(e[1].w), gm_head(e[2].w), gm_head(e[3].w));
-                        *reinterpret_cast<float4*>(oh + q * 32 + 0) = hx;
-                        *reinterpret_cast<float4*>(oh + q * 32 + 4) = hy;
-                        *reinterpret_cast<float4*>(oh + q * 32 + 8) = hz;
-                        *reinterpret_cast<float4*>(oh + q * 32 + 12) = hw;
-                        if (split) {
-                            // 2 (w - h): exact (h is w truncated; doubling is exact)
-                            *reinterpret_cast<float4*>(ol + q * 32 + 0) =
-                                make_float4(2.0f * (e[0].x - hx.x), 2.0f * (e[1].x - hx.y), 2.0f * (e[2].x - hx.z),
-                                            2.0f * (e[3].x - hx.w));
-                            *reinterpret_cast<float4*>(ol + q * 32 + 4) =
-                                make_float4(2.0f * (e[0].y - hy.x), 2.0f * (e[1].y - hy.y), 2.0f * (e[2].y - hy.z),
-                                            2.0f * (e[3].y - hy.w));
-                            *reinterpret_cast<float4*>(ol + q * 32 + 8) =
-                                make_float4(2.0f * (e[0].z - hz.x), 2.0f * (e[1].z - hz.y), 2.0f * (e[2].z - hz.z),
-                                            2.0f * (e[3].z - hz.w));
-                            *reinterpret_cast<float4*>(ol + q * 32 + 12) =
-                                make_float4(2.0f * (e[0].w - hw.x), 2.0f * (e[1].w - hw.y), 2.0f * (e[2].w - hw.z),
-                                            2.0f * (e[3].w - hw.w));
-                        }
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) gm_arrive(&raw_empty[rs]);   // the slot may be refilled
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) gm_arrive(&full_bar[st]);
+            for (int c4 = 0; c4 < kGChunk / 4; ++c4)   // operand c4 / 2, patch quad c4 % 2
+                *reinterpret_cast<float4*>(stg + (c4 >> 1) * kGOpFloats + b_base + (c4 & 1) * 32) =
+                    make_float4(h[4 * c4], h[4 * c4 + 1], h[4 * c4 + 2], h[4 * c4 + 3]);
+            gm_st_wait();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                gm_arrive(&raw_empty[rs]);
+                gm_arrive(&full_bar[st]);
             }
             if (wk.c == wk.nch - 1) {
-                // the end of an item: this warp's share of Y_p (its chunks)
-                float4 yo = make_float4(y[0], y[1], y[2], y[3]);
-                *reinterpret_cast<float4*>(a.Ypart + ((size_t)wk.it * kGConverters + w) * kGAtoms + 4 * lane) = yo;
-                y[0] = y[1] = y[2] = y[3] = 0.0f;
+                // the end of an item: Y_p for this warp's 32 atoms
+                a.Ypart[(size_t)wk.it * kGAtoms + atom] = y;
+                y = 0.0f;
             }
         }
     } else if (warp == kGLoaderWarp) {
@@ -485,12 +479,14 @@ __global__ void __launch_bounds__(kGThreads, 1)
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const float* stg = stages + (size_t)s * kGStageFloats;
+                    const uint32_t acol = tmem + (uint32_t)(kGACol0 + s * kGAStageCols);
                     const int nvalid = min(kGChunk, cnt - c * kGChunk);
                     for (int kb = 0; kb * kGStep < nvalid; ++kb) {
-                        const uint64_t dh = gm_desc(stg + kb * kGOpFloats);
-                        gm_mma(acc_tmem, dh, dh, idesc, acc);
+                        const uint64_t bh = gm_desc(stg + kb * kGOpFloats);
+                        gm_mma_tmem_a(acc_tmem, acol + (uint32_t)(kb * kGStep), bh, idesc, acc);   // H H^T
                         acc = 1;
-                        if (split) gm_mma(acc_tmem, dh, gm_desc(stg + (kGChunk / kGStep + kb) * kGOpFloats), idesc, 1u);
+                        if (split)   // 2L H^T
+                            gm_mma_tmem_a(acc_tmem, acol + (uint32_t)(kGChunk + kb * kGStep), bh, idesc, 1u);
                     }
                     gm_commit(&empty_bar[s]);
                 }
@@ -600,7 +596,7 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(GramArgs a)
         for (int jj = i0; jj < i1; ++jj) {
             const size_t it = (size_t)a.pitem_idx[jj];
 #pragma unroll
-            for (int w = 0; w < kGConverters; ++w) gm_sum2(ys, yc, a.Ypart[(it * kGConverters + w) * kGAtoms + t]);
+            gm_sum2(ys, yc, a.Ypart[it * kGAtoms + t]);
         }
         a.Y64[(size_t)p * kGAtoms + t] = (double)ys + (double)yc;
     }

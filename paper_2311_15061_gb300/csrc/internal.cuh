@@ -351,6 +351,8 @@ struct SweepArgs {
     double* part_s2;           // [NW] per 32-patch chunk
     double* part_r2;           // [NW] per 32-patch chunk
     unsigned int* chunk_counter;  // work counter, zeroed before each launch
+    unsigned int unit_lo = 0;     // the launch's work units: unit_lo + counter values below unit_hi
+    unsigned int unit_hi = 0;     // (0: every unit)
     DevScalars* sc_out;           // change counters (same object as sc)
     PhiloxKeys keys;              // round keys of the seed
     uint32_t t;
@@ -424,7 +426,7 @@ struct GramArgs {
     const int4* items;         // (p, first entry, entries, -): segments of the per-pixel lists
     long long n_items;
     float* Cpart;              // [items][128][128] per-item partials T^T, C = (T + T^T) / 2 (FP32)
-    float* Ypart;              // [items][4][128] per-item correlation partials (FP32)
+    float* Ypart;              // [items][128] per-item correlation partials (FP32)
     double* C64;               // [P][128][128] FP64 sums of the partials (symmetrised by the draws)
     double* Y64;               // [P][128] Y_p
     const int* pitem_start;    // [P + 1] pixel p's items: pitem_idx[pitem_start[p] ..]
@@ -543,7 +545,18 @@ struct SweepPlan {
     int slice_atoms = 0;
     int slices = 0;
     long long slice_stride = 0;
+    // Split by observed-pixel count (resident dictionary, one lane per
+    // patch): the first split_units work units (slots in decreasing |Omega_i|
+    // order) run the kernel for the largest count on split_grid CTAs, the
+    // rest the kernel for kSplitObs pixels on light_grid CTAs, concurrently
+    // (the latter on `side`, forked and joined by events); 0: no split.
+    unsigned int split_units = 0;
+    int split_grid = 0, light_grid = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    unsigned int* counter2 = nullptr;
 };
+constexpr int kSplitObs = 16;   // the light kernel's pixel capacity (3 CTAs per SM)
 // Resident when it fits (unless force_stream); else the largest slice that
 // fits, or force_slice_atoms (a multiple of 8 no larger than that) if > 0.
 bool plan_sweep(const Geom& g, int maxobs, int device, bool force_stream, int force_slice_atoms, SweepPlan* out);
@@ -553,6 +566,7 @@ long long slice_capacity_floats(const Geom& g);
 // null) receives the number of kernels launched.
 cudaError_t launch_code_sweep(SweepArgs a, const SweepPlan& plan, int maxobs, float* Dsl, cudaStream_t s,
                               int* nlaunch);
+cudaError_t launch_sweep_split(const SweepArgs& a, const SweepPlan& plan, int maxobs, cudaStream_t s);
 // The residual x - D W rebuilt by the sweep's rebuild into a.R (through
 // a.pos) and its squares' sums per work unit into a.part_r2 (resident
 // dictionary only).

@@ -60,12 +60,13 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
     const uint32_t t_it = launch_t(a.t, a.t_dev, a.sc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int half = LANES == 1 ? 0 : (lane & 1);
-    const unsigned int units = (unsigned int)NW * LANES;   // 32-patch chunks, or 16-patch halves
+    // 32-patch chunks, or 16-patch halves; a split launch takes a range
+    const unsigned int units = a.unit_hi ? a.unit_hi : (unsigned int)NW * LANES;
     const uint32_t col0 = smem_addr(Ds) + 4u * kDictColumnOffset;   // atom 0's column, row 0
     CodeTally tl;
 
     for (;;) {
-        if (lane == 0) chunk_slot[warp] = atomicAdd(a.chunk_counter, 1u);
+        if (lane == 0) chunk_slot[warp] = a.unit_lo + atomicAdd(a.chunk_counter, 1u);
         __syncwarp();
         const unsigned int unit = chunk_slot[warp];
         __syncwarp();
@@ -128,8 +129,16 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
     flush_counts(a, lane, tl);
 }
 
+// Resident CTAs per SM the register budget is set for: 3 at kSplitObs
+// pixels (the light half of a split sweep), 2 up to 48, else 1.
 template <int MAXOBS, int LANES>
-__global__ void __launch_bounds__(kSweepThreads, (MAXOBS <= 48 && LANES == 1 ? 2 : 1)) sweep_kernel(const SweepArgs a)
+constexpr int sweep_min_ctas()
+{
+    return LANES == 1 ? (MAXOBS == kSplitObs ? 3 : (MAXOBS <= 48 ? 2 : 1)) : 1;
+}
+
+template <int MAXOBS, int LANES>
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_ctas<MAXOBS, LANES>()) sweep_kernel(const SweepArgs a)
 {
     sweep_body<MAXOBS, LANES>(a);
 }
@@ -323,6 +332,28 @@ cudaError_t launch_sweep(const SweepArgs& a, int maxobs, int grid, cudaStream_t 
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&a};
     return cudaLaunchKernel(fn, dim3(grid), dim3(kSweepThreads), args, (size_t)smem, s);
+}
+
+// The split sweep: units [0, split_units) on s with the kernel for maxobs,
+// the rest concurrently on plan.side with the kernel for kSplitObs pixels
+// (three CTAs per SM), forked from and joined to s by events.  The heavy
+// launch goes first so its few CTAs are resident before the light kernel
+// fills the GPU.
+cudaError_t launch_sweep_split(const SweepArgs& a, const SweepPlan& plan, int maxobs, cudaStream_t s)
+{
+    SweepArgs heavy = a, light = a;
+    heavy.unit_lo = 0;
+    heavy.unit_hi = plan.split_units;
+    light.unit_lo = plan.split_units;
+    light.unit_hi = (unsigned int)a.g.NW;
+    light.chunk_counter = plan.counter2;
+    cudaError_t e = cudaEventRecord(plan.fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(plan.side, plan.fork, 0);
+    if (e == cudaSuccess) e = launch_sweep(heavy, maxobs, plan.split_grid, s);
+    if (e == cudaSuccess) e = launch_sweep(light, kSplitObs, plan.light_grid, plan.side);
+    if (e == cudaSuccess) e = cudaEventRecord(plan.join, plan.side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan.join, 0);
+    return e;
 }
 
 cudaError_t launch_rebuild(const SweepArgs& a, int maxobs, int grid, cudaStream_t s)

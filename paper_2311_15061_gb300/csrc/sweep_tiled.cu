@@ -446,7 +446,10 @@ cudaError_t launch_code_sweep(SweepArgs a, const SweepPlan& plan, int maxobs, fl
     if (maxobs < 1) maxobs = 1;
     cudaError_t e;
     int n = 0;
-    if (plan.slice_atoms == 0) {
+    if (plan.slice_atoms == 0 && plan.split_units > 0) {
+        e = launch_sweep_split(a, plan, maxobs, s);
+        n = 2;
+    } else if (plan.slice_atoms == 0) {
         e = launch_sweep(a, maxobs, plan.grid, s);
         n = 1;
     } else {
