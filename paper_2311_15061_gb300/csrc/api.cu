@@ -104,8 +104,6 @@ struct sensai_ctx {
     int4* items = nullptr;      // work items: segments of the per-pixel patch lists
     long long n_items = 0;
     int gram_grid = 0;
-    CUtensorMap wmap;           // W for gram_kernel's record copies (set on first use)
-    bool wmap_set = false;
     float* Cpart = nullptr;     // [items][128][128]
     float* Ypart = nullptr;     // [items][128]
     double* C64 = nullptr;      // [P][128][128]
@@ -425,12 +423,7 @@ sensai_status run_gram(sensai_ctx* ctx, cudaStream_t s)
         ctx->launches += 1;
         ctx->xlist_valid = true;
     }
-    if (!ctx->wmap_set) {
-        SENSAI_CUDA(ctx, gram_weight_map(ctx->g, ctx->W, &ctx->wmap));
-        ctx->wmap_set = true;
-    }
     GramArgs a{};
-    a.wmap = ctx->wmap;
     a.g = ctx->g;
     a.W = ctx->W;
     a.Ilist = ctx->Ilist;

@@ -19,12 +19,12 @@
 // records of neighbouring patches (L2 reuse).  An item is cut into chunks of
 // 32 patches.  With w = h + l split into a TF32 head h (the top 19 bits, what
 // the tensor core reads) and an FP32 tail l, per 8 patches of a chunk two
-// tcgen05.mma kind::tf32 (M = N = 128 atoms, K = 8 patches, operands K-major
-// in shared memory) accumulate
-//   T += H H^T + H (2L)^T,
-// i.e. one product with the K dimension doubled, [H | H] [H | 2L]^T, into a
+// tcgen05.mma kind::tf32 (M = N = 128 atoms, K = 8 patches; A in tensor
+// memory, B = H K-major in shared memory) accumulate
+//   T' += H H^T + (2L) H^T,
+// i.e. one product with the K dimension doubled, [H | 2L] [H | H]^T, into a
 // 128-column tensor-memory accumulator.  Since H H^T is symmetric,
-// C = (T + T^T) / 2 = H H^T + H L^T + L H^T: the h h + h l + l h products,
+// C = (T' + T'^T) / 2 = H H^T + L H^T + H L^T: the h h + l h + h l products,
 // the dropped l l below 2^-20 relative (FP32-level).  With
 // SENSAI_FLAG_TF32_STATISTICS only H H^T is formed (TF32-level).
 // The tensor core's FP32 accumulation rounds toward minus infinity (each
@@ -35,22 +35,22 @@
 // nearest: a simulation of that arithmetic on the 128x128 K = 64 workload
 // gives <= 2e-6 relative on the drawn atoms.
 // Warp roles (320 threads, one CTA per SM):
-//  * warp 9, loader: per chunk, lane j copies patch j's whole weight record
-//    (KB blocks of 32 bytes, 8 MB apart in W) with one tensor copy
-//    (cp.async.bulk.tensor, a 3-D box over W), into one of five raw slots;
-//    the patch indices and frame values are loaded a chunk ahead and the
-//    frame values stored beside the slot; completion is the slot's mbarrier
-//    (the loader's arrival and the copies' bytes);
-//  * warps 0-3, converters: warp w takes chunks w, w + 4, ...: lane l reads
-//    atoms 4l .. 4l + 3 of every patch of the chunk (16-byte shared loads),
-//    splits them, writes H and 2L into one of four operand stages as
-//    16-byte stores (an 8-row group pitch of 272 bytes keeps them free of
-//    bank conflicts) and accumulates Y_p for its atoms in FP32;
-//  * warp 8, lane 0: issues the MMAs (a wait per chunk, 8 MMAs, a commit)
-//    into two accumulators in turn, one per group of 4 chunks;
+//  * warp 9, loader: per chunk, the 32 patch indices and frame values
+//    (loaded a chunk ahead) into one slot of an 8-slot shared ring;
+//  * warps 0-3, converters: every chunk, warp q the 32 atoms of TMEM lane
+//    quarter q: lane l (atom 32 q + l) loads its weight of each of the 32
+//    patches straight from W, a chunk ahead of their use (8 lanes read one
+//    32-byte record block: 4 full sectors per warp instruction), splits
+//    them into h and l, writes its row of A = [H | 2L] into tensor memory
+//    (tcgen05.st) and its row of B = H into one of two shared-memory stages
+//    (K-major, no swizzle; an 8-row group pitch of 272 bytes), and
+//    accumulates Y_p for its atom in FP32;
+//  * warp 8, lane 0: issues the MMAs (a wait per chunk, 8 MMAs with A in
+//    tensor memory, a commit) into two accumulators in turn, one per group
+//    of 4 chunks;
 //  * warps 4-7, epilogue: warp w reads TMEM lanes 32 (w % 4) .., i.e. the
 //    rows of 32 atoms, adds each group's accumulator into running sums kept
-//    in tensor memory and frees it; at the end of an item it writes T^T
+//    in tensor memory and frees it; at the end of an item it writes T'^T
 //    (coalesced) as the item's FP32 partial.
 // Every wait is bounded; a timeout sets SENSAI_ETIMEOUT in the status word,
 // every role stops (each warp's decision is its lane 0's, broadcast), the
@@ -74,11 +74,11 @@ constexpr int kGEpilogue0 = 4;                  // warps 4-7
 constexpr int kGMmaWarp = 8;
 constexpr int kGLoaderWarp = 9;
 constexpr int kGThreads = 32 * (kGLoaderWarp + 1);
-constexpr int kGRawSlots = 8;                   // raw record ring (TMA destination)
+constexpr int kGRawSlots = 8;                   // ring of the chunks' patch indices and frame values
 constexpr int kGStages = 2;                     // operand stages (A in TMEM, B in shared memory)
 constexpr int kGGroup = 4;                      // chunks per accumulator drain
 constexpr int kGSegment = 2048;                 // most patches of an item
-constexpr int kGRawFloats = kGChunk * kGAtoms;  // one chunk's records [32 patches][128 atoms]
+constexpr int kGRingWords = 2 * kGChunk;        // one chunk's patch indices, then its frame values
 constexpr int kGSboBytes = 272;                 // 8-row group pitch (256 B of data + 16 B)
 constexpr int kGOpFloats = (kGAtoms / 8) * kGSboBytes / 4;   // one 128 x 8 operand: 1088 floats
 constexpr int kGStageFloats = (kGChunk / kGStep) * kGOpFloats;   // B = H of a chunk: 4 operands
@@ -152,25 +152,6 @@ __device__ __forceinline__ bool gm_wait(uint64_t* bar, uint32_t parity)
         ns = ns < kGSleepCapNs ? 2 * ns : kGSleepCapNs;
     }
     return false;
-}
-
-// Arrival that also expects tx more bytes of asynchronous copies.
-__device__ __forceinline__ void gm_arrive_tx(uint64_t* bar, uint32_t tx)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(gm_smem(bar)), "r"(tx) : "memory");
-}
-
-// One patch's weight record by the tensor-memory-access unit: the box
-// (8 floats, 1 patch, KB atom blocks) of the map over W [KB][Npad][8] at
-// patch i, into 512 contiguous bytes (atoms in order); completion counted
-// in bytes on bar.
-__device__ __forceinline__ void gm_tma_record(float* dst, const CUtensorMap* map, int i, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(gm_smem(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(i), "r"(0), "r"(gm_smem(bar))
-        : "memory");
 }
 
 __device__ __forceinline__ void gm_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
@@ -250,6 +231,18 @@ __device__ __forceinline__ void gm_st32(uint32_t taddr, const float (&v)[32])
         : "memory");
 }
 
+__device__ __forceinline__ void gm_st16(uint32_t taddr, const float* v)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
 __device__ __forceinline__ void gm_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ int gm_chunks(int cnt) { return (cnt + kGChunk - 1) / kGChunk; }
@@ -286,8 +279,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
     extern __shared__ __align__(1024) float gsm[];
     __shared__ __align__(8) uint64_t full_bar[kGStages];     // stage written (a converter warp)
     __shared__ __align__(8) uint64_t empty_bar[kGStages];    // stage read (the MMA commit)
-    __shared__ __align__(8) uint64_t raw_full[kGRawSlots];   // raw slot landed (loader arrival + TMA bytes)
-    __shared__ __align__(8) uint64_t raw_empty[kGRawSlots];  // raw slot read (a converter warp)
+    __shared__ __align__(8) uint64_t raw_full[kGRawSlots];   // ring slot written (the loader)
+    __shared__ __align__(8) uint64_t raw_empty[kGRawSlots];  // ring slot read (every converter warp)
     __shared__ __align__(8) uint64_t accf_bar[2];          // a group's MMAs complete
     __shared__ __align__(8) uint64_t acce_bar[2];          // a group's accumulator drained
     __shared__ __align__(8) uint64_t done_bar;
@@ -299,8 +292,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     // 1024-byte aligned whatever the dynamic segment's base (tensor copies
     // and the MMA operands want aligned shared addresses)
     float* stages = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~(uintptr_t)1023);
-    float* raw = stages + kGStages * kGStageFloats;        // [kGRawSlots][kGRawFloats]
-    float* rawx = raw + kGRawSlots * kGRawFloats;          // [kGRawSlots][kGChunk] frame values
+    float* ring = stages + kGStages * kGStageFloats;       // [kGRawSlots][kGRingWords]
 
     if (tid == 0) {
         abort_s = 0;
@@ -309,7 +301,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
             gm_bar_init(&empty_bar[s], 1);             // the MMA commit
         }
         for (int r = 0; r < kGRawSlots; ++r) {
-            gm_bar_init(&raw_full[r], 1);              // the loader (and the copies' bytes)
+            gm_bar_init(&raw_full[r], 1);              // the loader
             gm_bar_init(&raw_empty[r], kGConverters);
         }
         for (int b = 0; b < 2; ++b) {
@@ -349,52 +341,78 @@ __global__ void __launch_bounds__(kGThreads, 1)
     if (warp < kGConverters) {
         // ----------------------------------------------------- converters --
         // warp q, every chunk: lane l holds atom a = 32 q + l of the chunk's
-        // 32 patches; writes its row of the A operands H and 2L into tensor
+        // 32 patches, loaded from W one chunk ahead (one 4-byte load per
+        // patch: 8 lanes read a 32-byte record block, 4 full sectors per
+        // instruction); writes its row of the A operands H and 2L into tensor
         // memory (TMEM lane a, one column per patch) and its row of B = H
         // into the chunk's shared-memory stage, and accumulates Y_pa
         const int q = warp;
         const int atom = 32 * q + lane;
         const bool live = atom < K;
+        const float* wcol = a.W + (long long)(atom >> 3) * Npad * kAtomBlock + (atom & 7);
         // float offset of (row atom, patches 4 c4 .. + 3) in a 128 x 8 operand
         const int b_base = (atom >> 3) * (kGSboBytes / 4) + (atom & 7) * 4;
         const uint32_t tm_lanes = tmem + ((uint32_t)(32 * q) << 16);
         float y = 0.0f;
         bool ok = true;
+        float pre[kGChunk];   // the next chunk's weights of this lane's atom
+        // issues the loads of chunk c (its ring slot is waited for first)
+        auto fetch = [&](const ChunkWalk& c) {
+            const int rs = (int)(c.u % kGRawSlots);
+            ok = warp_wait(&raw_full[rs], (uint32_t)((c.u / kGRawSlots) & 1));
+            if (!ok) return;
+            const int* ri = reinterpret_cast<const int*>(ring + rs * kGRingWords);
+            const int nv = min(kGChunk, a.items[c.it].z - c.c * kGChunk);
+#pragma unroll
+            for (int j = 0; j < kGChunk; ++j)
+                pre[j] = (j < nv && live) ? __ldg(wcol + (long long)ri[j] * kAtomBlock) : 0.0f;
+        };
+        if (wk.valid(a)) fetch(wk);
         for (; wk.valid(a) && ok; wk.next(a)) {
-            const int cnt = a.items[wk.it].z;
-            const int nvalid = min(kGChunk, cnt - wk.c * kGChunk);
+            const int nvalid = min(kGChunk, a.items[wk.it].z - wk.c * kGChunk);
             const int rs = (int)(wk.u % kGRawSlots);
             const int st = (int)(wk.u % kGStages);
-            if (!(ok = warp_wait(&raw_full[rs], (uint32_t)((wk.u / kGRawSlots) & 1)))) break;
+            float cur[kGChunk];
+#pragma unroll
+            for (int j = 0; j < kGChunk; ++j) cur[j] = pre[j];
+            const float* rx = ring + rs * kGRingWords + kGChunk;
+#pragma unroll
+            for (int j = 0; j < kGChunk; ++j) y = fmaf(cur[j], j < nvalid ? rx[j] : 0.0f, y);
+            __syncwarp();
+            if (lane == 0) gm_arrive(&raw_empty[rs]);   // indices and frame values read
+            {
+                ChunkWalk nx = wk;
+                nx.next(a);
+                if (nx.valid(a)) fetch(nx);   // in flight during this chunk's conversion
+                if (!ok) break;
+            }
             if (!(ok = warp_wait(&empty_bar[st], (uint32_t)(((wk.u / kGStages) & 1) ^ 1)))) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const float* rw = raw + (size_t)rs * kGRawFloats;
-            const float* rx = rawx + rs * kGChunk;
-            float h[kGChunk], l2[kGChunk];
-#pragma unroll
-            for (int j = 0; j < kGChunk; ++j) {
-                const bool pv = j < nvalid;
-                const float w = (pv && live) ? rw[j * kGAtoms + atom] : 0.0f;
-                y = fmaf(w, pv ? rx[j] : 0.0f, y);
-                h[j] = gm_head(w);
-                l2[j] = 2.0f * (w - h[j]);   // exact: h is w truncated, doubling is exact
-            }
             const uint32_t acol = (uint32_t)(kGACol0 + st * kGAStageCols);
-            gm_st32(tm_lanes + acol, h);
-            if (split) gm_st32(tm_lanes + acol + kGChunk, l2);
             float* stg = stages + (size_t)st * kGStageFloats;
 #pragma unroll
-            for (int c4 = 0; c4 < kGChunk / 4; ++c4)   // operand c4 / 2, patch quad c4 % 2
-                *reinterpret_cast<float4*>(stg + (c4 >> 1) * kGOpFloats + b_base + (c4 & 1) * 32) =
-                    make_float4(h[4 * c4], h[4 * c4 + 1], h[4 * c4 + 2], h[4 * c4 + 3]);
+            for (int hf = 0; hf < 2; ++hf) {   // patches 16 hf .. 16 hf + 15
+                float h[16], l2[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float w = cur[16 * hf + j];
+                    h[j] = gm_head(w);
+                    l2[j] = 2.0f * (w - h[j]);   // exact: h is w truncated, doubling is exact
+                }
+                gm_st16(tm_lanes + acol + (uint32_t)(16 * hf), h);
+                if (split) gm_st16(tm_lanes + acol + (uint32_t)(kGChunk + 16 * hf), l2);
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {   // patch quad 4 hf + c4: operand (4 hf + c4) / 2
+                    const int qd = 4 * hf + c4;
+                    *reinterpret_cast<float4*>(stg + (qd >> 1) * kGOpFloats + b_base + (qd & 1) * 32) =
+                        make_float4(h[4 * c4], h[4 * c4 + 1], h[4 * c4 + 2], h[4 * c4 + 3]);
+                }
+            }
             gm_st_wait();
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) {
-                gm_arrive(&raw_empty[rs]);
-                gm_arrive(&full_bar[st]);
-            }
+            if (lane == 0) gm_arrive(&full_bar[st]);
             if (wk.c == wk.nch - 1) {
                 // the end of an item: Y_p for this warp's 32 atoms
                 a.Ypart[(size_t)wk.it * kGAtoms + atom] = y;
@@ -403,9 +421,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
         }
     } else if (warp == kGLoaderWarp) {
         // ---------------------------------------------------------- loader --
-        // per chunk: lane j fetches patch j's record with one tensor copy;
-        // the patch indices and frame values are loaded a chunk ahead
-        const uint32_t rec_bytes = (uint32_t)a.g.KB * kAtomBlock * sizeof(float);
+        // per chunk: the 32 patch indices and frame values (loaded a chunk
+        // ahead) into one ring slot
         int idx = 0;
         float xv = 0.0f;
         auto load_lane = [&](const ChunkWalk& c, int& i_out, float& x_out) {
@@ -421,38 +438,21 @@ __global__ void __launch_bounds__(kGThreads, 1)
         };
         ChunkWalk cur = wk;
         load_lane(cur, idx, xv);
-        long long last_u[kGRawSlots];   // the last chunk copied into each slot
-#pragma unroll
-        for (int r = 0; r < kGRawSlots; ++r) last_u[r] = -1;
         while (cur.valid(a)) {
             ChunkWalk nxt = cur;
             nxt.next(a);
             int idx_n;
             float xv_n;
             load_lane(nxt, idx_n, xv_n);
-            const int cnt = a.items[cur.it].z;
-            const int nvalid = min(kGChunk, cnt - cur.c * kGChunk);
             const int rs = (int)(cur.u % kGRawSlots);
             if (!warp_wait(&raw_empty[rs], (uint32_t)(((cur.u / kGRawSlots) & 1) ^ 1))) break;
-            if (lane < nvalid) rawx[rs * kGChunk + lane] = xv;
+            reinterpret_cast<int*>(ring + rs * kGRingWords)[lane] = idx;
+            ring[rs * kGRingWords + kGChunk + lane] = xv;
             __syncwarp();
-            if (lane == 0) gm_arrive_tx(&raw_full[rs], (uint32_t)nvalid * rec_bytes);
-            __syncwarp();
-            if (lane < nvalid) gm_tma_record(raw + (size_t)rs * kGRawFloats + lane * kGAtoms, &a.wmap, idx, &raw_full[rs]);
-#pragma unroll
-            for (int r = 0; r < kGRawSlots; ++r)
-                if (r == rs) last_u[r] = cur.u;
+            if (lane == 0) gm_arrive(&raw_full[rs]);
             cur = nxt;
             idx = idx_n;
             xv = xv_n;
-        }
-        // no copy may still be writing shared memory when the CTA ends (the
-        // converters have consumed every slot unless a wait gave up)
-        if (lane == 0) {
-#pragma unroll
-            for (int r = 0; r < kGRawSlots; ++r)
-                if (last_u[r] >= 0 && !gm_wait(&raw_full[r], (uint32_t)((last_u[r] / kGRawSlots) & 1)))
-                    atomicExch(a.status, (int)SENSAI_ETIMEOUT);
         }
     } else if (warp == kGMmaWarp) {
         // ---------------------------------------------------- MMA issuer --
@@ -687,7 +687,7 @@ void gram_plan_items(const std::vector<int>& Rbase, int P, int seg, std::vector<
 
 size_t gram_smem_bytes()
 {
-    return 1024 + sizeof(float) * ((size_t)kGStages * kGStageFloats + (size_t)kGRawSlots * (kGRawFloats + kGChunk));
+    return 1024 + sizeof(float) * ((size_t)kGStages * kGStageFloats + (size_t)kGRawSlots * kGRingWords);
 }
 
 // Xlist[e] = x[origin(Ilist[e]) + imgoff[p]] for the entries of pixel p.
@@ -724,27 +724,6 @@ cudaError_t launch_gram(const GramArgs& a, int grid, cudaStream_t s)
     if (e != cudaSuccess) return e;
     gram_draw_kernel<<<a.g.P, kGAtoms, dsmem, s>>>(a);
     return cudaGetLastError();
-}
-
-cudaError_t gram_weight_map(const Geom& g, const float* W, CUtensorMap* map)
-{
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess) return e;
-    if (!fn || q != cudaDriverEntryPointSuccess) return cudaErrorNotSupported;
-    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-    const cuuint64_t dims[3] = {(cuuint64_t)kAtomBlock, (cuuint64_t)g.Npad, (cuuint64_t)g.KB};
-    const cuuint64_t strides[2] = {(cuuint64_t)kAtomBlock * sizeof(float), (cuuint64_t)g.Npad * kAtomBlock * sizeof(float)};
-    const cuuint32_t box[3] = {(cuuint32_t)kAtomBlock, 1u, (cuuint32_t)g.KB};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
-    const CUresult r = reinterpret_cast<Encode>(fn)(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(W), dims,
-                                                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 bool gram_available(const Geom& g) { return g.K >= 1 && g.K <= kGAtoms; }

@@ -7,7 +7,6 @@
 // with the U^(1/alpha) boost below shape 1, Beta as a ratio of Gammas.
 #pragma once
 
-#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -418,7 +417,6 @@ struct DictSpaceArgs {
 
 // The dictionary step in its dense-statistics form (gram.cu).
 struct GramArgs {
-    CUtensorMap wmap;          // W as a 3-D tensor (8 floats, Npad patches, KB blocks) for one-record copies
     Geom g;
     const float* W;            // [KB][Npad][8]
     const int* Ilist;          // per pixel p: the patches observing p (Rbase layout)
@@ -622,9 +620,7 @@ void gram_plan_items(const std::vector<int>& Rbase, int P, int seg, std::vector<
                      std::vector<int>* pitem_start, std::vector<int>* pitem_idx);
 cudaError_t launch_xlist(const Geom& g, const int* Ilist, const int* Rbase, int max_slots, const int* imgoff,
                          const float* x, float* Xlist, cudaStream_t s);
-cudaError_t launch_gram(const GramArgs& a, int grid, cudaStream_t s);
-// The tensor map of W for gram_kernel's record copies (box: one patch's KB blocks).
-cudaError_t gram_weight_map(const Geom& g, const float* W, CUtensorMap* map);   // statistics, then the draws
+cudaError_t launch_gram(const GramArgs& a, int grid, cudaStream_t s);   // statistics, then the draws
 cudaError_t launch_geometry(const Geom& g, const uint8_t* mask_bytes, uint32_t* mask_bits, int* imgoff,
                             uint16_t* nobs, int* maxobs, unsigned long long* total, cudaStream_t s);
 cudaError_t launch_fill_obs(const Geom& g, const uint32_t* mask_bits, const int* imgoff, uint16_t* obs, cudaStream_t s);
