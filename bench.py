@@ -300,6 +300,8 @@ def run_gpu(args):
         line["video3d"] = run_video3d()
     if not args.no_batch:
         line["batch64"] = run_batch64()
+    if not args.no_precision and world == 1:
+        line["precision"] = run_precision()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     ctx.close()
@@ -544,6 +546,64 @@ def run_video3d(cfg=VIDEO):
     return res
 
 
+PRECISION_ITERS = 50
+
+
+def run_precision():
+    """The dictionary draw's three forms on the 512x512, K = 128 workload:
+    the residual form (FP32, the default), the dense-statistics form with
+    FP32-level Grams (TF32 head/tail split on the tensor cores) and with
+    TF32-level Grams.  Per form: the dictionary phase and whole iteration
+    times over 50 Gibbs iterations from the prior, the PSNR of the final
+    reconstruction, and -- from one shared state (the residual form's after
+    10 iterations) -- the largest per-atom relative difference of one
+    dictionary draw from the residual form's draw.  The errors against the
+    FP64 oracle are measured by the parity tests."""
+    import torch
+    from paper_2311_15061_gb300 import sensai
+    x, clean, mask = _frame()
+    w = WORKLOAD
+    stream = torch.cuda.current_stream()
+    frame = torch.from_numpy(x).cuda()
+    forms = {"residual_fp32": 0, "dense_fp32_split": sensai.SENSAI_FLAG_DENSE_STATISTICS,
+             "dense_tf32": sensai.SENSAI_FLAG_TF32_STATISTICS}
+    ref = sensai.Context(sensai.make_params(w["M"], w["B"], w["S"], w["K"], seed=w["seed"]), mask)
+    ref.sensai_learn(x, 10)
+    state = ref.sensai_get_state()
+    ref.sensai_draw_dictionary()
+    d_ref = ref.sensai_get_dictionary().astype(np.float64)
+    ref.close()
+    res = {"workload": WORKLOAD_NAME, "iterations": PRECISION_ITERS, "forms": {}}
+    for name, flags in forms.items():
+        ctx = sensai.Context(sensai.make_params(w["M"], w["B"], w["S"], w["K"], seed=w["seed"], flags=flags), mask)
+        ctx.sensai_set_frame(frame, stream)
+        ctx.sensai_learn(None, 3, stream)   # warm-up
+        ctx.sensai_reset(stream)
+        torch.cuda.synchronize()
+        ctx.sensai_profile(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.sensai_learn(None, PRECISION_ITERS, stream)
+        e1.record(stream)
+        out = ctx.sensai_reconstruct()
+        torch.cuda.synchronize()
+        prof = ctx.sensai_profile_read()
+        ctx.sensai_profile(0)
+        psnr = float(10 * np.log10(1.0 / np.mean((out.astype(np.float64) - clean) ** 2)))
+        ctx.sensai_set_state(**state)
+        ctx.sensai_draw_dictionary()
+        d = ctx.sensai_get_dictionary().astype(np.float64)
+        diff = np.linalg.norm(d - d_ref, axis=1) / np.maximum(np.linalg.norm(d_ref, axis=1), 1e-30)
+        res["forms"][name] = {
+            "ms_per_iteration": e0.elapsed_time(e1) / PRECISION_ITERS,
+            "dictionary_ms_per_iteration": prof["dictionary"][0] / PRECISION_ITERS,
+            "psnr_db_vs_clean": psnr,
+            "dictionary_draw_max_rel_diff_vs_residual_fp32": float(diff.max()),
+        }
+        ctx.close()
+    return res
+
+
 BATCH = dict(sizes=(64, 96, 128, 192, 256, 384, 512), per_size=8, cubes=8, cube_shape=(128, 128, 512),
              cube_B=(4, 4, 32), cube_S=(1, 1, 32), Ks=(64, 128, 256), frac2d=(0.05, 0.30),
              frac_cube=(0.05, 0.30), iters=20, seed=11)
@@ -693,6 +753,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the live-serving measurement")
     ap.add_argument("--no-video", action="store_true", help="skip the 3-D video measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances measurement")
+    ap.add_argument("--no-precision", action="store_true", help="skip the dictionary-form comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

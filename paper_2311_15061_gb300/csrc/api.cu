@@ -105,7 +105,7 @@ struct sensai_ctx {
     long long n_items = 0;
     int gram_grid = 0;
     float* Cpart = nullptr;     // [items][128][128]
-    float* Ypart = nullptr;     // [items][128]
+    float* Ypart = nullptr;     // [items][2][128]
     double* C64 = nullptr;      // [P][128][128]
     double* Y64 = nullptr;      // [P][128]
     int* pitem_start = nullptr; // [P + 1]
@@ -735,7 +735,7 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
         CREATE_CUDA(dalloc(&ctx->pitem_start, ps.size()));
         CREATE_CUDA(dalloc(&ctx->pitem_idx, pi.size()));
         CREATE_CUDA(dalloc(&ctx->Cpart, items.size() * 128 * 128));
-        CREATE_CUDA(dalloc(&ctx->Ypart, items.size() * 128));
+        CREATE_CUDA(dalloc(&ctx->Ypart, items.size() * 2 * 128));
         CREATE_CUDA(dalloc(&ctx->C64, (size_t)P * 128 * 128));
         CREATE_CUDA(dalloc(&ctx->Y64, (size_t)P * 128));
         CREATE_CUDA(cudaMemcpy(ctx->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));

@@ -34,21 +34,21 @@
 // patches) into running sums, added in FP32 round-to-
 // nearest: a simulation of that arithmetic on the 128x128 K = 64 workload
 // gives <= 2e-6 relative on the drawn atoms.
-// Warp roles (320 threads, one CTA per SM):
-//  * warp 9, loader: per chunk, the 32 patch indices and frame values
+// Warp roles (448 threads, one CTA per SM):
+//  * warp 13, loader: per chunk, the 32 patch indices and frame values
 //    (loaded a chunk ahead) into one slot of an 8-slot shared ring;
-//  * warps 0-3, converters: every chunk, warp q the 32 atoms of TMEM lane
-//    quarter q: lane l (atom 32 q + l) loads its weight of each of the 32
-//    patches straight from W, a chunk ahead of their use (8 lanes read one
-//    32-byte record block: 4 full sectors per warp instruction), splits
-//    them into h and l, writes its row of A = [H | 2L] into tensor memory
-//    (tcgen05.st) and its row of B = H into one of two shared-memory stages
-//    (K-major, no swizzle; an 8-row group pitch of 272 bytes), and
-//    accumulates Y_p for its atom in FP32;
-//  * warp 8, lane 0: issues the MMAs (a wait per chunk, 8 MMAs with A in
+//  * warps 0-7, converters: every chunk, warp w the 32 atoms of TMEM lane
+//    quarter w % 4 and the patches 16 (w / 4) .. + 15: lane l (atom
+//    32 (w % 4) + l) loads its weight of each patch straight from W, a chunk
+//    ahead of use (8 lanes read one 32-byte record block: 4 full sectors
+//    per warp instruction), splits it into h and l, writes its row of
+//    A = [H | 2L] into tensor memory (tcgen05.st) and its row of B = H into
+//    one of two shared-memory stages (K-major, no swizzle; an 8-row group
+//    pitch of 272 bytes), and accumulates Y_p for its atom in FP32;
+//  * warp 12, lane 0: issues the MMAs (a wait per chunk, 8 MMAs with A in
 //    tensor memory, a commit) into two accumulators in turn, one per group
 //    of 4 chunks;
-//  * warps 4-7, epilogue: warp w reads TMEM lanes 32 (w % 4) .., i.e. the
+//  * warps 8-11, epilogue: warp w reads TMEM lanes 32 (w % 4) .., i.e. the
 //    rows of 32 atoms, adds each group's accumulator into running sums kept
 //    in tensor memory and frees it; at the end of an item it writes T'^T
 //    (coalesced) as the item's FP32 partial.
@@ -69,10 +69,11 @@ namespace sensai {
 constexpr int kGAtoms = 128;                    // M = N: atoms, K padded to 128
 constexpr int kGStep = 8;                       // patches per MMA (tf32 K)
 constexpr int kGChunk = 32;                     // patches per chunk (4 MMA steps)
-constexpr int kGConverters = 4;                 // warps 0-3
-constexpr int kGEpilogue0 = 4;                  // warps 4-7
-constexpr int kGMmaWarp = 8;
-constexpr int kGLoaderWarp = 9;
+constexpr int kGConverters = 8;                 // warps 0-7: lane quarter w % 4, patch half w / 4
+constexpr int kGHalf = 16;                      // patches per converter warp and chunk
+constexpr int kGEpilogue0 = 8;                  // warps 8-11
+constexpr int kGMmaWarp = 12;
+constexpr int kGLoaderWarp = 13;
 constexpr int kGThreads = 32 * (kGLoaderWarp + 1);
 constexpr int kGRawSlots = 8;                   // ring of the chunks' patch indices and frame values
 constexpr int kGStages = 2;                     // operand stages (A in TMEM, B in shared memory)
@@ -91,7 +92,7 @@ constexpr long long kGSpins = 1LL << 22;
 
 // Every converter warp takes part in every chunk (its quarter of the atoms),
 // so each waits on every phase of every barrier in order.
-static_assert(kGConverters == 4, "converter warp q writes TMEM lane quarter q");
+static_assert(kGConverters == 8 && kGEpilogue0 % 4 == 0, "warp w accesses TMEM lane quarter w % 4");
 
 
 __device__ __forceinline__ uint32_t gm_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -340,13 +341,14 @@ __global__ void __launch_bounds__(kGThreads, 1)
     wk.start(a);
     if (warp < kGConverters) {
         // ----------------------------------------------------- converters --
-        // warp q, every chunk: lane l holds atom a = 32 q + l of the chunk's
-        // 32 patches, loaded from W one chunk ahead (one 4-byte load per
-        // patch: 8 lanes read a 32-byte record block, 4 full sectors per
-        // instruction); writes its row of the A operands H and 2L into tensor
-        // memory (TMEM lane a, one column per patch) and its row of B = H
-        // into the chunk's shared-memory stage, and accumulates Y_pa
-        const int q = warp;
+        // warp w, every chunk: lane l holds atom a = 32 (w % 4) + l of the
+        // chunk's patches 16 (w / 4) .. + 15, loaded from W one chunk ahead
+        // (one 4-byte load per patch: 8 lanes read a 32-byte record block, 4
+        // full sectors per instruction); writes its row of the A operands H
+        // and 2L into tensor memory (TMEM lane a, one column per patch) and
+        // its row of B = H into the chunk's shared-memory stage, and
+        // accumulates Y_pa over its patches
+        const int q = warp & 3, hf = warp >> 2;
         const int atom = 32 * q + lane;
         const bool live = atom < K;
         const float* wcol = a.W + (long long)(atom >> 3) * Npad * kAtomBlock + (atom & 7);
@@ -355,29 +357,29 @@ __global__ void __launch_bounds__(kGThreads, 1)
         const uint32_t tm_lanes = tmem + ((uint32_t)(32 * q) << 16);
         float y = 0.0f;
         bool ok = true;
-        float pre[kGChunk];   // the next chunk's weights of this lane's atom
+        float pre[kGHalf];   // the next chunk's weights of this lane's atom
         // issues the loads of chunk c (its ring slot is waited for first)
         auto fetch = [&](const ChunkWalk& c) {
             const int rs = (int)(c.u % kGRawSlots);
             ok = warp_wait(&raw_full[rs], (uint32_t)((c.u / kGRawSlots) & 1));
             if (!ok) return;
-            const int* ri = reinterpret_cast<const int*>(ring + rs * kGRingWords);
-            const int nv = min(kGChunk, a.items[c.it].z - c.c * kGChunk);
+            const int* ri = reinterpret_cast<const int*>(ring + rs * kGRingWords) + kGHalf * hf;
+            const int nv = min(kGChunk, a.items[c.it].z - c.c * kGChunk) - kGHalf * hf;
 #pragma unroll
-            for (int j = 0; j < kGChunk; ++j)
+            for (int j = 0; j < kGHalf; ++j)
                 pre[j] = (j < nv && live) ? __ldg(wcol + (long long)ri[j] * kAtomBlock) : 0.0f;
         };
         if (wk.valid(a)) fetch(wk);
         for (; wk.valid(a) && ok; wk.next(a)) {
-            const int nvalid = min(kGChunk, a.items[wk.it].z - wk.c * kGChunk);
+            const int nvalid = min(kGChunk, a.items[wk.it].z - wk.c * kGChunk) - kGHalf * hf;
             const int rs = (int)(wk.u % kGRawSlots);
             const int st = (int)(wk.u % kGStages);
-            float cur[kGChunk];
+            float cur[kGHalf];
 #pragma unroll
-            for (int j = 0; j < kGChunk; ++j) cur[j] = pre[j];
-            const float* rx = ring + rs * kGRingWords + kGChunk;
+            for (int j = 0; j < kGHalf; ++j) cur[j] = pre[j];
+            const float* rx = ring + rs * kGRingWords + kGChunk + kGHalf * hf;
 #pragma unroll
-            for (int j = 0; j < kGChunk; ++j) y = fmaf(cur[j], j < nvalid ? rx[j] : 0.0f, y);
+            for (int j = 0; j < kGHalf; ++j) y = fmaf(cur[j], j < nvalid ? rx[j] : 0.0f, y);
             __syncwarp();
             if (lane == 0) gm_arrive(&raw_empty[rs]);   // indices and frame values read
             {
@@ -388,25 +390,21 @@ __global__ void __launch_bounds__(kGThreads, 1)
             }
             if (!(ok = warp_wait(&empty_bar[st], (uint32_t)(((wk.u / kGStages) & 1) ^ 1)))) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t acol = (uint32_t)(kGACol0 + st * kGAStageCols);
+            const uint32_t acol = (uint32_t)(kGACol0 + st * kGAStageCols + kGHalf * hf);
             float* stg = stages + (size_t)st * kGStageFloats;
+            float h[kGHalf], l2[kGHalf];
 #pragma unroll
-            for (int hf = 0; hf < 2; ++hf) {   // patches 16 hf .. 16 hf + 15
-                float h[16], l2[16];
+            for (int j = 0; j < kGHalf; ++j) {
+                h[j] = gm_head(cur[j]);
+                l2[j] = 2.0f * (cur[j] - h[j]);   // exact: h is w truncated, doubling is exact
+            }
+            gm_st16(tm_lanes + acol, h);
+            if (split) gm_st16(tm_lanes + acol + kGChunk, l2);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float w = cur[16 * hf + j];
-                    h[j] = gm_head(w);
-                    l2[j] = 2.0f * (w - h[j]);   // exact: h is w truncated, doubling is exact
-                }
-                gm_st16(tm_lanes + acol + (uint32_t)(16 * hf), h);
-                if (split) gm_st16(tm_lanes + acol + (uint32_t)(kGChunk + 16 * hf), l2);
-#pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {   // patch quad 4 hf + c4: operand (4 hf + c4) / 2
-                    const int qd = 4 * hf + c4;
-                    *reinterpret_cast<float4*>(stg + (qd >> 1) * kGOpFloats + b_base + (qd & 1) * 32) =
-                        make_float4(h[4 * c4], h[4 * c4 + 1], h[4 * c4 + 2], h[4 * c4 + 3]);
-                }
+            for (int c4 = 0; c4 < kGHalf / 4; ++c4) {   // patch quad 4 hf + c4: operand (4 hf + c4) / 2
+                const int qd = 4 * hf + c4;
+                *reinterpret_cast<float4*>(stg + (qd >> 1) * kGOpFloats + b_base + (qd & 1) * 32) =
+                    make_float4(h[4 * c4], h[4 * c4 + 1], h[4 * c4 + 2], h[4 * c4 + 3]);
             }
             gm_st_wait();
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -414,8 +412,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
             __syncwarp();
             if (lane == 0) gm_arrive(&full_bar[st]);
             if (wk.c == wk.nch - 1) {
-                // the end of an item: Y_p for this warp's 32 atoms
-                a.Ypart[(size_t)wk.it * kGAtoms + atom] = y;
+                // the end of an item: this warp's share of Y_p for its atom
+                a.Ypart[((size_t)wk.it * 2 + hf) * kGAtoms + atom] = y;
                 y = 0.0f;
             }
         }
@@ -596,7 +594,8 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(GramArgs a)
         for (int jj = i0; jj < i1; ++jj) {
             const size_t it = (size_t)a.pitem_idx[jj];
 #pragma unroll
-            gm_sum2(ys, yc, a.Ypart[it * kGAtoms + t]);
+            gm_sum2(ys, yc, a.Ypart[(it * 2 + 0) * kGAtoms + t]);
+            gm_sum2(ys, yc, a.Ypart[(it * 2 + 1) * kGAtoms + t]);
         }
         a.Y64[(size_t)p * kGAtoms + t] = (double)ys + (double)yc;
     }

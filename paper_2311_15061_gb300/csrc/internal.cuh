@@ -424,7 +424,7 @@ struct GramArgs {
     const int4* items;         // (p, first entry, entries, -): segments of the per-pixel lists
     long long n_items;
     float* Cpart;              // [items][128][128] per-item partials T^T, C = (T + T^T) / 2 (FP32)
-    float* Ypart;              // [items][128] per-item correlation partials (FP32)
+    float* Ypart;              // [items][2][128] per-item correlation partials (FP32), one per patch half
     double* C64;               // [P][128][128] FP64 sums of the partials (symmetrised by the draws)
     double* Y64;               // [P][128] Y_p
     const int* pitem_start;    // [P + 1] pixel p's items: pitem_idx[pitem_start[p] ..]
