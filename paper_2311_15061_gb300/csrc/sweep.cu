@@ -248,6 +248,7 @@ static void* select_kernel(int maxobs, int multi = 0)
         return nullptr;
     }
     if (maxobs <= 8) return kernel_ptr<8>(multi);
+    if (maxobs <= 12) return kernel_ptr<12>(multi);
     if (maxobs <= 16) return kernel_ptr<16>(multi);
     if (maxobs <= 24) return kernel_ptr<24>(multi);
     if (maxobs <= 32) return kernel_ptr<32>(multi);
@@ -262,7 +263,7 @@ static void* select_kernel(int maxobs, int multi = 0)
 // Variant key: equal keys run the same kernel template.
 int sweep_variant(int maxobs)
 {
-    const int caps[] = {8, 16, 24, 32, 40, 48, 64, 72, 80, 96, 128, 192, 224, 256};
+    const int caps[] = {8, 12, 16, 24, 32, 40, 48, 64, 72, 80, 96, 128, 192, 224, 256};
     for (int c : caps)
         if (maxobs <= c) return c;
     return 0;
@@ -293,7 +294,7 @@ int sweep_multi_ctas_per_sm(int maxobs, size_t smem)
 // variant would otherwise pay for it (a latency spike when serving).
 cudaError_t preload_sweep_variants()
 {
-    const int obs[] = {8, 16, 24, 32, 40, 48, 64, 72, 80, 96, 128, 192, 224, 256};
+    const int obs[] = {8, 12, 16, 24, 32, 40, 48, 64, 72, 80, 96, 128, 192, 224, 256};
     for (int m : obs) {
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, select_kernel(m));
