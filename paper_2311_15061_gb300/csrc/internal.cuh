@@ -554,7 +554,7 @@ struct SweepPlan {
     cudaEvent_t fork = nullptr, join = nullptr;
     unsigned int* counter2 = nullptr;
 };
-constexpr int kSplitObs = 16;   // the light kernel's pixel capacity (3 CTAs per SM)
+constexpr int kSplitObs = 16;   // the light kernel's pixel capacity
 // Resident when it fits (unless force_stream); else the largest slice that
 // fits, or force_slice_atoms (a multiple of 8 no larger than that) if > 0.
 bool plan_sweep(const Geom& g, int maxobs, int device, bool force_stream, int force_slice_atoms, SweepPlan* out);

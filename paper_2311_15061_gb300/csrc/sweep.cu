@@ -129,12 +129,13 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
     flush_counts(a, lane, tl);
 }
 
-// Resident CTAs per SM the register budget is set for: 3 at kSplitObs
-// pixels (the light half of a split sweep), 2 up to 48, else 1.
+// Resident CTAs per SM the register budget is set for: 2 up to 48 pixels,
+// else 1.  (3 CTAs per SM for the 16-pixel kernel spill 76 bytes per
+// thread and measured 3% slower than 2 without spills.)
 template <int MAXOBS, int LANES>
 constexpr int sweep_min_ctas()
 {
-    return LANES == 1 ? (MAXOBS == kSplitObs ? 3 : (MAXOBS <= 48 ? 2 : 1)) : 1;
+    return LANES == 1 && MAXOBS <= 48 ? 2 : 1;
 }
 
 template <int MAXOBS, int LANES>
@@ -337,7 +338,8 @@ cudaError_t launch_sweep(const SweepArgs& a, int maxobs, int grid, cudaStream_t 
 
 // The split sweep: units [0, split_units) on s with the kernel for maxobs,
 // the rest concurrently on plan.side with the kernel for kSplitObs pixels
-// (three CTAs per SM), forked from and joined to s by events.  The heavy
+// (shorter pixel loops, fewer registers), forked from and joined to s by
+// events.  The heavy
 // launch goes first so its few CTAs are resident before the light kernel
 // fills the GPU.
 cudaError_t launch_sweep_split(const SweepArgs& a, const SweepPlan& plan, int maxobs, cudaStream_t s)
