@@ -294,6 +294,7 @@ def run_gpu(args):
         "wall_s": wall,
         "clocks": clocks.summary(),
     }
+    line["posterior_mean"] = posterior_mean_psnr(ctx, clean, iters, stream=stream)
     if not args.no_serving:
         line["serving"] = run_serving(ctx, dict(B=w["B"], S=w["S"], K=w["K"], seed=w["seed"] + rank))
     if not args.no_video:
@@ -541,12 +542,33 @@ def run_video3d(cfg=VIDEO):
            "ms_per_iteration": ms / cfg["iters"],
            "phases_ms_per_iteration": {k: v[0] / cfg["iters"] for k, v in prof.items()},
            "slice_atoms": st.slice_atoms, "slices": st.slices, "max_observed": st.max_observed,
-           "psnr_db_vs_clean": psnr}
+           "psnr_db_vs_clean": psnr,
+           "posterior_mean": posterior_mean_psnr(ctx, clean, cfg["iters"], stream=stream)}
     ctx.close()
     return res
 
 
 PRECISION_ITERS = 50
+MEAN_LAST = 10
+
+
+def posterior_mean_psnr(ctx, clean, iters, last=MEAN_LAST, stream=None):
+    """From the prior, iters Gibbs iterations with the overlap-add
+    reconstructions of the last `last` accumulated on the device: PSNR
+    against the clean frame of the final sample and of the mean of the last
+    `last` samples (the posterior-mean estimate)."""
+    def psnr(a):
+        return float(10 * np.log10(1.0 / np.mean((a.astype(np.float64) - clean) ** 2)))
+    ctx.sensai_reset(stream)
+    ctx.sensai_learn(None, iters - last, stream)
+    ctx.sensai_mean_reset(stream)
+    for _ in range(last):
+        ctx.sensai_learn(None, 1, stream)
+        ctx.sensai_mean_add(stream)
+    final = ctx.sensai_reconstruct(None, stream)
+    mean = ctx.sensai_mean_read(None, stream)
+    return {"iterations": iters, "last_samples": last, "psnr_final_sample_db": psnr(final),
+            "psnr_mean_of_last_db": psnr(mean)}
 
 
 def run_precision():
