@@ -107,6 +107,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
         }
 
         float s2 = 0.0f;
+        begin_patch_counts(tl);
         AtomCarry carry;
         carry.dw = 0.0f;
         carry.cur = code_pair(i, 0, t_it, a.keys);
@@ -124,6 +125,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
                          wb.v[5], wb.v[6], wb.v[7]);
         }
         apply_update<MAXOBS>(ad, r, lp.wmax, carry.dw);   // the last atom's rank-1 update
+        end_patch_counts(tl, lp.nobs);
         finish_patch<MAXOBS, LANES>(a, r, lp.wmax, nl, slot, unit, lane, s2);
     }
     flush_counts(a, lane, tl);

@@ -209,8 +209,17 @@ __device__ __forceinline__ uint32_t even_lane_bits(uint32_t b)
 // Work tallies of one thread (changed updates, their |Omega_i|, z = 1 draws).
 struct CodeTally {
     unsigned int chg_n = 0, chg_obs = 0, act_n = 0;
+    unsigned int chg_n_patch0 = 0;   // chg_n when the current patch began
     unsigned int rb_obs = 0;   // in-sweep residual rebuild: this lane's pixels x non-zero stored weights
 };
+
+// At a patch's start and end: chg_obs gains |Omega_i| per changed update of
+// the patch (counted in chg_n during its atoms).
+__device__ __forceinline__ void begin_patch_counts(CodeTally& tl) { tl.chg_n_patch0 = tl.chg_n; }
+__device__ __forceinline__ void end_patch_counts(CodeTally& tl, int nobs)
+{
+    tl.chg_obs += (tl.chg_n - tl.chg_n_patch0) * (unsigned int)nobs;
+}
 
 // Non-zero weights of a stored 8-atom block.
 __device__ __forceinline__ unsigned int w8_nonzero(const W8& wb)
@@ -305,7 +314,7 @@ __device__ __forceinline__ bool code_block(const PixelAddr<MAXOBS>& ad, Resid<MA
         const bool z = lp.valid && k < K && (x0 < thr || sig >= 1.0f);
         // branch-free from here to the ballot: one basic block per atom lets
         // the next atom's random numbers interleave with this chain
-        const float w_new = z ? fmaf(nrm, sqrtf(rlam), c.ge * g * rlam) : 0.0f;
+        const float w_new = z ? fmaf(nrm, rsqrtf(lam), c.ge * g * rlam) : 0.0f;
         const bool zo = z && owner;
         s2 = zo ? fmaf(w_new, w_new, s2) : s2;
         tl.act_n += zo ? 1u : 0u;
@@ -313,8 +322,7 @@ __device__ __forceinline__ bool code_block(const PixelAddr<MAXOBS>& ad, Resid<MA
         const bool chg = dw != 0.0f;
         changed = changed || chg;
         const bool co = chg && owner;
-        tl.chg_n += co ? 1u : 0u;
-        tl.chg_obs += co ? (unsigned int)lp.nobs : 0u;
+        tl.chg_n += co ? 1u : 0u;   // chg_obs: once per patch (the caller's add_changed_obs)
         wb.v[KK] = w_new;
         carry.dw = dw;
         // the activity word; the pi draws sum the per-atom counts from it

@@ -187,6 +187,7 @@ __device__ __forceinline__ void tiled_body(const SweepArgs& a)
         gather_patch<MAXOBS, LANES>(a, lp.valid ? slot : 0, nl, org, ad, r, half, from_resid);
 
         float s2 = 0.0f;
+        begin_patch_counts(tl);
         W8 nb;
         AtomCarry carry;
         carry.dw = 0.0f;
@@ -236,6 +237,7 @@ __device__ __forceinline__ void tiled_body(const SweepArgs& a)
             }
         }
         if (!ok) break;
+        end_patch_counts(tl, lp.nobs);
         if (warp_on) finish_patch<MAXOBS, LANES>(a, r, lp.wmax, nl, slot, unit, lane, s2);
     }
     // The copies still in flight land before the CTA exits: uses q and q + 1
