@@ -53,10 +53,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
         const int p = idx / ldK, k = idx - p * ldK - kDictColumnOffset;
         Ds[idx] = (p < P && k >= 0 && k < K) ? a.D[(long long)k * P + p] : 0.0f;
     }
-    for (int k = threadIdx.x; k < Kpad; k += blockDim.x) lpi[k] = k < K ? a.lpi[k] : 0.0f;
+    const CodeConst c = code_const(a.sc);
+    // logit(pi_k) + ln(gamma_s) / 2: the log-odds terms that do not depend on the patch
+    for (int k = threadIdx.x; k < Kpad; k += blockDim.x) lpi[k] = (k < K ? a.lpi[k] : 0.0f) + c.half_log_gs;
     __syncthreads();
 
-    const CodeConst c = code_const(a.sc);
     const uint32_t t_it = launch_t(a.t, a.t_dev, a.sc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int half = LANES == 1 ? 0 : (lane & 1);

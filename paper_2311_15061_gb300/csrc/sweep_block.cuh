@@ -304,7 +304,9 @@ __device__ __forceinline__ bool code_block(const PixelAddr<MAXOBS>& ad, Resid<MA
         const float g = fmaf(w_old, n, h);
         const float lam = fmaf(c.ge, n, c.gs);
         const float rlam = __fdividef(1.0f, lam);
-        const float L = lpi_blk[KK] + c.half_log_gs - 0.5f * __logf(lam) + c.half_ge2 * g * g * rlam;
+        const float grl = g * rlam;
+        // lpi_blk holds logit(pi_k) + ln(gamma_s) / 2 (staged per launch)
+        const float L = fmaf(c.half_ge2 * g, grl, fmaf(-0.5f, __logf(lam), lpi_blk[KK]));
         const float sig = __fdividef(1.0f, 1.0f + __expf(-L));
         // z = [x0 < floor(sig 2^32)] in 32-bit integers: the saturating
         // conversion gives the floor below 2^32, and sig = 1 (threshold
@@ -314,7 +316,7 @@ __device__ __forceinline__ bool code_block(const PixelAddr<MAXOBS>& ad, Resid<MA
         const bool z = lp.valid && k < K && (x0 < thr || sig >= 1.0f);
         // branch-free from here to the ballot: one basic block per atom lets
         // the next atom's random numbers interleave with this chain
-        const float w_new = z ? fmaf(nrm, rsqrtf(lam), c.ge * g * rlam) : 0.0f;
+        const float w_new = z ? fmaf(nrm, rsqrtf(lam), c.ge * grl) : 0.0f;
         const bool zo = z && owner;
         s2 = zo ? fmaf(w_new, w_new, s2) : s2;
         tl.act_n += zo ? 1u : 0u;

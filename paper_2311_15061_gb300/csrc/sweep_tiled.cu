@@ -131,7 +131,9 @@ __device__ __forceinline__ void tiled_body(const SweepArgs& a)
     const unsigned int units = (unsigned int)NW * LANES;   // 32-patch chunks, or 16-patch halves
     const long long nitems = (units + kTiledWarps - 1) / kTiledWarps;
 
-    for (int k = threadIdx.x; k < Kpad; k += blockDim.x) lpi[k] = k < K ? a.lpi[k] : 0.0f;
+    // logit(pi_k) + ln(gamma_s) / 2: the log-odds terms that do not depend on the patch
+    const float half_log_gs = code_const(a.sc).half_log_gs;
+    for (int k = threadIdx.x; k < Kpad; k += blockDim.x) lpi[k] = (k < K ? a.lpi[k] : 0.0f) + half_log_gs;
     if (threadIdx.x == 0) {
         abort_s = 0;
         mbar_init(&bar[0], 1);
