@@ -69,3 +69,42 @@ def test_trace_without_ground_truth_and_bad_path(tmp_path):
         ctx.sensai_trace(tmp_path / "missing_dir" / "t.jsonl")
     assert err.value.status == sensai.SENSAI_EINVAL
     ctx.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("flags", [0, "stream"])
+def test_work_tallies_count_the_sweep(flags):
+    """The counters the bench's lane-op model reads, for one code sweep from
+    a state with known codes: patch extraction multiply-adds
+    (sum_i |Omega_i| x non-zero stored weights of i), changed updates and
+    their |Omega_i|, z = 1 draws (both checked against the sweep's result)."""
+    from paper_2311_15061_gb300 import sensai
+    prm, x, clean, mask = problem((64, 64), (8, 8), (1, 1), 16, 0.25, seed=3)
+    st = O.State(prm)
+    O.learn(st, x, mask, 2)
+    fl = 0 if flags == 0 else sensai.SENSAI_FLAG_STREAM_DICTIONARY
+    ctx = gpu_context(prm, mask, fl)
+    ctx.sensai_set_frame(np.ascontiguousarray(x, np.float32))
+    ctx.sensai_set_state(D=st.D.astype(np.float32), Z=st.Z, S=st.S.astype(np.float32), pi=st.pi,
+                         gamma_s=st.gamma_s, gamma_eps=st.gamma_eps, iter=st.t)
+    before = ctx.sensai_get_state()
+    ctx.sensai_profile(1)
+    ctx.sensai_sweep_codes()
+    stats = ctx.sensai_get_stats()
+    after = ctx.sensai_get_state()
+    ctx.sensai_profile(0)
+    ctx.close()
+    # |Omega_i| from the mask: observed pixels of each patch
+    G = [prm.M[d] - prm.B[d] + 1 for d in range(2)]
+    obs = np.array([[int(mask[r:r + 8, c:c + 8].sum()) for c in range(G[1])] for r in range(G[0])]).ravel()
+    w0 = before["Z"].astype(bool) & (before["S"] != 0)
+    # the resident sweep rebuilds the residual itself; the streamed one reads
+    # it from the rebuild pass run before it (not part of the sweep's count)
+    expect_rb = int((obs * w0.sum(axis=1)).sum()) if flags == 0 else 0
+    assert stats.rebuild_observed == expect_rb
+    w_old = np.where(before["Z"].astype(bool), before["S"], 0.0)
+    w_new = np.where(after["Z"].astype(bool), after["S"], 0.0)
+    changed = w_new != w_old
+    assert stats.changed_updates == int(changed.sum())
+    assert stats.changed_observed == int((obs[:, None] * changed).sum())
+    assert stats.active_draws == int(after["Z"].sum())
