@@ -723,7 +723,7 @@ sensai_status sensai_create(const sensai_params* prm, const uint8_t* mask, sensa
     }
     if (ctx->gram) {
         // the work items: each pixel's patch list in segments of at most
-        // 2048 patches (256 tensor-core steps accumulated in FP32)
+        // 2048 patches (one FP32 partial per segment)
         std::vector<int> hr((size_t)P + 1);
         CREATE_CUDA(cudaMemcpy(hr.data(), ctx->Rbase, sizeof(int) * hr.size(), cudaMemcpyDeviceToHost));
         std::vector<int4> items;

@@ -78,7 +78,6 @@ constexpr int kGThreads = 32 * (kGLoaderWarp + 1);
 constexpr int kGRawSlots = 8;                   // ring of the chunks' patch indices and frame values
 constexpr int kGStages = 2;                     // operand stages (A in TMEM, B in shared memory)
 constexpr int kGGroup = 4;                      // chunks per accumulator drain
-constexpr int kGSegment = 2048;                 // most patches of an item
 constexpr int kGRingWords = 2 * kGChunk;        // one chunk's patch indices, then its frame values
 constexpr int kGSboBytes = 272;                 // 8-row group pitch (256 B of data + 16 B)
 constexpr int kGOpFloats = (kGAtoms / 8) * kGSboBytes / 4;   // one 128 x 8 operand: 1088 floats
@@ -593,7 +592,6 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(GramArgs a)
         float ys = 0.0f, yc = 0.0f;
         for (int jj = i0; jj < i1; ++jj) {
             const size_t it = (size_t)a.pitem_idx[jj];
-#pragma unroll
             gm_sum2(ys, yc, a.Ypart[(it * 2 + 0) * kGAtoms + t]);
             gm_sum2(ys, yc, a.Ypart[(it * 2 + 1) * kGAtoms + t]);
         }
