@@ -271,6 +271,18 @@ def test_full_size_chain_dictionary(c2_state):
     assert dict_errors(Dg, od.D).max() <= D_TOL
 
 
+@pytest.mark.parametrize("case", [
+    dict(M=(37, 45), B=(5, 4), S=(1, 1), K=12, frac=0.3),       # ragged chunks, K not a multiple of 8
+    dict(M=(333,), B=(9,), S=(2,), K=5, frac=0.4),               # 1-D, stride 2
+    dict(M=(6, 20, 21), B=(2, 4, 3), S=(2, 2, 3), K=7, frac=0.35),   # 3-D, strides
+    dict(M=(20, 20), B=(4, 4), S=(1, 1), K=1, frac=0.5),         # one atom
+    dict(M=(24, 24), B=(8, 8), S=(1, 1), K=16, frac=1.0, full_mask=True),
+    dict(M=(48, 40), B=(6, 5), S=(3, 5), K=128, frac=0.2),       # the full 128-atom tile
+])
+def test_dense_statistics_edge_geometries(case):
+    _phase_parity(**case, flags=_dense())
+
+
 def test_full_size_dense_statistics_dictionary(c2_state):
     """The dense-statistics form (tensor-core Grams) at full size."""
     prm, x, mask, st = c2_state
