@@ -31,9 +31,9 @@
 // step aligns the addends to the largest with one guard bit and floors; an
 // in-bounds probe on this GPU showed it), a bias that grows with the steps
 // accumulated.  So the accumulator is drained every 4 chunks (16 steps of 8
-// patches) into running sums, added in FP32 round-to-
-// nearest: a simulation of that arithmetic on the 128x128 K = 64 workload
-// gives <= 2e-6 relative on the drawn atoms.
+// patches) into running sums added in FP32 round-to-nearest: a simulation of
+// that arithmetic on the 128x128 K = 64 workload gives <= 2e-6 relative on
+// the drawn atoms.
 // Warp roles (448 threads, one CTA per SM):
 //  * warp 13, loader: per chunk, the 32 patch indices and frame values
 //    (loaded a chunk ahead) into one slot of an 8-slot shared ring;
@@ -57,8 +57,8 @@
 // MMAs in flight are waited for and TMEM is freed.
 //
 // gram_reduce_kernel -- the compensated sums of every pixel's item partials,
-// in item order; gram_draw_kernel -- one CTA per pixel p: symmetrises the sum into
-// C_p and makes the K atom-ordered draws in FP64.
+// in item order; gram_draw_kernel -- one CTA per pixel p: symmetrises the
+// sum into C_p and makes the K atom-ordered draws in FP64.
 #include <algorithm>
 #include <vector>
 
