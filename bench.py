@@ -559,6 +559,7 @@ def posterior_mean_psnr(ctx, clean, iters, last=MEAN_LAST, stream=None):
     `last` samples (the posterior-mean estimate)."""
     def psnr(a):
         return float(10 * np.log10(1.0 / np.mean((a.astype(np.float64) - clean) ** 2)))
+    last = max(1, min(last, iters))
     ctx.sensai_reset(stream)
     ctx.sensai_learn(None, iters - last, stream)
     ctx.sensai_mean_reset(stream)

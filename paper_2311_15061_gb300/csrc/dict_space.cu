@@ -26,8 +26,10 @@
 // CTA sums its threads per chain in a fixed order and publishes the partial;
 // (3) grid barrier; (4) CTA c sums the partials (stored chain-major, so one
 // owner reads one contiguous block) of chains c, c + grid, ...
-// over all CTAs in a fixed order (FP64) and draws the block's 8 atoms at those
-// pixels; (5) grid barrier; (6) every thread reads its chain's 8 updates.
+// over all CTAs in a fixed order (compensated FP32: FP64 arithmetic runs at a
+// small fraction of the FP32 rate on this part) and draws the block's 8 atoms
+// at those pixels; (5) grid barrier; (6) every thread reads its chain's 8
+// updates.
 // One cooperative launch, one CTA per SM; the barrier spins are bounded and
 // report SENSAI_ETIMEOUT through the status word instead of hanging.
 #include "internal.cuh"
@@ -180,14 +182,24 @@ __global__ void __launch_bounds__(kDSThreads) ds_fill_kernel(Geom g, const int* 
     }
 }
 
+// s + e += x by Knuth's TwoSum: s takes the rounded sum, e collects its exact
+// rounding error.
+__device__ __forceinline__ void two_sum_acc(float& s, float& e, float x)
+{
+    const float t = s + x;
+    const float bp = t - s;
+    e += (s - (t - bp)) + (x - bp);
+    s = t;
+}
+
 template <bool RHO_SMEM>
 __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpaceArgs a)
 {
     extern __shared__ float dyn[];
     __shared__ float dold8[kAtomBlock];
     __shared__ float gain8[kAtomBlock], noise8[kAtomBlock];
-    __shared__ double fin[kDSRed];
-    __shared__ double tmp[kDSRed][11];
+    __shared__ float fin[kDSRed];
+    __shared__ float tmp_s[kDSRed][11], tmp_e[kDSRed][11];
     __shared__ float r2_s[kDSThreads / 32];
     const Geom& g = a.g;
     const int P = g.P, K = g.K, KB = g.KB;
@@ -275,7 +287,10 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
 #undef DS_APPLY
         if (kb == KB) break;
 
-        // per chain: sum the groups in order, publish the CTA partial [c][v][q]
+        // per chain: sum the groups in order and publish the CTA partial
+        // part[q][c][v].  With several groups the sums are staged in shared
+        // memory (group 0 overwrites its own row of slot 0 after reading it)
+        // and the whole CTA stores them as P contiguous 44-word runs.
         if (active && grp > 0) {
 #pragma unroll
             for (int v = 0; v < kDSRed; ++v) red[((size_t)(grp - 1) * P + q) * kDSRedPad + v] = acc[v];
@@ -286,13 +301,25 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
 #pragma unroll
                 for (int v = 0; v < kDSRed; ++v) acc[v] += red[((size_t)(h - 1) * P + q) * kDSRedPad + v];
             }
+            if (G > 1) {
 #pragma unroll
-            for (int v = 0; v < kDSRed; ++v) a.part[((size_t)q * ncta + c) * kDSRed + v] = acc[v];
+                for (int v = 0; v < kDSRed; ++v) red[(size_t)q * kDSRedPad + v] = acc[v];
+            } else {
+#pragma unroll
+                for (int v = 0; v < kDSRed; ++v) a.part[((size_t)q * ncta + c) * kDSRed + v] = acc[v];
+            }
+        }
+        if (G > 1) {
+            __syncthreads();
+            for (int e = t; e < P * kDSRed; e += T) {
+                const int qq = e / kDSRed, v = e - qq * kDSRed;
+                a.part[((size_t)qq * ncta + c) * kDSRed + v] = red[(size_t)qq * kDSRedPad + v];
+            }
         }
         if (!grid_barrier(a.bar, (unsigned int)(2 * kb + 1) * ncta, &a.sc->status)) return;
 
-        // chains c, c + grid, ...: fixed-order FP64 sums of the CTA partials,
-        // then the 8 sequential draws
+        // chains c, c + grid, ...: fixed-order compensated sums of the CTA
+        // partials, then the 8 sequential draws
         for (int ch = c; ch < P; ch += ncta) {
             // 11 groups of CTAs per value; each thread's loads are issued
             // together (independent), then summed in order
@@ -300,46 +327,50 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
             if (t < kDSRed * 11) {
                 const int v = t % kDSRed, h = t / kDSRed;
                 const int c0 = h * per, c1 = min(ncta, (h + 1) * per);
-                double sum = 0.0;
+                float sum = 0.0f, err = 0.0f;
                 for (int cb = c0; cb < c1; cb += 16) {
                     float x[16];
 #pragma unroll
                     for (int u = 0; u < 16; ++u)
                         x[u] = (cb + u < c1) ? __ldcg(&a.part[((size_t)ch * ncta + cb + u) * kDSRed + v]) : 0.0f;
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) sum += (double)x[u];
+                    for (int u = 0; u < 16; ++u) two_sum_acc(sum, err, x[u]);
                 }
-                tmp[v][h] = sum;
+                tmp_s[v][h] = sum;
+                tmp_e[v][h] = err;
             }
             if (t < kAtomBlock && kb * kAtomBlock + t < K) dold8[t] = a.D[(long long)(kb * kAtomBlock + t) * P + ch];
             __syncthreads();
             if (t < kDSRed) {
-                double sum = 0.0;
-                for (int h = 0; h < 11; ++h) sum += tmp[t][h];
-                fin[t] = sum;
+                float sum = 0.0f, err = 0.0f;
+                for (int h = 0; h < 11; ++h) {
+                    two_sum_acc(sum, err, tmp_s[t][h]);
+                    err += tmp_e[t][h];
+                }
+                fin[t] = sum + err;
             }
             __syncthreads();
             const float* xo = xis + (size_t)((ch - c) / ncta) * K;
             if (t < kAtomBlock) {
                 // per atom, in parallel: gamma_eps / Lambda and the noise term Lambda^-1/2 xi
                 const int k = kb * kAtomBlock + t;
-                const float ckk = (float)fin[kAtomBlock + t * (t + 1) / 2 + t];
+                const float ckk = fin[kAtomBlock + t * (t + 1) / 2 + t];
                 const float prec = (float)P + gef * ckk;
                 gain8[t] = gef / prec;
                 noise8[t] = k < K ? xo[k] * rsqrtf(prec) : 0.0f;
             }
             __syncthreads();
             if (t == 0) {
-                // the 8 sequential draws in FP32 on the FP64-reduced sums
+                // the 8 sequential draws in FP32 on the reduced sums
                 float dl[kAtomBlock];
                 for (int kk = 0; kk < kAtomBlock; ++kk) {
                     const int k = kb * kAtomBlock + kk;
                     dl[kk] = 0.0f;
                     if (k >= K) continue;
                     const float d_old = dold8[kk];
-                    const float ckk = (float)fin[kAtomBlock + kk * (kk + 1) / 2 + kk];
-                    float num = (float)fin[kk] + d_old * ckk;             // sum w_k r^{-k}
-                    for (int l = 0; l < kk; ++l) num = fmaf(-dl[l], (float)fin[kAtomBlock + kk * (kk + 1) / 2 + l], num);
+                    const float ckk = fin[kAtomBlock + kk * (kk + 1) / 2 + kk];
+                    float num = fin[kk] + d_old * ckk;                    // sum w_k r^{-k}
+                    for (int l = 0; l < kk; ++l) num = fmaf(-dl[l], fin[kAtomBlock + kk * (kk + 1) / 2 + l], num);
                     const float dnew = fmaf(gain8[kk], num, noise8[kk]);
                     a.D[(long long)k * P + ch] = dnew;
                     dl[kk] = dnew - d_old;
