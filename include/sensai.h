@@ -167,6 +167,10 @@ typedef struct {
     int32_t slices;            /* code sweep: streamed slices per pass (0 when resident) */
     int64_t rebuild_observed;  /* residual rebuilds inside code sweeps (patch extraction): sum of
                                   |Omega_i| x non-zero stored weights, since the last profile start */
+    int32_t dictionary_form;   /* kernel of the dictionary draw: 0 one CTA per chain, 1 space-organised
+                                  (weight records read through L1), 2 space-organised with each atom
+                                  block's weight records staged in shared memory, 3 dense statistics */
+    int32_t dictionary_smem_kb;  /* dynamic shared memory of the dictionary kernel, KB (forms 1 and 2) */
 } sensai_stats;
 
 /* Create a context on the current CUDA device.  `mask` is prod(M) host bytes

@@ -1159,6 +1159,8 @@ sensai_status sensai_get_stats(sensai_ctx* ctx, sensai_stats* stats)
     stats->rebuild_observed = (int64_t)sc.rb_obs;
     stats->slice_atoms = ctx->sweep_plan.slice_atoms;
     stats->slices = ctx->sweep_plan.slices;
+    stats->dictionary_form = ctx->gram ? 3 : ctx->ds.grid > 0 ? (ctx->ds.staged ? 2 : 1) : 0;
+    stats->dictionary_smem_kb = ctx->gram || ctx->ds.grid == 0 ? 0 : (int32_t)((ctx->ds.smem + 1023) / 1024);
     return SENSAI_OK;
 }
 

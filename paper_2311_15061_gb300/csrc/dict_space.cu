@@ -52,28 +52,38 @@ constexpr long long kBarrierSpins = 1LL << 24;               // x ~64 ns sleep: 
 // (release is cumulative over what the block barrier ordered before it), and
 // polls with acquire loads.  Returns false (and sets *status) if it does not
 // complete within the spin and time limits.
+// The two halves, for a CTA that works between its arrival and its wait:
+// grid_arrive by one thread after a block barrier, grid_wait by the same
+// thread (1 = complete, 0 = gave up and set *status).
+__device__ __forceinline__ void grid_arrive(unsigned int* count)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+}
+
+__device__ int grid_wait(unsigned int* count, unsigned int target, int* status)
+{
+    unsigned long long t0 = 0;   // the global timer (a slow read) once a poll has failed
+    long long spins = 0;
+    for (;;) {
+        unsigned int v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+        if (v >= target) return 1;
+        if (spins == 0) t0 = global_ns();
+        if (++spins > kBarrierSpins || ((spins & 255) == 0 && global_ns() - t0 > kWaitLimitNs)) {
+            atomicExch(status, (int)SENSAI_ETIMEOUT);
+            return 0;
+        }
+        __nanosleep(32);
+    }
+}
+
 __device__ bool grid_barrier(unsigned int* count, unsigned int target, int* status)
 {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ok = 1;
-        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
-        unsigned long long t0 = 0;   // the global timer (a slow read) once a poll has failed
-        long long spins = 0;
-        for (;;) {
-            unsigned int v;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
-            if (v >= target) break;
-            if (spins == 0) t0 = global_ns();
-            if (++spins > kBarrierSpins || ((spins & 255) == 0 && global_ns() - t0 > kWaitLimitNs)) {
-                atomicExch(status, (int)SENSAI_ETIMEOUT);
-                ok = 0;
-                break;
-            }
-            __nanosleep(32);
-        }
-        ok_s = ok;
+        grid_arrive(count);
+        ok_s = grid_wait(count, target, status);
     }
     __syncthreads();
     return ok_s != 0;
@@ -154,11 +164,27 @@ __global__ void __launch_bounds__(kDSThreads) ds_count_kernel(Geom g, const int*
     }
 }
 
-// Planning pass 2: the patch of every pair and, for the sweep, the pair of
-// every (observed pixel j, patch i): pos[j][i].
+// Position of patch i inside CTA c's staged neighbourhood nb[c] = {origin
+// a0[kMaxDim], extents E[kMaxDim]} of the patch grid (row-major).
+__device__ __forceinline__ int local_record(const Geom& g, long long i, const int* nb)
+{
+    int l = 0, mul = 1;
+    for (int d = g.ndim - 1; d >= 0; --d) {
+        const int a = (int)(i % g.G[d]);
+        i /= g.G[d];
+        l += (a - nb[d]) * mul;
+        mul *= nb[kMaxDim + d];
+    }
+    return l;
+}
+
+// Planning pass 2: the patch of every pair (its neighbourhood position when
+// the weights are staged) and, for the sweep, the pair of every (observed
+// pixel j, patch i): pos[j][i].
 __global__ void __launch_bounds__(kDSThreads) ds_fill_kernel(Geom g, const int* order, const int* start,
                                                              const long long* base, const uint16_t* obs,
-                                                             const uint16_t* nobs, int* pidx, int* pos)
+                                                             const uint16_t* nobs, const int* nb, int* pidx,
+                                                             int* pos)
 {
     const int c = blockIdx.x, t = threadIdx.x;
     const int G = kDSThreads / g.P;
@@ -171,7 +197,7 @@ __global__ void __launch_bounds__(kDSThreads) ds_fill_kernel(Geom g, const int* 
     for (int j = grp; j < L; j += G) {
         const long long i = pair_patch(g, order[lo + j], qd);
         if (i < 0) continue;
-        pidx[idx] = (int)i;
+        pidx[idx] = nb ? local_record(g, i, nb + (size_t)c * 2 * kMaxDim) : (int)i;
         const int no = nobs[i];
         for (int jj = 0; jj < no; ++jj)
             if (obs[(long long)jj * g.N + i] == q) {
@@ -192,10 +218,60 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& e, float x)
     s = t;
 }
 
-template <bool RHO_SMEM>
+// One 8-atom block's weight records for this CTA's patch neighbourhood, by
+// cp.async copies of 16 bytes: the first half of every record (atoms 0-3 of
+// the block) to buf[0, half), the second half to buf[half, 2 half), both in
+// neighbourhood order, so that a warp reading a run of neighbouring records
+// reads consecutive shared-memory words.  Consecutive threads copy
+// consecutive 16-byte pieces of a neighbourhood row.
+__device__ __forceinline__ void ds_stage(float* buf, int half, const float* Wblk, const int* rowbase, int nrec,
+                                         int elast)
+{
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(buf);
+    for (int c = threadIdx.x; c < 2 * nrec; c += kDSThreads) {
+        const int rec = c >> 1, h = c & 1;
+        const int r = rec / elast;
+        const float* src = Wblk + ((long long)rowbase[r] + (rec - r * elast)) * kAtomBlock + h * 4;
+        const uint32_t dst = s0 + (uint32_t)(((size_t)h * half + (size_t)rec * 4) * sizeof(float));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Waits for this thread's staging copies (plain loads: they always complete).
+__device__ __forceinline__ void ds_stage_wait()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Record l of a staged block.
+__device__ __forceinline__ W8 lds_w8_split(const float* buf, int half, int l)
+{
+    const float4 lo = *reinterpret_cast<const float4*>(buf + (size_t)l * 4);
+    const float4 hi = *reinterpret_cast<const float4*>(buf + half + (size_t)l * 4);
+    W8 w;
+    w.v[0] = lo.x;
+    w.v[1] = lo.y;
+    w.v[2] = lo.z;
+    w.v[3] = lo.w;
+    w.v[4] = hi.x;
+    w.v[5] = hi.y;
+    w.v[6] = hi.z;
+    w.v[7] = hi.w;
+    return w;
+}
+
+// RHO_SMEM: the residual pairs live in shared memory during the launch.
+// STAGED: each block's weight records for the CTA's neighbourhood are copied
+// to shared memory (two buffers: block b in buffer b & 1, the next block
+// copied while the CTAs reduce and draw the current one) instead of being
+// read through L1 from global memory.
+// Dynamic shared memory: [buffer 0][buffer 1][red, unless it shares the
+// buffer of the previous block][rowbase][xis][rho_s].
+template <bool RHO_SMEM, bool STAGED>
 __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpaceArgs a)
 {
-    extern __shared__ float dyn[];
+    extern __shared__ __align__(16) float dyn[];
     __shared__ float dold8[kAtomBlock];
     __shared__ float gain8[kAtomBlock], noise8[kAtomBlock];
     __shared__ float fin[kDSRed];
@@ -212,13 +288,39 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
     const int lane = t & 31, warp = t >> 5;
     constexpr int T = kDSThreads;
 
-    float* red = dyn;                                               // [G-1][P][kDSRedPad]
-    float* xis = red + (size_t)(G - 1) * P * kDSRedPad;            // [own_max][K] normals of owned chains
+    float* bufs = dyn;                                               // 2 x buf_floats (staged)
+    float* red_sep = dyn + 2 * (size_t)a.buf_floats;                 // [G-1][P][kDSRedPad] or empty
+    int* rowbase = reinterpret_cast<int*>(red_sep + a.red_sep_floats);   // [rows_max] (staged)
+    float* xis = reinterpret_cast<float*>(rowbase + a.rows_max);     // [own_max][K] normals of owned chains
     float* rho_s = xis + (size_t)a.own_max * K;                      // [max_np][T] staged residual pairs
     const long long base = a.base[c];
     const int np = a.np[(size_t)c * T + t];                         // 0 for idle threads
     const int* pid = a.pidx + base + t;                             // pair jp: pid[jp * T]
     float* rho = RHO_SMEM ? rho_s + t : a.R + base + t;            // pair jp: rho[jp * T]
+
+    // the neighbourhood of the CTA's box in the patch grid: nrec records in
+    // rows of elast; rowbase[r] = global index of row r's first record
+    int nrec = 0, elast = 1;
+    if (STAGED) {
+        const int* nbc = a.nb + (size_t)c * 2 * kMaxDim;
+        nrec = 1;
+        for (int d = 0; d < g.ndim; ++d) nrec *= nbc[kMaxDim + d];
+        elast = max(1, nbc[kMaxDim + g.ndim - 1]);
+        const int rows = nrec / elast;
+        for (int r = t; r < rows; r += T) {
+            long long i = nbc[g.ndim - 1], mul = g.G[g.ndim - 1];
+            int rr = r;
+            for (int d = g.ndim - 2; d >= 0; --d) {
+                const int e = nbc[kMaxDim + d];
+                i += (long long)(nbc[d] + rr % e) * mul;
+                rr /= e;
+                mul *= g.G[d];
+            }
+            rowbase[r] = (int)i;
+        }
+        __syncthreads();
+        if (KB > 0) ds_stage(bufs, a.half_floats, a.W, rowbase, nrec, elast);
+    }
     if (RHO_SMEM)
         for (int jp = 0; jp < np; ++jp) rho[(size_t)jp * T] = a.R[base + t + (long long)jp * T];
     for (int idx = t; idx < a.own_max * K; idx += blockDim.x) {
@@ -237,60 +339,120 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
 #pragma unroll
     for (int k = 0; k < kAtomBlock; ++k) dq[k] = 0.0f;
 
+    // staged: the record index and residual of a pair are loaded four pairs
+    // ahead; the first four of a pass are loaded before the barriers that
+    // precede it
+    int hp0 = 0, hp1 = 0, hp2 = 0, hp3 = 0;
+    float hr0 = 0.0f, hr1 = 0.0f, hr2 = 0.0f, hr3 = 0.0f;
+#define DS_HEAD(J_, PX, RX)                                                \
+    do {                                                                   \
+        if ((J_) < np) {                                                   \
+            PX = pid[(size_t)(J_) * T];                                    \
+            RX = rho[(size_t)(J_) * T];                                    \
+        }                                                                  \
+    } while (0)
+    if (STAGED) {
+        DS_HEAD(0, hp0, hr0);
+        DS_HEAD(1, hp1, hr1);
+        DS_HEAD(2, hp2, hr2);
+        DS_HEAD(3, hp3, hr3);
+    }
+
     for (int kb = 0; kb <= KB; ++kb) {
+        if (STAGED) {   // block kb has landed in buffer kb & 1
+            ds_stage_wait();
+            __syncthreads();
+        }
         float acc[kDSRed];
 #pragma unroll
         for (int v = 0; v < kDSRed; ++v) acc[v] = 0.0f;
-        const float* qprev = a.W + (long long)(kb > 0 ? kb - 1 : 0) * Npad * kAtomBlock;
-        const float* qcur = a.W + (long long)(kb < KB ? kb : 0) * Npad * kAtomBlock;
-        // two pairs in flight: the loads of one are issued before the other
-        // is applied (alternating register sets, no copies of pending loads)
         const bool has_prev = kb > 0, has_cur = kb < KB;
-        W8 ua, va, ub, vb;
-        float ra = 0.0f, rb = 0.0f;
-        // each register set's next patch index is loaded one loop iteration
-        // (two pairs) before the weight loads that use it
-        int pa = np > 0 ? pid[0] : 0, pb = np > 1 ? pid[(size_t)T] : 0;
-#define DS_LOAD(J_, R_, U, V, PX)                                          \
+#define DS_ACCUMULATE(R_, V)                                               \
         do {                                                               \
-            const long long i_ = PX;                                       \
-            PX = (J_) + 2 < np ? pid[(size_t)((J_) + 2) * T] : 0;          \
-            R_ = rho[(size_t)(J_) * T];                                    \
-            if (has_prev) U = load_w8(qprev + i_ * kAtomBlock);            \
-            if (has_cur) V = load_w8(qcur + i_ * kAtomBlock);              \
-        } while (0)
-#define DS_APPLY(J_, R_, U, V)                                             \
-        do {                                                               \
-            if (has_prev) {                                                \
-                _Pragma("unroll") for (int k = 0; k < kAtomBlock; ++k)     \
-                    R_ = fmaf(-dq[k], U.v[k], R_);                         \
-                rho[(size_t)(J_) * T] = R_;                                \
+            _Pragma("unroll") for (int k = 0; k < kAtomBlock; ++k) {       \
+                acc[k] = fmaf(V.v[k], R_, acc[k]);                         \
+                _Pragma("unroll") for (int l = 0; l <= k; ++l)             \
+                    acc[kAtomBlock + k * (k + 1) / 2 + l] =                \
+                        fmaf(V.v[k], V.v[l], acc[kAtomBlock + k * (k + 1) / 2 + l]); \
             }                                                              \
-            if (has_cur) {                                                 \
-                _Pragma("unroll") for (int k = 0; k < kAtomBlock; ++k) {   \
-                    acc[k] = fmaf(V.v[k], R_, acc[k]);                     \
-                    _Pragma("unroll") for (int l = 0; l <= k; ++l)         \
-                        acc[kAtomBlock + k * (k + 1) / 2 + l] =            \
-                            fmaf(V.v[k], V.v[l], acc[kAtomBlock + k * (k + 1) / 2 + l]); \
+        } while (0)
+        if (STAGED) {
+            const float* sprev = bufs + (size_t)((kb + 1) & 1) * a.buf_floats;   // block kb - 1
+            const float* scur = bufs + (size_t)(kb & 1) * a.buf_floats;          // block kb
+            const int half = a.half_floats;
+#define DS_PAIR(J_, PX, RX)                                                \
+            do {                                                           \
+                const int l_ = PX;                                         \
+                float r_ = RX;                                             \
+                DS_HEAD((J_) + 4, PX, RX);                                 \
+                if (has_prev) {                                            \
+                    const W8 u_ = lds_w8_split(sprev, half, l_);           \
+                    _Pragma("unroll") for (int k = 0; k < kAtomBlock; ++k) \
+                        r_ = fmaf(-dq[k], u_.v[k], r_);                    \
+                    rho[(size_t)(J_) * T] = r_;                            \
                 }                                                          \
-            }                                                              \
-        } while (0)
-        if (np > 0) DS_LOAD(0, ra, ua, va, pa);
-        for (int jp = 0; jp < np; jp += 2) {
-            if (jp + 1 < np) DS_LOAD(jp + 1, rb, ub, vb, pb);
-            DS_APPLY(jp, ra, ua, va);
-            if (jp + 1 >= np) break;
-            if (jp + 2 < np) DS_LOAD(jp + 2, ra, ua, va, pa);
-            DS_APPLY(jp + 1, rb, ub, vb);
-        }
+                if (has_cur) {                                             \
+                    const W8 v_ = lds_w8_split(scur, half, l_);            \
+                    DS_ACCUMULATE(r_, v_);                                 \
+                }                                                          \
+            } while (0)
+            for (int jp = 0; jp < np; jp += 4) {
+                DS_PAIR(jp, hp0, hr0);
+                if (jp + 1 < np) DS_PAIR(jp + 1, hp1, hr1);
+                if (jp + 2 < np) DS_PAIR(jp + 2, hp2, hr2);
+                if (jp + 3 < np) DS_PAIR(jp + 3, hp3, hr3);
+            }
+#undef DS_PAIR
+        } else {
+            const float* qprev = a.W + (long long)(kb > 0 ? kb - 1 : 0) * Npad * kAtomBlock;
+            const float* qcur = a.W + (long long)(kb < KB ? kb : 0) * Npad * kAtomBlock;
+            // two pairs in flight: the loads of one are issued before the other
+            // is applied (alternating register sets, no copies of pending loads)
+            W8 ua, va, ub, vb;
+            float ra = 0.0f, rb = 0.0f;
+            // each register set's next patch index is loaded one loop iteration
+            // (two pairs) before the weight loads that use it
+            int pa = np > 0 ? pid[0] : 0, pb = np > 1 ? pid[(size_t)T] : 0;
+#define DS_LOAD(J_, R_, U, V, PX)                                          \
+            do {                                                           \
+                const long long i_ = PX;                                   \
+                PX = (J_) + 2 < np ? pid[(size_t)((J_) + 2) * T] : 0;      \
+                R_ = rho[(size_t)(J_) * T];                                \
+                if (has_prev) U = load_w8(qprev + i_ * kAtomBlock);        \
+                if (has_cur) V = load_w8(qcur + i_ * kAtomBlock);          \
+            } while (0)
+#define DS_APPLY(J_, R_, U, V)                                             \
+            do {                                                           \
+                if (has_prev) {                                            \
+                    _Pragma("unroll") for (int k = 0; k < kAtomBlock; ++k) \
+                        R_ = fmaf(-dq[k], U.v[k], R_);                     \
+                    rho[(size_t)(J_) * T] = R_;                            \
+                }                                                          \
+                if (has_cur) DS_ACCUMULATE(R_, V);                         \
+            } while (0)
+            if (np > 0) DS_LOAD(0, ra, ua, va, pa);
+            for (int jp = 0; jp < np; jp += 2) {
+                if (jp + 1 < np) DS_LOAD(jp + 1, rb, ub, vb, pb);
+                DS_APPLY(jp, ra, ua, va);
+                if (jp + 1 >= np) break;
+                if (jp + 2 < np) DS_LOAD(jp + 2, ra, ua, va, pa);
+                DS_APPLY(jp + 1, rb, ub, vb);
+            }
 #undef DS_LOAD
 #undef DS_APPLY
+        }
+#undef DS_ACCUMULATE
         if (kb == KB) break;
 
         // per chain: sum the groups in order and publish the CTA partial
         // part[q][c][v].  With several groups the sums are staged in shared
         // memory (group 0 overwrites its own row of slot 0 after reading it)
-        // and the whole CTA stores them as P contiguous 44-word runs.
+        // and the whole CTA stores them as P contiguous 44-word runs.  When
+        // staged, the scratch may be the buffer of block kb - 1, which the
+        // pass has just finished reading.
+        const bool red_in_buf = STAGED && a.red_sep_floats == 0;
+        float* red = red_in_buf ? bufs + (size_t)((kb + 1) & 1) * a.buf_floats : red_sep;
+        if (red_in_buf) __syncthreads();
         if (active && grp > 0) {
 #pragma unroll
             for (int v = 0; v < kDSRed; ++v) red[((size_t)(grp - 1) * P + q) * kDSRedPad + v] = acc[v];
@@ -316,7 +478,28 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
                 a.part[((size_t)qq * ncta + c) * kDSRed + v] = red[(size_t)qq * kDSRedPad + v];
             }
         }
-        if (!grid_barrier(a.bar, (unsigned int)(2 * kb + 1) * ncta, &a.sc->status)) return;
+        // grid barrier: arrive once the whole CTA has published; then, before
+        // waiting, copy block kb + 1 into buffer (kb + 1) & 1 (free now that
+        // every thread is past the pass and the publish) and load the head
+        // of the next pass, all of which overlaps the other CTAs' arrivals
+        __shared__ int ok_s;
+        __syncthreads();
+        if (t == 0) grid_arrive(a.bar);
+        if (STAGED) {
+            if (kb + 1 < KB)
+                ds_stage(bufs + (size_t)((kb + 1) & 1) * a.buf_floats, a.half_floats,
+                         a.W + (long long)(kb + 1) * Npad * kAtomBlock, rowbase, nrec, elast);
+            DS_HEAD(0, hp0, hr0);
+            DS_HEAD(1, hp1, hr1);
+            DS_HEAD(2, hp2, hr2);
+            DS_HEAD(3, hp3, hr3);
+        }
+        if (t == 0) ok_s = grid_wait(a.bar, (unsigned int)(2 * kb + 1) * ncta, &a.sc->status);
+        __syncthreads();
+        if (!ok_s) {
+            if (STAGED) ds_stage_wait();
+            return;
+        }
 
         // chains c, c + grid, ...: fixed-order compensated sums of the CTA
         // partials, then the 8 sequential draws
@@ -379,13 +562,17 @@ __global__ void __launch_bounds__(kDSThreads, 1) dict_space_kernel(const DictSpa
             }
             __syncthreads();
         }
-        if (!grid_barrier(a.bar, (unsigned int)(2 * kb + 2) * ncta, &a.sc->status)) return;
+        if (!grid_barrier(a.bar, (unsigned int)(2 * kb + 2) * ncta, &a.sc->status)) {
+            if (STAGED) ds_stage_wait();
+            return;
+        }
         if (active) {
 #pragma unroll
             for (int k = 0; k < kAtomBlock; ++k) dq[k] = __ldcg(&a.delta[q * kAtomBlock + k]);
         }
     }
 
+#undef DS_HEAD
     // write the residual back; this CTA's share of sum ||r||^2
     float r2 = 0.0f;
     for (int jp = 0; jp < np; ++jp) {
@@ -476,14 +663,15 @@ void split_boxes(const Geom& g, const uint8_t* mask, const Box& b, int n, std::v
 }
 
 // Observed pixels of each box, tile by tile, raster order inside a tile.
-void order_pixels(const Geom& g, const uint8_t* mask, int ncta, std::vector<int>& order, std::vector<int>& start)
+void order_pixels(const Geom& g, const uint8_t* mask, int ncta, std::vector<int>& order, std::vector<int>& start,
+                  std::vector<Box>& boxes)
 {
     Box all;
     for (int d = 0; d < g.ndim; ++d) {
         all.lo[d] = 0;
         all.hi[d] = (int)g.M[d];
     }
-    std::vector<Box> boxes;
+    boxes.clear();
     split_boxes(g, mask, all, ncta, boxes);
     int tile[kMaxDim];
     for (int d = 0; d < g.ndim; ++d) tile[d] = std::max(1, std::min(g.B[d], 8));
@@ -511,14 +699,39 @@ void order_pixels(const Geom& g, const uint8_t* mask, int ncta, std::vector<int>
 
 size_t ds_fixed_smem()
 {
-    return sizeof(double) * (kDSRed + kDSRed * 11) + 4 * kAtomBlock + 4 * (kDSThreads / 32) + 256;
+    return sizeof(float) * (kDSRed + 2 * kDSRed * 11 + 3 * kAtomBlock + kDSThreads / 32) + 256;
+}
+
+// The patch-grid neighbourhood of box b: the patches holding any of its
+// pixels, origin o[d] and extents o[kMaxDim + d].  Returns the record count.
+long long box_neighbourhood(const Geom& g, const Box& b, int* o)
+{
+    long long n = 1;
+    for (int d = 0; d < g.ndim; ++d) {
+        int a0 = 0, a1 = -1;
+        if (b.hi[d] > b.lo[d]) {
+            const long long lo = (long long)b.lo[d] - g.B[d] + 1;   // first pixel a patch may start at
+            a0 = lo <= 0 ? 0 : (int)((lo + g.S[d] - 1) / g.S[d]);
+            a1 = (int)std::min<long long>(g.G[d] - 1, (b.hi[d] - 1) / g.S[d]);
+        }
+        o[d] = a0;
+        o[kMaxDim + d] = std::max(0, a1 - a0 + 1);
+        n *= o[kMaxDim + d];
+    }
+    return n;
+}
+
+void* ds_kernel_fn(const DictSpacePlan& p)
+{
+    if (p.staged) return p.rho_smem ? (void*)dict_space_kernel<true, true> : (void*)dict_space_kernel<false, true>;
+    return p.rho_smem ? (void*)dict_space_kernel<true, false> : (void*)dict_space_kernel<false, false>;
 }
 
 }  // namespace
 
 void ds_free(DictSpacePlan* p)
 {
-    void* ptrs[] = {p->order, p->start, p->np, p->base, p->pidx, p->part, p->delta, p->bar};
+    void* ptrs[] = {p->order, p->start, p->np, p->base, p->pidx, p->part, p->delta, p->bar, p->nb};
     for (void* v : ptrs)
         if (v) cudaFree(v);
     *p = DictSpacePlan{};
@@ -540,11 +753,13 @@ cudaError_t ds_build(const Geom& g, const uint8_t* mask, const uint16_t* obs, co
     const int grid = sms;
     const int G = kDSThreads / P;
     const int own = (P + grid - 1) / grid;
-    const size_t base_smem = sizeof(float) * ((size_t)(G - 1) * P * kDSRedPad + (size_t)own * g.K);
+    const size_t red_floats = (size_t)(G - 1) * P * kDSRedPad;
+    const size_t base_smem = sizeof(float) * (red_floats + (size_t)own * g.K);
     if (base_smem + ds_fixed_smem() > (size_t)optin) return cudaSuccess;
 
     std::vector<int> order, start;
-    order_pixels(g, mask, grid, order, start);
+    std::vector<Box> boxes;
+    order_pixels(g, mask, grid, order, start, boxes);
     if (order.empty()) return cudaSuccess;
 
     DictSpacePlan p{};
@@ -585,12 +800,39 @@ cudaError_t ds_build(const Geom& g, const uint8_t* mask, const uint16_t* obs, co
         return cudaSuccess;
     }
     DS_TRY(cudaMemcpy(p.base, base.data(), sizeof(long long) * grid, cudaMemcpyHostToDevice));
+
+    // Staging: every CTA's neighbourhood in two buffers of the largest (the
+    // group-sum scratch shares the buffer of the previous block when it fits).
+    std::vector<int> nbh((size_t)grid * 2 * kMaxDim, 0);
+    long long nrec_max = 0, rows_max = 0;
+    for (int c = 0; c < grid; ++c) {
+        int* o = &nbh[(size_t)c * 2 * kMaxDim];
+        const long long n = box_neighbourhood(g, boxes[c], o);
+        const int el = o[kMaxDim + g.ndim - 1];
+        nrec_max = std::max(nrec_max, n);
+        rows_max = std::max(rows_max, el > 0 ? n / el : 0LL);
+    }
+    const long long half = (nrec_max * 4 + 31) / 32 * 32;
+    const size_t stage_red = red_floats <= (size_t)(2 * half) ? 0 : red_floats;
+    const size_t rows_pad = (size_t)(rows_max + 3) / 4 * 4;
+    const size_t staged_smem = sizeof(float) * ((size_t)(4 * half) + stage_red + rows_pad + (size_t)own * g.K);
+    p.staged = nrec_max > 0 && staged_smem + ds_fixed_smem() <= (size_t)optin;
+    if (p.staged) {
+        p.half_floats = (int)half;
+        p.buf_floats = (int)(2 * half);
+        p.red_sep_floats = (int)stage_red;
+        p.rows_max = (int)rows_pad;
+        DS_TRY(cudaMalloc((void**)&p.nb, sizeof(int) * nbh.size()));
+        DS_TRY(cudaMemcpy(p.nb, nbh.data(), sizeof(int) * nbh.size(), cudaMemcpyHostToDevice));
+    } else {
+        p.red_sep_floats = (int)red_floats;
+    }
     DS_TRY(cudaMalloc((void**)&p.pidx, sizeof(int) * (size_t)(total > 0 ? total : 1)));
     float* Rd = nullptr;
     DS_TRY(cudaMalloc((void**)&Rd, sizeof(float) * (size_t)(total > 0 ? total : 1)));
     e = cudaMemsetAsync(Rd, 0, sizeof(float) * (size_t)(total > 0 ? total : 1), s);
     if (e == cudaSuccess) {
-        ds_fill_kernel<<<grid, kDSThreads, 0, s>>>(g, p.order, p.start, p.base, obs, nobs, p.pidx, pos);
+        ds_fill_kernel<<<grid, kDSThreads, 0, s>>>(g, p.order, p.start, p.base, obs, nobs, p.nb, p.pidx, pos);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -599,11 +841,15 @@ cudaError_t ds_build(const Geom& g, const uint8_t* mask, const uint16_t* obs, co
         ds_free(&p);
         return e;
     }
-    // stage the residual pairs in shared memory when that leaves >= 64 KB of L1
+    // the residual pairs in shared memory: beside staged weights when they
+    // fit; else when that leaves >= 64 KB of L1 for the weight records
     const size_t rho_bytes = sizeof(float) * (size_t)p.max_np * kDSThreads;
-    p.rho_smem = base_smem + rho_bytes + ds_fixed_smem() <= (size_t)160 * 1024;
-    p.smem = base_smem + (p.rho_smem ? rho_bytes : 0);
-    void* fn = p.rho_smem ? (void*)dict_space_kernel<true> : (void*)dict_space_kernel<false>;
+    if (p.staged)
+        p.rho_smem = staged_smem + rho_bytes + ds_fixed_smem() <= (size_t)optin;
+    else
+        p.rho_smem = base_smem + rho_bytes + ds_fixed_smem() <= (size_t)160 * 1024;
+    p.smem = (p.staged ? staged_smem : base_smem) + (p.rho_smem ? rho_bytes : 0);
+    void* fn = ds_kernel_fn(p);
     int per_sm = 0;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kDSThreads, p.smem);
@@ -627,9 +873,15 @@ cudaError_t ds_build(const Geom& g, const uint8_t* mask, const uint16_t* obs, co
     return cudaSuccess;
 }
 
-cudaError_t launch_dict_space(const DictSpaceArgs& a, const DictSpacePlan& p, cudaStream_t s)
+cudaError_t launch_dict_space(const DictSpaceArgs& args_in, const DictSpacePlan& p, cudaStream_t s)
 {
-    void* fn = p.rho_smem ? (void*)dict_space_kernel<true> : (void*)dict_space_kernel<false>;
+    DictSpaceArgs a = args_in;
+    a.nb = p.nb;
+    a.half_floats = p.half_floats;
+    a.buf_floats = p.buf_floats;
+    a.red_sep_floats = p.red_sep_floats;
+    a.rows_max = p.rows_max;
+    void* fn = ds_kernel_fn(p);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned int), s);   // the barrier counts from zero each launch

@@ -384,6 +384,12 @@ struct DictSpacePlan {
     int grid = 0;              // CTAs of the cooperative launch; 0: use dict.cu
     size_t smem = 0;           // dynamic shared memory
     bool rho_smem = false;     // residual pairs staged in shared memory
+    bool staged = false;       // weight records staged in shared memory per block
+    int* nb = nullptr;         // [grid][2 * kMaxDim] neighbourhood origin and extents (staged)
+    int half_floats = 0;       // floats of one half-record array of a staging buffer
+    int buf_floats = 0;        // floats of one staging buffer (0 when not staged)
+    int red_sep_floats = 0;    // group-sum scratch outside the staging buffers
+    int rows_max = 0;          // largest neighbourhood row count (staged)
     int own_max = 0;           // chains per CTA: ceil(P / grid)
     int max_np = 0;            // largest pair count of a thread
     long long pairs = 0;       // length of R and pidx (padded)
@@ -391,7 +397,7 @@ struct DictSpacePlan {
     int* start = nullptr;      // [grid + 1] each CTA's range of order
     int* np = nullptr;         // [grid][512] pairs per thread
     long long* base = nullptr; // [grid] first pair of each CTA
-    int* pidx = nullptr;       // patch of every pair
+    int* pidx = nullptr;       // patch of every pair (staged: its neighbourhood position)
     float* part = nullptr;     // [P][grid][44] per-CTA block sums, chain-major
     float* delta = nullptr;    // [P][8] the block's updates
     unsigned int* bar = nullptr;   // grid barrier arrival counter, zeroed per launch
@@ -411,6 +417,8 @@ struct DictSpaceArgs {
     float* delta;
     unsigned int* bar;
     int own_max;
+    const int* nb;             // staged: [grid][2 * kMaxDim]
+    int half_floats, buf_floats, red_sep_floats, rows_max;
     unsigned long long seed;
     uint32_t t;
 };

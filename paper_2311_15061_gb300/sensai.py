@@ -88,6 +88,8 @@ class sensai_stats(ctypes.Structure):
         ("slice_atoms", ctypes.c_int32),
         ("slices", ctypes.c_int32),
         ("rebuild_observed", ctypes.c_int64),
+        ("dictionary_form", ctypes.c_int32),
+        ("dictionary_smem_kb", ctypes.c_int32),
     ]
 
 

@@ -98,6 +98,18 @@ def test_phases_128x128_k64():
     _phase_parity(**C1)
 
 
+def test_dictionary_forms_reported():
+    """sensai_stats.dictionary_form names the kernel each context plans."""
+    from paper_2311_15061_gb300 import sensai
+    prm, x, clean, mask = problem(**C1)
+    for flags, form in ((0, 2), (sensai.SENSAI_FLAG_CHAIN_DICTIONARY, 0), (sensai.SENSAI_FLAG_DENSE_STATISTICS, 3)):
+        ctx = gpu_context(prm, mask, flags)
+        st = ctx.sensai_get_stats()
+        assert st.dictionary_form == form, (flags, st.dictionary_form)
+        assert (st.dictionary_smem_kb > 0) == (form in (1, 2))
+        ctx.close()
+
+
 @pytest.mark.parametrize("seed", [1, 2])
 def test_phases_128x128_other_seeds(seed):
     _phase_parity(**C1, seed=seed, warm=1)
@@ -242,6 +254,7 @@ def test_full_size_code_sweep_sampled(c2_state):
 def test_full_size_dictionary_and_hyper(c2_state):
     prm, x, mask, st = c2_state
     ctx = gpu_context(prm, mask)
+    assert ctx.sensai_get_stats().dictionary_form == 2   # weight records staged in shared memory
     push_state(ctx, st, x)
     ctx.sensai_draw_dictionary()
     Dg = ctx.sensai_get_dictionary()
@@ -256,6 +269,28 @@ def test_full_size_dictionary_and_hyper(c2_state):
     np.testing.assert_allclose(gh["pi"], hst.pi, rtol=1e-9)
     assert abs(gh["gamma_eps"] / hst.gamma_eps - 1) <= 1e-5
     ctx.close()
+
+
+@pytest.mark.parametrize("frac", [0.02, 0.10])
+def test_space_dictionary_unstaged(frac):
+    """768 x 768 frames, 10 x 10 patches, K = 16: the per-CTA patch
+    neighbourhoods are too large to stage, so the space-organised kernel reads
+    the weight records through L1, with the residual pairs in shared memory
+    (2 % observed) or in global memory (10 %)."""
+    prm, x, clean, mask = problem((768, 768), (10, 10), (1, 1), 16, frac, 0)
+    st = O.State(prm)
+    O.zs_sweep(st, x, mask)
+    st.t = 1
+    st = round_state(st)
+    ctx = gpu_context(prm, mask)
+    assert ctx.sensai_get_stats().dictionary_form == 1
+    push_state(ctx, st, x)
+    ctx.sensai_draw_dictionary()
+    Dg = ctx.sensai_get_dictionary()
+    ctx.close()
+    od = st.copy()
+    O.d_sweep(od, x, mask)
+    assert dict_errors(Dg, od.D).max() <= D_TOL
 
 
 def test_full_size_chain_dictionary(c2_state):
