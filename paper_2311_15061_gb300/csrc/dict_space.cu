@@ -13,8 +13,15 @@
 //    (tiles of min(B_d, 8) pixels per dimension), raster order within a tile;
 //  * a thread owns one chain q and every G-th pixel of its CTA's list
 //    (G = 512 / P groups), so at any moment the CTA works on a few
-//    neighbouring pixels.  The ~P patches covering them are a small
-//    neighbourhood of the patch grid whose 32-byte weight records stay in L1;
+//    neighbouring pixels, whose covering patches are neighbours in the
+//    patch grid;
+//  * the patches holding any pixel of a box form its neighbourhood, a box
+//    of the patch grid.  When two neighbourhood-sized buffers fit in shared
+//    memory for every CTA, the kernel is staged: each 8-atom block's 32-byte
+//    weight records of the neighbourhood are copied into shared memory (the
+//    record halves in separate arrays, so a warp reading neighbouring
+//    records reads consecutive words), and a pair's index is its position
+//    in the neighbourhood.  Otherwise the records are read through L1;
 //  * pair jp of thread t in CTA c is element base_c + jp * 512 + t of the
 //    residual array R and of the patch-index array pidx.  Threads of a warp
 //    therefore touch consecutive words; the sweep writes its residuals
