@@ -4,6 +4,9 @@
   include/sensai.h declares (and nothing else under the sensai_ prefix).
 * Argument validation happens before any CUDA call: invalid geometry returns
   SENSAI_EINVAL with a message, on machines with or without a GPU.
+* The binding's ctypes structures have the header's layout: a C program
+  compiled against include/sensai.h prints every structure's size and field
+  offsets, which must equal the ctypes ones.
 """
 import ctypes
 import os
@@ -118,3 +121,31 @@ def test_static_reconstruction_binding_checks_counts(lib):
             lib.sensai_reconstruct_static(prm, args["D"], args["S"], args["out"])
     with pytest.raises(TypeError, match="CUDA"):   # right sizes, host memory
         lib.sensai_reconstruct_static(prm, good["D"], good["S"], good["out"])
+
+
+STRUCTS = ("sensai_params", "sensai_state", "sensai_stats", "sensai_serve_params")
+
+
+def test_struct_layouts_match_header(lib, tmp_path):
+    """Size and every field offset of the C structures (compiled by the host C
+    compiler against the header) equal the binding's ctypes structures."""
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "sensai.h"', "int main(void) {"]
+    for name in STRUCTS:
+        lines.append(f'    printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, *_ in getattr(lib, name)._fields_:
+            lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["    return 0;", "}"]
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in filter(None, out):
+        name, field, value = line.split()
+        got[(name, field)] = int(value)
+    for name in STRUCTS:
+        cls = getattr(lib, name)
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for field, *_ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
