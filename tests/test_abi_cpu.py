@@ -6,7 +6,8 @@
   SENSAI_EINVAL with a message, on machines with or without a GPU.
 * The binding's ctypes structures have the header's layout: a C program
   compiled against include/sensai.h prints every structure's size and field
-  offsets, which must equal the ctypes ones.
+  offsets, which must equal the ctypes ones; likewise the status codes, the
+  flags and the slice-size encoding.
 """
 import ctypes
 import os
@@ -149,3 +150,26 @@ def test_struct_layouts_match_header(lib, tmp_path):
         assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
         for field, *_ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def test_constants_match_header(lib, tmp_path):
+    """Status codes, SENSAI_FLAG_* values and SENSAI_SLICE_ATOMS(n) as the
+    header defines them equal the binding's."""
+    header = open(os.path.join(ROOT, "include", "sensai.h")).read()
+    names = sorted(set(re.findall(r"\b(SENSAI_(?:FLAG_[A-Z0-9_]+|OK|E[A-Z]+))\b", header)))
+    assert "SENSAI_FLAG_DENSE_STATISTICS" in names and "SENSAI_ETIMEOUT" in names
+    slices = (0, 8, 16, 104, 256, 2040)
+    lines = ["#include <stdio.h>", '#include "sensai.h"', "int main(void) {"]
+    lines += [f'    printf("{n} %lld\\n", (long long)({n}));' for n in names]
+    lines += [f'    printf("SLICE{n} %lld\\n", (long long)SENSAI_SLICE_ATOMS({n}));' for n in slices]
+    lines += ["    return 0;", "}"]
+    src, exe = tmp_path / "constants.c", tmp_path / "constants"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.split("\n") if line)
+    for n in names:
+        assert int(out[n]) == getattr(lib, n), n
+    for n in slices:
+        assert int(out[f"SLICE{n}"]) == lib.SENSAI_SLICE_ATOMS(n), n
